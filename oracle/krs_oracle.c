@@ -1,0 +1,561 @@
+/*
+ * krs_oracle.c -- plain, slow, obviously-correct FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark may load this file's library.  It shares no code, header, table or helper
+ * with the CUDA path; the two meet only on the seeded inputs.
+ *
+ * What it computes (Gosselet, Rey & Pebrel, "Total and selective reuse of Krylov
+ * subspaces for the resolution of sequences of nonlinear structural problems"):
+ *   - APCG, the C-augmented M-preconditioned conjugate gradient implemented by
+ *     projection (Section 2.1, Algorithm 1, the initialisation/projector pair of Eq. 5),
+ *     with full reorthogonalisation of the search directions (Section 2.1 remark and
+ *     Section 5 preamble) by classical Gram-Schmidt in the A inner product;
+ *   - TRKS, total reuse of the previous directions (Section 3, Algorithm 2);
+ *   - SRKS, selective reuse of converged Ritz vectors (Section 4, Algorithm 3): the
+ *     Lanczos tridiagonal from the CG coefficients (Section 4.1), its eigenpairs, the
+ *     stagnation test of Section 4.4 and the 1/sqrt(theta) scaling.
+ * Readings of the paper where it is silent or garbled:
+ *   - Algorithm 1's z_j = P M^-1 r_{j+1} is read as P M^-1 r_j; its beta is computed
+ *     before it is used (Gram-Schmidt form); alpha = (r, w)/(Aw, w) as printed.
+ *   - The Lanczos off-diagonal uses beta~_j = rho_{j+1}/rho_j >= 0, rho_j = (r_j, z_j),
+ *     delta_0 = 1/alpha_0, delta_j = 1/alpha_j + beta~_{j-1}/alpha_{j-1},
+ *     eta_j = sqrt(beta~_j)/alpha_j.
+ *   - Ritz values are sorted descending (Algorithm 3 and the interlacing of Section 4.1).
+ *   - The selection is the union (no duplicates) of both stagnation tests; an optional
+ *     filter theta < theta_frac * theta_max follows; the kept vectors are appended in
+ *     ascending theta until the cap; the restart mode resets C to C^(0).
+ *   - Convergence: ||r_j||^2 <= tol^2 ||b||^2 on the recursive residual.
+ * Every floating-point expression is evaluated as written (compiled with
+ * -ffp-contract=off), in plain loops, with no blocking or reordering.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { ORC_OK = 0, ORC_ERR_INVALID_ARG = 1, ORC_ERR_NOT_SPD = 2, ORC_ERR_NO_CONVERGENCE = 3,
+       ORC_ERR_OOM = 4 };
+enum { ORC_RECYCLE_NONE = 0, ORC_RECYCLE_TRKS = 1, ORC_RECYCLE_SRKS = 2 };
+enum { ORC_PRECOND_JACOBI = 0, ORC_PRECOND_BLOCK_JACOBI3 = 1, ORC_PRECOND_IDENTITY = 2 };
+enum { ORC_REORTH_FULL = 0, ORC_REORTH_NONE = 1 };
+enum { ORC_CAP_TRUNCATE = 0, ORC_CAP_RESTART = 1 };
+
+typedef struct {
+  int32_t recycle, precond, reorth, cap_mode, max_aug, max_iter;
+  double ritz_eps, theta_frac;
+} orc_policy;
+
+typedef struct {
+  int32_t status, m, n_c, n_selected, n_c_after;
+  double rel_res, true_rel_res;
+} orc_stats;
+
+/* ----------------------------------------------------------------------------------- */
+/* Dense and sparse building blocks                                                     */
+/* ----------------------------------------------------------------------------------- */
+
+/* y = A x for a 3x3 block-CSR A: y_{3i+d} = sum_k sum_e A_k[d][e] x_{3 col_k + e}. */
+void orc_spmv(int nbr, const int32_t* rp, const int32_t* ci, const double* v,
+              const double* x, double* y) {
+  for (int i = 0; i < nbr; i++) {
+    for (int d = 0; d < 3; d++) {
+      double s = 0.0;
+      for (int k = rp[i]; k < rp[i + 1]; k++) {
+        for (int e = 0; e < 3; e++) s += v[9 * (int64_t)k + 3 * d + e] * x[3 * (int64_t)ci[k] + e];
+      }
+      y[3 * (int64_t)i + d] = s;
+    }
+  }
+}
+
+static double dot(int64_t n, const double* a, const double* b) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
+  return s;
+}
+
+/* Preconditioner M^-1 (Algorithm 1's M): Jacobi stores 1/A_ii, block Jacobi stores the
+ * inverse of each diagonal 3x3 block (adjugate / determinant), identity stores nothing. */
+int orc_precond_setup(int kind, int nbr, const int32_t* rp, const int32_t* ci,
+                      const double* v, double* minv) {
+  for (int i = 0; i < nbr; i++) {
+    const double* D = NULL;
+    for (int k = rp[i]; k < rp[i + 1]; k++)
+      if (ci[k] == i) D = v + 9 * (int64_t)k;
+    if (kind == ORC_PRECOND_IDENTITY) continue;
+    if (D == NULL) return ORC_ERR_INVALID_ARG;
+    if (kind == ORC_PRECOND_JACOBI) {
+      for (int d = 0; d < 3; d++) {
+        if (!(D[4 * d] > 0.0)) return ORC_ERR_NOT_SPD;
+        minv[3 * (int64_t)i + d] = 1.0 / D[4 * d];
+      }
+    } else {
+      double a = D[0], b = D[1], c = D[2], d = D[3], e = D[4], f = D[5], g = D[6], h = D[7], k = D[8];
+      double det = a * (e * k - f * h) - b * (d * k - f * g) + c * (d * h - e * g);
+      if (!(det > 0.0) || !(a > 0.0)) return ORC_ERR_NOT_SPD;
+      double* o = minv + 9 * (int64_t)i;
+      o[0] = (e * k - f * h) / det; o[1] = (c * h - b * k) / det; o[2] = (b * f - c * e) / det;
+      o[3] = (f * g - d * k) / det; o[4] = (a * k - c * g) / det; o[5] = (c * d - a * f) / det;
+      o[6] = (d * h - e * g) / det; o[7] = (b * g - a * h) / det; o[8] = (a * e - b * d) / det;
+    }
+  }
+  return ORC_OK;
+}
+
+void orc_precond_apply(int kind, int nbr, const double* minv, const double* r, double* u) {
+  int64_t n = 3 * (int64_t)nbr;
+  if (kind == ORC_PRECOND_IDENTITY) {
+    for (int64_t i = 0; i < n; i++) u[i] = r[i];
+  } else if (kind == ORC_PRECOND_JACOBI) {
+    for (int64_t i = 0; i < n; i++) u[i] = minv[i] * r[i];
+  } else {
+    for (int64_t i = 0; i < nbr; i++)
+      for (int d = 0; d < 3; d++)
+        u[3 * i + d] = minv[9 * i + 3 * d + 0] * r[3 * i + 0] + minv[9 * i + 3 * d + 1] * r[3 * i + 1]
+                     + minv[9 * i + 3 * d + 2] * r[3 * i + 2];
+  }
+}
+
+/* Cholesky G = L L^T in place (G column-major m x m, lower triangle used and returned). */
+int orc_cholesky(int m, double* G) {
+  for (int j = 0; j < m; j++) {
+    double s = G[j + (int64_t)j * m];
+    for (int k = 0; k < j; k++) s -= G[j + (int64_t)k * m] * G[j + (int64_t)k * m];
+    if (!(s > 0.0)) return ORC_ERR_NOT_SPD;
+    double ljj = sqrt(s);
+    G[j + (int64_t)j * m] = ljj;
+    for (int i = j + 1; i < m; i++) {
+      double t = G[i + (int64_t)j * m];
+      for (int k = 0; k < j; k++) t -= G[i + (int64_t)k * m] * G[j + (int64_t)k * m];
+      G[i + (int64_t)j * m] = t / ljj;
+    }
+  }
+  return ORC_OK;
+}
+
+/* y <- (L L^T)^-1 y by a forward then a backward substitution. */
+void orc_chol_solve(int m, const double* L, double* y) {
+  for (int i = 0; i < m; i++) {
+    double t = y[i];
+    for (int k = 0; k < i; k++) t -= L[i + (int64_t)k * m] * y[k];
+    y[i] = t / L[i + (int64_t)i * m];
+  }
+  for (int i = m - 1; i >= 0; i--) {
+    double t = y[i];
+    for (int k = i + 1; k < m; k++) t -= L[k + (int64_t)i * m] * y[k];
+    y[i] = t / L[i + (int64_t)i * m];
+  }
+}
+
+/* Lanczos tridiagonal H_m from the CG coefficients (Section 4.1, Eq. 15 and Algorithm 3):
+ * delta[0..m-1] (diagonal), eta[0..m-2] (off-diagonal). */
+void orc_lanczos(int m, const double* alpha, const double* rho, double* delta, double* eta) {
+  for (int j = 0; j < m; j++) {
+    delta[j] = 1.0 / alpha[j];
+    if (j > 0) delta[j] += (rho[j] / rho[j - 1]) / alpha[j - 1];
+    if (j < m - 1) eta[j] = sqrt(rho[j + 1] / rho[j]) / alpha[j];
+  }
+}
+
+/* Cyclic Jacobi eigensolver for a dense symmetric m x m matrix S (column-major, destroyed).
+ * theta: eigenvalues sorted descending; Q (may be NULL): matching orthonormal eigenvectors
+ * (column-major).  A pair (p, q) is rotated while |s_pq| > eps sqrt(|s_pp s_qq|); the
+ * rotation annihilating s_pq is the textbook one, t = sign(tau)/(|tau| + sqrt(1 + tau^2)),
+ * tau = (s_qq - s_pp)/(2 s_pq). */
+int orc_sym_eig(int m, double* S, double* theta, double* Q) {
+  const double eps = 1.1102230246251565e-16;
+  double* V = (double*)calloc((size_t)m * m + 1, sizeof(double));
+  int* order = (int*)malloc(sizeof(int) * (size_t)(m + 1));
+  if (!V || !order) { free(V); free(order); return ORC_ERR_OOM; }
+  for (int i = 0; i < m; i++) V[i + (int64_t)i * m] = 1.0;
+  for (int sweep = 0; sweep < 100; sweep++) {
+    int rotated = 0;
+    for (int p = 0; p < m - 1; p++) {
+      for (int q = p + 1; q < m; q++) {
+        double apq = S[p + (int64_t)q * m];
+        double app = S[p + (int64_t)p * m], aqq = S[q + (int64_t)q * m];
+        if (!(fabs(apq) > eps * sqrt(fabs(app * aqq))) || apq == 0.0) continue;
+        rotated = 1;
+        double tau = (aqq - app) / (2.0 * apq);
+        double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        /* S <- J^T S J with J the rotation in the (p, q) plane */
+        for (int k = 0; k < m; k++) {
+          double skp = S[k + (int64_t)p * m], skq = S[k + (int64_t)q * m];
+          S[k + (int64_t)p * m] = c * skp - s * skq;
+          S[k + (int64_t)q * m] = s * skp + c * skq;
+        }
+        for (int k = 0; k < m; k++) {
+          double spk = S[p + (int64_t)k * m], sqk = S[q + (int64_t)k * m];
+          S[p + (int64_t)k * m] = c * spk - s * sqk;
+          S[q + (int64_t)k * m] = s * spk + c * sqk;
+        }
+        S[p + (int64_t)q * m] = 0.0;
+        S[q + (int64_t)p * m] = 0.0;
+        for (int k = 0; k < m; k++) {
+          double vkp = V[k + (int64_t)p * m], vkq = V[k + (int64_t)q * m];
+          V[k + (int64_t)p * m] = c * vkp - s * vkq;
+          V[k + (int64_t)q * m] = s * vkp + c * vkq;
+        }
+      }
+    }
+    if (!rotated) break;
+  }
+  /* selection sort by descending eigenvalue (stable for ties: lower index first) */
+  for (int i = 0; i < m; i++) order[i] = i;
+  for (int i = 0; i < m; i++) {
+    int best = i;
+    for (int k = i + 1; k < m; k++)
+      if (S[order[k] + (int64_t)order[k] * m] > S[order[best] + (int64_t)order[best] * m]) best = k;
+    int t = order[i]; order[i] = order[best]; order[best] = t;
+  }
+  for (int i = 0; i < m; i++) {
+    theta[i] = S[order[i] + (int64_t)order[i] * m];
+    if (Q) memcpy(Q + (int64_t)i * m, V + (int64_t)order[i] * m, sizeof(double) * (size_t)m);
+  }
+  free(V);
+  free(order);
+  return ORC_OK;
+}
+
+/* Eigen-decomposition of the symmetric tridiagonal (delta, eta) of order m. */
+int orc_tridiag_eig(int m, const double* delta, const double* eta, double* theta, double* Q) {
+  if (m <= 0) return ORC_OK;
+  double* S = (double*)calloc((size_t)m * m, sizeof(double));
+  if (!S) return ORC_ERR_OOM;
+  for (int j = 0; j < m; j++) {
+    S[j + (int64_t)j * m] = delta[j];
+    if (j < m - 1) { S[j + (int64_t)(j + 1) * m] = eta[j]; S[(j + 1) + (int64_t)j * m] = eta[j]; }
+  }
+  int st = orc_sym_eig(m, S, theta, Q);
+  free(S);
+  return st;
+}
+
+/* SRKS stagnation selection (Section 4.4, Eq. 16, Algorithm 3), then the optional
+ * theta < theta_frac * theta_max filter, then ascending-theta order, then at most `room`
+ * indices.  theta_m: m values (descending), theta_m1: m-1 values (descending).
+ * Writes 0-based indices into theta_m; returns their count. */
+int orc_srks_select(int m, const double* theta_m, const double* theta_m1, double eps,
+                    double theta_frac, int room, int32_t* out) {
+  if (m < 2 || room <= 0) return 0;
+  char* sel = (char*)calloc((size_t)m, 1);
+  if (!sel) return 0;
+  /* paper index j (1-based) -> array index j-1 */
+  for (int j = 1; j <= m - 1; j++) {
+    double a = theta_m[j - 1], b = theta_m1[j - 1];
+    if (fabs(a - b) <= eps * fabs(a)) sel[j - 1] = 1;
+    double c = theta_m[j];
+    if (fabs(c - b) <= eps * fabs(c)) sel[j] = 1;
+  }
+  if (theta_frac > 0.0) {
+    for (int i = 0; i < m; i++)
+      if (sel[i] && !(theta_m[i] < theta_frac * theta_m[0])) sel[i] = 0;
+  }
+  int cnt = 0;
+  for (int i = m - 1; i >= 0 && cnt < room; i--)  /* descending order -> ascending theta */
+    if (sel[i]) out[cnt++] = i;
+  free(sel);
+  return cnt;
+}
+
+/* ----------------------------------------------------------------------------------- */
+/* Sequence state                                                                       */
+/* ----------------------------------------------------------------------------------- */
+
+typedef struct {
+  int64_t n;
+  int nc, nc0;
+  double* C;    /* n x nc, column-major */
+  double* C0;   /* C^(0) for the restart mode */
+  /* last solve */
+  int m, cap_w;
+  double *W, *AW, *Z, *alpha, *rho, *gamma;
+  double *theta_m, *theta_m1, *Y;
+  int32_t* sel;
+  int n_sel;
+  orc_stats st;
+} orc_seq;
+
+orc_seq* orc_seq_create(int64_t n) {
+  orc_seq* s = (orc_seq*)calloc(1, sizeof(orc_seq));
+  if (s) s->n = n;
+  return s;
+}
+
+void orc_seq_destroy(orc_seq* s) {
+  if (!s) return;
+  free(s->C); free(s->C0); free(s->W); free(s->AW); free(s->Z);
+  free(s->alpha); free(s->rho); free(s->gamma);
+  free(s->theta_m); free(s->theta_m1); free(s->Y); free(s->sel);
+  free(s);
+}
+
+int orc_seq_nc(const orc_seq* s) { return s->nc; }
+int orc_seq_m(const orc_seq* s) { return s->m; }
+int orc_seq_nsel(const orc_seq* s) { return s->n_sel; }
+
+void orc_seq_get_C(const orc_seq* s, double* out) {
+  memcpy(out, s->C, sizeof(double) * (size_t)s->n * (size_t)s->nc);
+}
+
+/* Replace C (lock-step comparisons); with as_c0 != 0 it also becomes C^(0). */
+int orc_seq_set_C(orc_seq* s, int nc, const double* C, int as_c0) {
+  double* c = NULL;
+  if (nc > 0) {
+    c = (double*)malloc(sizeof(double) * (size_t)s->n * (size_t)nc);
+    if (!c) return ORC_ERR_OOM;
+    memcpy(c, C, sizeof(double) * (size_t)s->n * (size_t)nc);
+  }
+  free(s->C);
+  s->C = c;
+  s->nc = nc;
+  if (as_c0) {
+    free(s->C0);
+    s->C0 = NULL;
+    if (nc > 0) {
+      s->C0 = (double*)malloc(sizeof(double) * (size_t)s->n * (size_t)nc);
+      if (!s->C0) return ORC_ERR_OOM;
+      memcpy(s->C0, C, sizeof(double) * (size_t)s->n * (size_t)nc);
+    }
+    s->nc0 = nc;
+  }
+  return ORC_OK;
+}
+
+/* Accessors of the last solve (m columns / values). */
+void orc_seq_get_W(const orc_seq* s, double* out) { memcpy(out, s->W, sizeof(double) * (size_t)s->n * s->m); }
+void orc_seq_get_AW(const orc_seq* s, double* out) { memcpy(out, s->AW, sizeof(double) * (size_t)s->n * s->m); }
+void orc_seq_get_Z(const orc_seq* s, double* out) { memcpy(out, s->Z, sizeof(double) * (size_t)s->n * s->m); }
+void orc_seq_get_coeffs(const orc_seq* s, double* alpha, double* rho, double* gamma) {
+  memcpy(alpha, s->alpha, sizeof(double) * s->m);
+  memcpy(rho, s->rho, sizeof(double) * s->m);
+  memcpy(gamma, s->gamma, sizeof(double) * s->m);
+}
+void orc_seq_get_ritz(const orc_seq* s, double* theta_m, double* theta_m1, int32_t* sel, double* Y) {
+  if (s->m >= 1 && s->theta_m) memcpy(theta_m, s->theta_m, sizeof(double) * s->m);
+  if (s->m >= 2 && s->theta_m1) memcpy(theta_m1, s->theta_m1, sizeof(double) * (s->m - 1));
+  if (s->n_sel > 0) {
+    memcpy(sel, s->sel, sizeof(int32_t) * s->n_sel);
+    memcpy(Y, s->Y, sizeof(double) * (size_t)s->n * s->n_sel);
+  }
+}
+
+static int grow(orc_seq* s, int need) {
+  if (need <= s->cap_w) return ORC_OK;
+  int cap = s->cap_w ? s->cap_w : 64;
+  while (cap < need) cap *= 2;
+  size_t nb = sizeof(double) * (size_t)s->n * (size_t)cap;
+  double* W = (double*)realloc(s->W, nb);
+  if (W) s->W = W;
+  double* AW = (double*)realloc(s->AW, nb);
+  if (AW) s->AW = AW;
+  double* Z = (double*)realloc(s->Z, nb);
+  if (Z) s->Z = Z;
+  double* a = (double*)realloc(s->alpha, sizeof(double) * cap);
+  if (a) s->alpha = a;
+  double* r = (double*)realloc(s->rho, sizeof(double) * (cap + 1));
+  if (r) s->rho = r;
+  double* g = (double*)realloc(s->gamma, sizeof(double) * cap);
+  if (g) s->gamma = g;
+  if (!W || !AW || !Z || !a || !r || !g) return ORC_ERR_OOM;
+  s->cap_w = cap;
+  return ORC_OK;
+}
+
+/* z = P M^-1 r with P = I - C (C^T A C)^-1 C^T A, applied as u - C L^-T L^-1 (AC)^T u. */
+static void project(int64_t n, int nc, const double* C, const double* AC, const double* L,
+                    const double* u, double* z, double* t) {
+  for (int64_t i = 0; i < n; i++) z[i] = u[i];
+  if (nc == 0) return;
+  for (int c = 0; c < nc; c++) t[c] = dot(n, AC + (int64_t)c * n, u);
+  orc_chol_solve(nc, L, t);
+  for (int c = 0; c < nc; c++)
+    for (int64_t i = 0; i < n; i++) z[i] -= C[(int64_t)c * n + i] * t[c];
+}
+
+/* One solve of the sequence, APCG(A, M, C, b) (Algorithm 1 with full reorthogonalisation)
+ * followed by the recycling step of Algorithm 2 (TRKS) or Algorithm 3 (SRKS).
+ * x: output (zero initial guess, Section 2.1).  On any error C is left unchanged. */
+int orc_seq_solve(orc_seq* s, int nbr, const int32_t* rp, const int32_t* ci, const double* v,
+                  const double* b, double* x, double tol, const orc_policy* p, orc_stats* out) {
+  const int64_t n = s->n;
+  orc_stats st;
+  memset(&st, 0, sizeof(st));
+  st.n_c = s->nc;
+  s->m = 0;
+  s->n_sel = 0;
+  if (3 * (int64_t)nbr != n || !(tol >= 0.0) || p->max_iter < 1) {
+    st.status = ORC_ERR_INVALID_ARG;
+    if (out) *out = st;
+    return st.status;
+  }
+  const int nc = s->nc;
+  int status = ORC_OK;
+  double *minv = NULL, *AC = NULL, *L = NULL, *r = NULL, *u = NULL, *z = NULL, *t = NULL,
+         *g = NULL, *q = NULL, *res = NULL;
+  minv = (double*)malloc(sizeof(double) * 9 * (size_t)nbr);
+  r = (double*)malloc(sizeof(double) * n);
+  u = (double*)malloc(sizeof(double) * n);
+  z = (double*)malloc(sizeof(double) * n);
+  res = (double*)malloc(sizeof(double) * n);
+  t = (double*)malloc(sizeof(double) * (nc + 1));
+  if (!minv || !r || !u || !z || !res || !t) { status = ORC_ERR_OOM; goto done; }
+  status = orc_precond_setup(p->precond, nbr, rp, ci, v, minv);
+  if (status) goto done;
+  double bb = dot(n, b, b);
+  if (!isfinite(bb)) { status = ORC_ERR_INVALID_ARG; goto done; }
+  double stop2 = tol * tol * bb;
+
+  /* Algorithm 1, step 1: AC, C^T A C and its Cholesky factor. */
+  if (nc > 0) {
+    AC = (double*)malloc(sizeof(double) * (size_t)n * nc);
+    L = (double*)malloc(sizeof(double) * (size_t)nc * nc);
+    if (!AC || !L) { status = ORC_ERR_OOM; goto done; }
+    for (int c = 0; c < nc; c++) orc_spmv(nbr, rp, ci, v, s->C + (int64_t)c * n, AC + (int64_t)c * n);
+    for (int i = 0; i < nc; i++)
+      for (int j = 0; j < nc; j++) L[i + (int64_t)j * nc] = dot(n, s->C + (int64_t)i * n, AC + (int64_t)j * n);
+    status = orc_cholesky(nc, L);
+    if (status) goto done;
+  }
+  /* steps 2-3: x0 = C G^-1 C^T b, r0 = b - AC G^-1 C^T b (= P^T b) */
+  for (int64_t i = 0; i < n; i++) { x[i] = 0.0; r[i] = b[i]; }
+  if (nc > 0) {
+    for (int c = 0; c < nc; c++) t[c] = dot(n, s->C + (int64_t)c * n, b);
+    orc_chol_solve(nc, L, t);
+    for (int c = 0; c < nc; c++)
+      for (int64_t i = 0; i < n; i++) {
+        x[i] += s->C[(int64_t)c * n + i] * t[c];
+        r[i] -= AC[(int64_t)c * n + i] * t[c];
+      }
+  }
+  double rr = dot(n, r, r);
+  st.rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  if (rr <= stop2) goto converged;  /* m = 0 */
+
+  /* step 4: z0 = P M^-1 r0, w0 = z0 */
+  if ((status = grow(s, 1))) goto done;
+  orc_precond_apply(p->precond, nbr, minv, r, u);
+  project(n, nc, s->C, AC, L, u, z, t);
+  memcpy(s->Z, z, sizeof(double) * n);
+  memcpy(s->W, z, sizeof(double) * n);
+  s->rho[0] = dot(n, r, z);
+  if (!(s->rho[0] > 0.0)) { status = ORC_ERR_NOT_SPD; goto done; }
+
+  for (int j = 0;; j++) {
+    double* wj = s->W + (int64_t)j * n;
+    double* qj = s->AW + (int64_t)j * n;
+    orc_spmv(nbr, rp, ci, v, wj, qj);
+    double gam = dot(n, wj, qj);
+    if (!(gam > 0.0)) { status = ORC_ERR_NOT_SPD; goto done; }
+    double alpha = dot(n, r, wj) / gam;
+    s->gamma[j] = gam;
+    s->alpha[j] = alpha;
+    for (int64_t i = 0; i < n; i++) { x[i] += alpha * wj[i]; r[i] -= alpha * qj[i]; }
+    s->m = j + 1;
+    rr = dot(n, r, r);
+    st.rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    if (rr <= stop2) break;
+    if (j + 1 >= p->max_iter) { status = ORC_ERR_NO_CONVERGENCE; goto done; }
+    if ((status = grow(s, j + 2))) goto done;
+    /* z_{j+1} = P M^-1 r_{j+1}; rho_{j+1} = (r_{j+1}, z_{j+1}) */
+    orc_precond_apply(p->precond, nbr, minv, r, u);
+    project(n, nc, s->C, AC, L, u, z, t);
+    s->rho[j + 1] = dot(n, r, z);
+    if (!(s->rho[j + 1] > 0.0)) { status = ORC_ERR_NOT_SPD; goto done; }
+    memcpy(s->Z + (int64_t)(j + 1) * n, z, sizeof(double) * n);
+    /* w_{j+1} = z - sum_i ((A w_i, z)/(w_i, A w_i)) w_i, coefficients all from z */
+    int i0 = (p->reorth == ORC_REORTH_NONE) ? j : 0;
+    free(g);
+    g = (double*)malloc(sizeof(double) * (j + 1));
+    if (!g) { status = ORC_ERR_OOM; goto done; }
+    for (int i = i0; i <= j; i++) g[i] = dot(n, s->AW + (int64_t)i * n, z) / s->gamma[i];
+    double* wn = s->W + (int64_t)(j + 1) * n;
+    for (int64_t k = 0; k < n; k++) wn[k] = z[k];
+    for (int i = i0; i <= j; i++)
+      for (int64_t k = 0; k < n; k++) wn[k] -= g[i] * s->W[(int64_t)i * n + k];
+  }
+
+converged:
+  /* true residual */
+  orc_spmv(nbr, rp, ci, v, x, res);
+  {
+    double tr = 0.0;
+    for (int64_t i = 0; i < n; i++) { double d = b[i] - res[i]; tr += d * d; }
+    st.true_rel_res = bb > 0.0 ? sqrt(tr / bb) : 0.0;
+  }
+  st.m = s->m;
+
+  /* Recycling step. */
+  {
+    int cap = p->max_aug > 0 ? p->max_aug : 0x7fffffff;
+    int m = s->m;
+    int add = 0;
+    double* newcols = NULL;
+    if (p->recycle == ORC_RECYCLE_TRKS && m > 0) {
+      /* Algorithm 2: C^(k+1) = [C^(k), W_m] */
+      add = m;
+      if (p->cap_mode == ORC_CAP_TRUNCATE && nc + add > cap) add = cap - nc > 0 ? cap - nc : 0;
+      newcols = s->W;
+    } else if (p->recycle == ORC_RECYCLE_SRKS && m >= 2) {
+      /* Algorithm 3: Lanczos H_m, eigenpairs, eigenvalues of H_{m-1}, selection. */
+      double* delta = (double*)malloc(sizeof(double) * m);
+      double* eta = (double*)malloc(sizeof(double) * m);
+      double* Q = (double*)malloc(sizeof(double) * (size_t)m * m);
+      free(s->theta_m); free(s->theta_m1); free(s->sel); free(s->Y);
+      s->theta_m = (double*)malloc(sizeof(double) * m);
+      s->theta_m1 = (double*)malloc(sizeof(double) * m);
+      s->sel = (int32_t*)malloc(sizeof(int32_t) * m);
+      s->Y = NULL;
+      if (!delta || !eta || !Q || !s->theta_m || !s->theta_m1 || !s->sel) {
+        free(delta); free(eta); free(Q);
+        status = ORC_ERR_OOM; goto done;
+      }
+      orc_lanczos(m, s->alpha, s->rho, delta, eta);
+      status = orc_tridiag_eig(m, delta, eta, s->theta_m, Q);
+      if (!status) status = orc_tridiag_eig(m - 1, delta, eta, s->theta_m1, NULL);
+      if (status) { free(delta); free(eta); free(Q); goto done; }
+      int room = (p->cap_mode == ORC_CAP_TRUNCATE) ? (cap - nc) : m;
+      s->n_sel = orc_srks_select(m, s->theta_m, s->theta_m1, p->ritz_eps, p->theta_frac, room, s->sel);
+      add = s->n_sel;
+      if (add > 0) {
+        /* y^s = V q^s / sqrt|theta^s|, V = [(-1)^j z_j / sqrt(rho_j)] (Section 4.1) */
+        s->Y = (double*)calloc((size_t)n * add, sizeof(double));
+        if (!s->Y) { free(delta); free(eta); free(Q); status = ORC_ERR_OOM; goto done; }
+        for (int c = 0; c < add; c++) {
+          int idx = s->sel[c];
+          double sc = 1.0 / sqrt(fabs(s->theta_m[idx]));
+          double* y = s->Y + (int64_t)c * n;
+          for (int j = 0; j < m; j++) {
+            double f = ((j & 1) ? -1.0 : 1.0) / sqrt(s->rho[j]) * Q[j + (int64_t)idx * m];
+            for (int64_t i = 0; i < n; i++) y[i] += s->Z[(int64_t)j * n + i] * f;
+          }
+          for (int64_t i = 0; i < n; i++) y[i] *= sc;
+        }
+      }
+      newcols = s->Y;
+      free(delta); free(eta); free(Q);
+    }
+    st.n_selected = add;
+    if (add > 0) {
+      double* C = (double*)realloc(s->C, sizeof(double) * (size_t)n * (size_t)(nc + add));
+      if (!C) { status = ORC_ERR_OOM; goto done; }
+      s->C = C;
+      memcpy(s->C + (int64_t)nc * n, newcols, sizeof(double) * (size_t)n * add);
+      s->nc = nc + add;
+    }
+    if (p->cap_mode == ORC_CAP_RESTART && p->max_aug > 0 && s->nc >= p->max_aug) {
+      /* Algorithm 3, last step: back to C^(0) */
+      orc_seq_set_C(s, s->nc0, s->C0, 0);
+    }
+    st.n_c_after = s->nc;
+  }
+
+done:
+  if (status) st.m = s->m;
+  st.status = status;
+  if (out) *out = st;
+  free(minv); free(AC); free(L); free(r); free(u); free(z); free(t); free(g); free(q); free(res);
+  return status;
+}
