@@ -1,0 +1,502 @@
+// krs_apcg.cu -- the APCG iteration on the GPU (Algorithm 1 with full
+// reorthogonalisation), in two execution modes that share every arithmetic routine:
+//   * persistent: one cooperative kernel runs the whole iteration loop of a solve; the
+//     phases are separated by bounded grid barriers;
+//   * kernels:    one kernel launch per phase (the launch boundary is the barrier).
+// Both use the same CTA partition and the same reduction order, so they produce the same
+// bits.
+//
+// One iteration j (literal order of Algorithm 1 with the readings: z_j = P M^-1 r_j, the
+// Gram-Schmidt beta computed before use, classical Gram-Schmidt over all stored
+// directions):
+//   P1  q = A w_j (stored as AW[:, j]); partials (w_j, q), (r_j, w_j)
+//   P2  gamma_j, alpha_j = (r_j, w_j)/gamma_j; x += alpha w_j; r -= alpha q; (r, r);
+//       u = M^-1 r; partials t = (AC)^T u
+//   P3  convergence ||r||^2 <= tol^2 ||b||^2; slice of t reduced
+//   P4  slice of s = (C^T A C)^-1 t
+//   P5  z = u - C s (stored as Z[:, j+1]); partials (r, z), g = (AW)^T z
+//   P6  rho_{j+1} = (r, z); slice of g_i / gamma_i
+//   P7  w_{j+1} = z - W g (stored as W[:, j+1])
+// The projection P u = u - C (C^T A C)^-1 (AC)^T u is the projector of Eq. 5; its two
+// block products and the coarse solve are the items of Section 2.3.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "krs_device.cuh"
+#include "krs_internal.h"
+
+namespace krs {
+
+struct ApcgCtx {
+  int64_t n, ld;       // order, leading dimension of multi-vectors and vector padding
+  int nbr, npc, P;     // block rows, nodes per CTA, CTAs
+  int nc, ldg;         // columns of C, leading dimension of Ginv
+  int max_iter, reorth_full, precond;
+  int j0;              // first iteration of this launch (persistent mode)
+  double tol2;         // tol^2 * ||b||^2
+  long long spin_limit;
+  const int* rp;
+  const int* ci;
+  const double* vals;
+  const double* minv;
+  const double* C;
+  const double* AC;
+  const double* Ginv;
+  double* W;
+  double* AW;
+  double* Z;
+  double* x;
+  double* r;
+  double* u;
+  double* alpha;
+  double* gamma;
+  double* rho;
+  double* tfull;
+  double* sfull;
+  double* gfull;
+  double* part;        // [P * PS_STRIDE]
+  double* vpart;       // [P * vld]
+  int64_t vld;
+  int* ctrl;
+  unsigned long long* bar;
+};
+
+// shared-memory layout (doubles): su[ROW_CHUNK] | red[4*TPB] | sv[kmax]
+struct Smem {
+  double* su;
+  double* red;
+  double* sv;
+};
+
+__device__ __forceinline__ Smem smem_layout(double* base) {
+  Smem s;
+  s.su = base;
+  s.red = base + ROW_CHUNK;
+  s.sv = base + ROW_CHUNK + 4 * TPB;
+  return s;
+}
+
+enum PhaseResult { PH_CONTINUE = 0, PH_STOP = 1 };
+
+__device__ __forceinline__ void finish(const ApcgCtx& c, int status, int m) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (status) atomicCAS(c.ctrl + CTRL_STATUS, 0, status);
+    c.ctrl[CTRL_M] = m;
+    c.ctrl[CTRL_DONE] = 1;
+  }
+}
+
+// Reduce a scalar partial over all CTAs (warp 0, fixed order) and broadcast it.
+__device__ __forceinline__ double grid_scalar(const ApcgCtx& c, int slot, double* red) {
+  if (threadIdx.x < 32) {
+    double v = warp_sum_strided(c.part + slot, c.P, PS_STRIDE);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  double v = red[0];
+  __syncthreads();
+  return v;
+}
+
+__device__ __forceinline__ void phase1(const ApcgCtx& c, int j, Smem& sm) {
+  int64_t r0, r1;
+  cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
+  const double* w = c.W + (int64_t)j * c.ld;
+  double* q = c.AW + (int64_t)j * c.ld;
+  double wq = 0.0, rw = 0.0;
+  cta_spmv(c.rp, c.ci, c.vals, w, q, c.r, r0, r1, wq, rw);
+  block_sum2(wq, rw, sm.red);
+  if (threadIdx.x == 0) {
+    c.part[blockIdx.x * PS_STRIDE + PS_WQ] = wq;
+    c.part[blockIdx.x * PS_STRIDE + PS_RW] = rw;
+  }
+}
+
+__device__ __forceinline__ int phase2(const ApcgCtx& c, int j, Smem& sm) {
+  const double gam = grid_scalar(c, PS_WQ, sm.red);
+  const double rws = grid_scalar(c, PS_RW, sm.red);
+  if (!(gam > 0.0)) {
+    finish(c, 2 /* KRS_ERR_NOT_SPD */, j);
+    return PH_STOP;
+  }
+  const double al = rws / gam;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c.alpha[j] = al;
+    c.gamma[j] = gam;
+  }
+  int64_t r0, r1;
+  cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
+  const double* w = c.W + (int64_t)j * c.ld;
+  const double* q = c.AW + (int64_t)j * c.ld;
+  double rr = 0.0;
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
+    c.x[row] += al * w[row];
+    const double rn = c.r[row] - al * q[row];
+    c.r[row] = rn;
+    rr += rn * rn;
+  }
+  __syncthreads();
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB)
+    c.u[row] = precond_row(c.precond, c.minv, c.r, row);
+  rr = block_sum(rr, sm.red);
+  if (threadIdx.x == 0) c.part[blockIdx.x * PS_STRIDE + PS_RR] = rr;
+  if (c.nc > 0) cta_gemv_t<true>(c.AC, c.ld, c.nc, c.u, r0, r1, c.vpart + blockIdx.x * c.vld, sm.su, sm.red);
+  return PH_CONTINUE;
+}
+
+// Slice [a, b) of the k reduced columns owned by this CTA.
+__device__ __forceinline__ void col_slice(int k, int P, int b, int& a, int& e) {
+  const int per = (k + P - 1) / P;
+  a = min(k, b * per);
+  e = min(k, a + per);
+}
+
+__device__ __forceinline__ int phase3(const ApcgCtx& c, int j, Smem& sm) {
+  const double rr = grid_scalar(c, PS_RR, sm.red);
+  if (rr <= c.tol2) {
+    finish(c, 0, j + 1);
+    return PH_STOP;
+  }
+  if (j + 1 >= c.max_iter) {
+    finish(c, 3 /* KRS_ERR_NO_CONVERGENCE */, j + 1);
+    return PH_STOP;
+  }
+  if (c.nc > 0) {
+    int a, e;
+    col_slice(c.nc, c.P, blockIdx.x, a, e);
+    const int warp = threadIdx.x >> 5;
+    for (int col = a + warp; col < e; col += TPB / 32) {
+      const double v = warp_sum_strided(c.vpart + col, c.P, c.vld);
+      if ((threadIdx.x & 31) == 0) c.tfull[col] = v;
+    }
+  }
+  return PH_CONTINUE;
+}
+
+__device__ __forceinline__ void phase4(const ApcgCtx& c) {
+  int a, e;
+  col_slice(c.nc, c.P, blockIdx.x, a, e);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int col = a + warp; col < e; col += TPB / 32) {
+    const double* g = c.Ginv + (int64_t)col * c.ldg;
+    double s = 0.0;
+    for (int k = lane; k < c.nc; k += 32) s += g[k] * c.tfull[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) c.sfull[col] = s;
+  }
+}
+
+__device__ __forceinline__ void phase5(const ApcgCtx& c, int j, Smem& sm) {
+  int64_t r0, r1;
+  cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
+  double* z = c.Z + (int64_t)(j + 1) * c.ld;
+  if (c.nc > 0) {
+    for (int k = threadIdx.x; k < c.nc; k += TPB) sm.sv[k] = c.sfull[k];
+    __syncthreads();
+    cta_gemv_n<true>(c.C, c.ld, c.nc, sm.sv, -1.0, c.u, z, r0, r1, sm.red);
+  } else {
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) z[row] = c.u[row];
+    __syncthreads();
+  }
+  double rz = 0.0;
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) rz += c.r[row] * z[row];
+  rz = block_sum(rz, sm.red);
+  if (threadIdx.x == 0) c.part[blockIdx.x * PS_STRIDE + PS_RZ] = rz;
+  const int base = c.reorth_full ? 0 : j;
+  const int kk = j + 1 - base;
+  cta_gemv_t<false>(c.AW + (int64_t)base * c.ld, c.ld, kk, z, r0, r1, c.vpart + blockIdx.x * c.vld,
+                    sm.su, sm.red);
+}
+
+__device__ __forceinline__ int phase6(const ApcgCtx& c, int j, Smem& sm) {
+  const double rz = grid_scalar(c, PS_RZ, sm.red);
+  if (!(rz > 0.0)) {
+    finish(c, 2 /* KRS_ERR_NOT_SPD */, j + 1);
+    return PH_STOP;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) c.rho[j + 1] = rz;
+  const int base = c.reorth_full ? 0 : j;
+  const int kk = j + 1 - base;
+  int a, e;
+  col_slice(kk, c.P, blockIdx.x, a, e);
+  const int warp = threadIdx.x >> 5;
+  for (int col = a + warp; col < e; col += TPB / 32) {
+    const double v = warp_sum_strided(c.vpart + col, c.P, c.vld);
+    if ((threadIdx.x & 31) == 0) c.gfull[col] = v / c.gamma[base + col];
+  }
+  return PH_CONTINUE;
+}
+
+__device__ __forceinline__ void phase7(const ApcgCtx& c, int j, Smem& sm) {
+  int64_t r0, r1;
+  cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
+  const int base = c.reorth_full ? 0 : j;
+  const int kk = j + 1 - base;
+  for (int k = threadIdx.x; k < kk; k += TPB) sm.sv[k] = c.gfull[k];
+  __syncthreads();
+  const double* z = c.Z + (int64_t)(j + 1) * c.ld;
+  double* wn = c.W + (int64_t)(j + 1) * c.ld;
+  cta_gemv_n<false>(c.W + (int64_t)base * c.ld, c.ld, kk, sm.sv, -1.0, z, wn, r0, r1, sm.red);
+}
+
+// ------------------------------------------------------------------------------------
+// persistent kernel: the whole iteration loop of one solve
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx c) {
+  extern __shared__ double4_32a smem_raw4[];
+  Smem sm = smem_layout(reinterpret_cast<double*>(smem_raw4));
+  unsigned long long target = 0;
+  const int TO = 6;  // KRS_ERR_TIMEOUT
+#define KRS_SYNC()                                                                   \
+  do {                                                                               \
+    if (!grid_barrier(c.bar, target, (unsigned)c.P, c.ctrl, c.spin_limit, TO)) return; \
+  } while (0)
+  for (int j = c.j0;; j++) {
+    phase1(c, j, sm);
+    KRS_SYNC();
+    if (phase2(c, j, sm) == PH_STOP) return;
+    KRS_SYNC();
+    if (phase3(c, j, sm) == PH_STOP) return;
+    if (c.nc > 0) {
+      KRS_SYNC();
+      phase4(c);
+    }
+    KRS_SYNC();
+    phase5(c, j, sm);
+    KRS_SYNC();
+    if (phase6(c, j, sm) == PH_STOP) return;
+    KRS_SYNC();
+    phase7(c, j, sm);
+    KRS_SYNC();
+  }
+#undef KRS_SYNC
+}
+
+// ------------------------------------------------------------------------------------
+// per-phase kernels (kernels mode).  Each returns at once when the solve has ended.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ bool ended(const ApcgCtx& c) {
+  return *((volatile int*)(c.ctrl + CTRL_DONE)) != 0;
+}
+
+#define KRS_PHASE_KERNEL(NAME, BODY)                                          \
+  __global__ void __launch_bounds__(TPB, 1) NAME(ApcgCtx c, int j) {         \
+    extern __shared__ double4_32a smem_raw4[];                                    \
+    Smem sm = smem_layout(reinterpret_cast<double*>(smem_raw4));              \
+    if (ended(c)) return;                                                     \
+    (void)sm;                                                                 \
+    BODY;                                                                     \
+  }
+
+KRS_PHASE_KERNEL(k_phase1, phase1(c, j, sm))
+KRS_PHASE_KERNEL(k_phase2, phase2(c, j, sm))
+KRS_PHASE_KERNEL(k_phase3, phase3(c, j, sm))
+KRS_PHASE_KERNEL(k_phase4, phase4(c))
+KRS_PHASE_KERNEL(k_phase5, phase5(c, j, sm))
+KRS_PHASE_KERNEL(k_phase6, phase6(c, j, sm))
+KRS_PHASE_KERNEL(k_phase7, phase7(c, j, sm))
+
+// ------------------------------------------------------------------------------------
+// set-up: x_0, r_0 = P^T b, z_0 = P M^-1 r_0, w_0 = z_0, rho_0 (Algorithm 1, steps 1-3)
+// ------------------------------------------------------------------------------------
+
+// partial t = V^T y over the CTA's rows (y global)
+__global__ void __launch_bounds__(TPB, 1) k_gemv_t_part(const double* V, int64_t ld, int k, const double* y,
+                                                        int nbr, int npc, double* vpart, int64_t vld) {
+  extern __shared__ double4_32a smem_raw4[];
+  Smem sm = smem_layout(reinterpret_cast<double*>(smem_raw4));
+  int64_t r0, r1;
+  cta_rows(nbr, npc, blockIdx.x, r0, r1);
+  cta_gemv_t<false>(V, ld, k, y, r0, r1, vpart + blockIdx.x * vld, sm.su, sm.red);
+}
+
+// out[c] = sum_b vpart[b*vld + c]  (c < k), then (optional) s = Ginv * out
+__global__ void k_reduce_cols(const double* vpart, int64_t vld, int P, int k, double* out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= k) return;
+  const double v = warp_sum_strided(vpart + warp, P, vld);
+  if ((threadIdx.x & 31) == 0) out[warp] = v;
+}
+
+__global__ void k_small_gemv(const double* G, int ldg, int k, const double* t, double* s) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= k) return;
+  const double* g = G + (int64_t)warp * ldg;
+  double a = 0.0;
+  for (int i = lane; i < k; i += 32) a += g[i] * t[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) s[warp] = a;
+}
+
+// x = C s, r = b - AC s (or x = 0, r = b when k == 0); partials (b, b) and (r, r)
+__global__ void __launch_bounds__(TPB, 1) k_init_xr(const double* C, const double* AC, int64_t ld, int k,
+                                                    const double* s, const double* b, double* x, double* r,
+                                                    int nbr, int npc, double* part) {
+  extern __shared__ double4_32a smem_raw4[];
+  Smem sm = smem_layout(reinterpret_cast<double*>(smem_raw4));
+  int64_t r0, r1;
+  cta_rows(nbr, npc, blockIdx.x, r0, r1);
+  if (k > 0) {
+    for (int i = threadIdx.x; i < k; i += TPB) sm.sv[i] = s[i];
+    __syncthreads();
+    cta_gemv_n<false>(C, ld, k, sm.sv, 1.0, nullptr, x, r0, r1, sm.red);
+    cta_gemv_n<false>(AC, ld, k, sm.sv, -1.0, b, r, r0, r1, sm.red);
+  } else {
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
+      x[row] = 0.0;
+      r[row] = b[row];
+    }
+    __syncthreads();
+  }
+  double bb = 0.0, rr = 0.0;
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
+    bb += b[row] * b[row];
+    rr += r[row] * r[row];
+  }
+  block_sum2(bb, rr, sm.red);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x * PS_STRIDE + 0] = bb;
+    part[blockIdx.x * PS_STRIDE + 1] = rr;
+  }
+}
+
+// u = M^-1 r
+__global__ void k_precond_rows(int kind, const double* minv, const double* r, double* u, int64_t n) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row < n) u[row] = precond_row(kind, minv, r, row);
+}
+
+// z0 = u - C s (or u), W[:,0] = Z[:,0] = z0, partial (r, z0)
+__global__ void __launch_bounds__(TPB, 1) k_init_z(const double* C, int64_t ld, int k, const double* s,
+                                                   const double* u, const double* r, double* Z, double* W,
+                                                   int nbr, int npc, double* part) {
+  extern __shared__ double4_32a smem_raw4[];
+  Smem sm = smem_layout(reinterpret_cast<double*>(smem_raw4));
+  int64_t r0, r1;
+  cta_rows(nbr, npc, blockIdx.x, r0, r1);
+  if (k > 0) {
+    for (int i = threadIdx.x; i < k; i += TPB) sm.sv[i] = s[i];
+    __syncthreads();
+    cta_gemv_n<false>(C, ld, k, sm.sv, -1.0, u, Z, r0, r1, sm.red);
+  } else {
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) Z[row] = u[row];
+    __syncthreads();
+  }
+  double rz = 0.0;
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
+    W[row] = Z[row];
+    rz += r[row] * Z[row];
+  }
+  rz = block_sum(rz, sm.red);
+  if (threadIdx.x == 0) part[blockIdx.x * PS_STRIDE + 2] = rz;
+}
+
+// scal[0] = bb, scal[1] = rr0, rho[0] = rho0 (all from partial slots 0, 1, 2)
+__global__ void k_init_finish(const double* part, int P, double* scal, double* rho) {
+  const int warp = threadIdx.x >> 5;
+  if (warp < 3) {
+    const double v = warp_sum_strided(part + warp, P, PS_STRIDE);
+    if ((threadIdx.x & 31) == 0) {
+      if (warp < 2) scal[warp] = v;
+      else rho[0] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// host launchers
+// ------------------------------------------------------------------------------------
+size_t apcg_smem_bytes(int kmax) {
+  return sizeof(double) * (size_t)(ROW_CHUNK + 4 * TPB + ((kmax + 3) & ~3));
+}
+
+static ApcgCtx make_ctx(const IterArgs& a) {
+  ApcgCtx c;
+  c.n = a.n; c.ld = a.ld; c.nbr = a.nbr; c.npc = a.npc; c.P = a.P;
+  c.nc = a.nc; c.ldg = a.ldg; c.max_iter = a.max_iter; c.reorth_full = a.reorth_full;
+  c.precond = a.precond; c.j0 = 0; c.tol2 = a.tol2; c.spin_limit = a.spin_limit;
+  c.rp = a.rp; c.ci = a.ci; c.vals = a.vals; c.minv = a.minv;
+  c.C = a.C; c.AC = a.AC; c.Ginv = a.Ginv;
+  c.W = a.W; c.AW = a.AW; c.Z = a.Z; c.x = a.x; c.r = a.r; c.u = a.u;
+  c.alpha = a.alpha; c.gamma = a.gamma; c.rho = a.rho;
+  c.tfull = a.tfull; c.sfull = a.sfull; c.gfull = a.gfull;
+  c.part = a.part; c.vpart = a.vpart; c.vld = a.vld; c.ctrl = a.ctrl; c.bar = a.bar;
+  return c;
+}
+
+cudaError_t apcg_prepare_attributes(int kmax) {
+  const size_t sm = apcg_smem_bytes(kmax);
+  cudaError_t e = cudaSuccess;
+  const void* fns[] = {(const void*)k_apcg_persistent, (const void*)k_phase1, (const void*)k_phase2,
+                       (const void*)k_phase3, (const void*)k_phase4, (const void*)k_phase5,
+                       (const void*)k_phase6, (const void*)k_phase7, (const void*)k_gemv_t_part,
+                       (const void*)k_init_xr, (const void*)k_init_z};
+  for (const void* f : fns) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  return e;
+}
+
+cudaError_t apcg_max_coresident(int kmax, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_apcg_persistent, TPB,
+                                                       apcg_smem_bytes(kmax));
+}
+
+// Set-up of x_0, r_0, z_0, w_0, rho_0, ||b||^2, ||r_0||^2 (scal[0..1]).  Counts launches.
+cudaError_t apcg_launch_init(const IterArgs& a, const double* b, double* scal, cudaStream_t st,
+                             int64_t* launches) {
+  const size_t sm = apcg_smem_bytes(a.kmax);
+  const int k = a.nc;
+  if (k > 0) {
+    k_gemv_t_part<<<a.P, TPB, sm, st>>>(a.C, a.ld, k, b, a.nbr, a.npc, a.vpart, a.vld);
+    k_reduce_cols<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.vpart, a.vld, a.P, k, a.tfull);
+    k_small_gemv<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.Ginv, a.ldg, k, a.tfull, a.sfull);
+    *launches += 3;
+  }
+  k_init_xr<<<a.P, TPB, sm, st>>>(a.C, a.AC, a.ld, k, a.sfull, b, a.x, a.r, a.nbr, a.npc, a.part);
+  k_precond_rows<<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a.precond, a.minv, a.r, a.u, a.n);
+  *launches += 2;
+  if (k > 0) {
+    k_gemv_t_part<<<a.P, TPB, sm, st>>>(a.AC, a.ld, k, a.u, a.nbr, a.npc, a.vpart, a.vld);
+    k_reduce_cols<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.vpart, a.vld, a.P, k, a.tfull);
+    k_small_gemv<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.Ginv, a.ldg, k, a.tfull, a.sfull);
+    *launches += 3;
+  }
+  k_init_z<<<a.P, TPB, sm, st>>>(a.C, a.ld, k, a.sfull, a.u, a.r, a.Z, a.W, a.nbr, a.npc, a.part);
+  k_init_finish<<<1, 96, 0, st>>>(a.part, a.P, scal, a.rho);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t apcg_launch_persistent(const IterArgs& a, cudaStream_t st, int64_t* launches) {
+  ApcgCtx c = make_ctx(a);
+  void* args[] = {&c};
+  *launches += 1;
+  return cudaLaunchCooperativeKernel((const void*)k_apcg_persistent, dim3(a.P), dim3(TPB), args,
+                                     apcg_smem_bytes(a.kmax), st);
+}
+
+// Launch the phases of iterations [j0, j1) (kernels mode).
+cudaError_t apcg_launch_phases(const IterArgs& a, int j0, int j1, cudaStream_t st, int64_t* launches) {
+  ApcgCtx c = make_ctx(a);
+  const size_t sm = apcg_smem_bytes(a.kmax);
+  for (int j = j0; j < j1; j++) {
+    k_phase1<<<a.P, TPB, sm, st>>>(c, j);
+    k_phase2<<<a.P, TPB, sm, st>>>(c, j);
+    k_phase3<<<a.P, TPB, sm, st>>>(c, j);
+    if (a.nc > 0) {
+      k_phase4<<<a.P, TPB, sm, st>>>(c, j);
+      *launches += 1;
+    }
+    k_phase5<<<a.P, TPB, sm, st>>>(c, j);
+    k_phase6<<<a.P, TPB, sm, st>>>(c, j);
+    k_phase7<<<a.P, TPB, sm, st>>>(c, j);
+    *launches += 6;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace krs

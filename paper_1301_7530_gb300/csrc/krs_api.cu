@@ -1,0 +1,932 @@
+// krs_api.cu -- the C ABI (include/krs.h): sequence state, device memory, and the
+// orchestration of one solve of the sequence:
+//   set-up  : upload A if its version changed, preconditioner, A C (new columns only
+//             while A is unchanged), C^T A C (new tiles only while A is unchanged), its
+//             Cholesky factor and inverse (Algorithm 1 step 1; Section 2.3);
+//   init    : x_0, r_0, z_0, w_0 (Algorithm 1 steps 2-3);
+//   iterate : the persistent kernel or the per-phase kernels (krs_apcg.cu);
+//   recycle : TRKS (Algorithm 2) or SRKS (Algorithm 3) on the device.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "krs.h"
+#include "krs_device.cuh"
+#include "krs_internal.h"
+
+using namespace krs;
+
+namespace krs {
+cudaError_t launch_tridiag_eigvals2(int m, int m1, const double* delta, const double* eta, double* theta_m,
+                                    double* theta_m1, cudaStream_t st);
+}
+
+static thread_local std::string g_last_error;
+
+static krs_status fail(krs_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+static krs_status fail(krs_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define KRS_CUDA(call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      return fail(KRS_ERR_CUDA, "%s failed: %s (line %d)", #call, cudaGetErrorString(e_), \
+                  __LINE__);                                                               \
+    }                                                                                      \
+  } while (0)
+
+#define KRS_TRY(expr)                  \
+  do {                                 \
+    krs_status s_ = (expr);            \
+    if (s_ != KRS_OK) return s_;       \
+  } while (0)
+
+static const long long kDefaultSpin = 1ll << 24;
+static const int kMinNodesPerCta = 16;
+
+struct krs_seq {
+  int64_t n = 0, ld = 0;
+  int nbr = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* (*ualloc)(size_t, void*) = nullptr;
+  void (*ufree)(void*, void*) = nullptr;
+  void* uctx = nullptr;
+  int sms = 0;
+  std::vector<void*> allocs;
+
+  // matrix
+  int32_t* rp = nullptr;
+  int32_t* ci = nullptr;
+  double* vals = nullptr;
+  int64_t nnzb_cap = 0;
+  const int32_t* rp_use = nullptr;
+  const int32_t* ci_use = nullptr;
+  const double* vals_use = nullptr;
+  bool A_valid = false;
+  uint64_t A_version = 0;
+  int precond_built = -1;
+  double* minv = nullptr;
+
+  // augmentation space
+  int nc = 0, cap_c = 0;
+  double* C = nullptr;
+  double* AC = nullptr;
+  int ac_valid = 0;   // columns of AC valid for the current A
+  int g_valid = 0;    // leading columns of G valid
+  bool ginv_valid = false;
+  double* G = nullptr;
+  double* Lw = nullptr;
+  double* Ginv = nullptr;
+  int nc0 = 0;
+  double* C0 = nullptr;
+
+  // Krylov storage and vectors
+  int cap_w = 0;
+  double *W = nullptr, *AW = nullptr, *Z = nullptr;
+  double *x = nullptr, *r = nullptr, *u = nullptr, *b = nullptr, *tmp = nullptr;
+
+  // scalars, partials, control
+  double *alpha = nullptr, *gamma = nullptr, *rho = nullptr;
+  double *tfull = nullptr, *sfull = nullptr, *gfull = nullptr;
+  double* part = nullptr;
+  double* vpart = nullptr;
+  int64_t vld = 0;
+  int vpart_P = 0;
+  int* ctrl = nullptr;
+  unsigned long long* bar = nullptr;
+  double* scal = nullptr;  // [0] bb, [1] rr0, [2] true residual^2
+
+  // eigen / Ritz scratch (sized by cap_w)
+  double *delta = nullptr, *eta = nullptr, *theta_m = nullptr, *theta_m1 = nullptr, *tsel = nullptr;
+  int* sel = nullptr;
+  int* selcount = nullptr;
+  double *Qsel = nullptr, *F = nullptr, *eigwork = nullptr;
+  int eig_cap = 0;
+
+  // Gram scratch
+  double* gram_scratch = nullptr;
+  size_t gram_cap = 0;
+
+  // pinned host mirrors
+  double* h_scal = nullptr;
+  int* h_ctrl = nullptr;
+
+  // last solve
+  krs_solve_stats st{};
+  int last_m = 0;
+  int last_srks = 0;
+  int last_nsel = 0;
+  long long spin_limit = kDefaultSpin;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+// ------------------------------------------------------------------------------------
+// memory helpers
+// ------------------------------------------------------------------------------------
+static krs_status dev_alloc(krs_seq* s, size_t bytes, void** out) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (s->ualloc) {
+    p = s->ualloc(bytes, s->uctx);
+    if (!p) return fail(KRS_ERR_OOM, "allocator returned NULL for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(e == cudaErrorMemoryAllocation ? KRS_ERR_OOM : KRS_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                  cudaGetErrorString(e));
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(p, 0, bytes, s->stream);
+  if (e != cudaSuccess) return fail(KRS_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  s->allocs.push_back(p);
+  *out = p;
+  return KRS_OK;
+}
+
+static void dev_free(krs_seq* s, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < s->allocs.size(); i++) {
+    if (s->allocs[i] == p) {
+      s->allocs[i] = s->allocs.back();
+      s->allocs.pop_back();
+      break;
+    }
+  }
+  if (s->ufree) {
+    cudaStreamSynchronize(s->stream);
+    s->ufree(p, s->uctx);
+  } else {
+    cudaFree(p);
+  }
+}
+
+template <typename T>
+static krs_status alloc_n(krs_seq* s, T** p, size_t count) {
+  void* v = nullptr;
+  KRS_TRY(dev_alloc(s, count * sizeof(T), &v));
+  *p = static_cast<T*>(v);
+  return KRS_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// grow C / AC (and C^T A C work) to hold `need` columns, keeping the first nc columns
+static krs_status ensure_cap_c(krs_seq* s, int need) {
+  if (need <= s->cap_c) return KRS_OK;
+  int cap = s->cap_c ? s->cap_c : 16;
+  while (cap < need) cap *= 2;
+  double *C = nullptr, *AC = nullptr, *G = nullptr, *Lw = nullptr, *Gi = nullptr;
+  KRS_TRY(alloc_n(s, &C, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &AC, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &G, (size_t)cap * cap));
+  KRS_TRY(alloc_n(s, &Lw, (size_t)2 * cap * cap));
+  KRS_TRY(alloc_n(s, &Gi, (size_t)cap * cap));
+  if (s->nc > 0) {
+    KRS_CUDA(cudaMemcpyAsync(C, s->C, sizeof(double) * (size_t)s->nc * s->ld, cudaMemcpyDeviceToDevice, s->stream));
+    if (s->ac_valid > 0)
+      KRS_CUDA(cudaMemcpyAsync(AC, s->AC, sizeof(double) * (size_t)s->ac_valid * s->ld, cudaMemcpyDeviceToDevice,
+                               s->stream));
+  }
+  if (s->g_valid > 0 && s->G)  // keep the valid leading block of C^T A C (new leading dimension)
+    KRS_CUDA(cudaMemcpy2DAsync(G, sizeof(double) * cap, s->G, sizeof(double) * s->cap_c, sizeof(double) * s->g_valid,
+                               s->g_valid, cudaMemcpyDeviceToDevice, s->stream));
+  dev_free(s, s->C);  // cudaFree / the stream sync in dev_free orders it after the copies
+  dev_free(s, s->AC);
+  dev_free(s, s->G);
+  dev_free(s, s->Lw);
+  dev_free(s, s->Ginv);
+  s->C = C;
+  s->AC = AC;
+  s->G = G;
+  s->Lw = Lw;
+  s->Ginv = Gi;
+  s->cap_c = cap;
+  s->ginv_valid = false;
+  return KRS_OK;
+}
+
+// direction storage and everything sized by the iteration limit
+static krs_status ensure_cap_w(krs_seq* s, int max_iter) {
+  const int need = max_iter + 1;
+  if (need <= s->cap_w) return KRS_OK;
+  int cap = (int)round_up(need, 32);
+  dev_free(s, s->W);
+  dev_free(s, s->AW);
+  dev_free(s, s->Z);
+  dev_free(s, s->alpha);
+  dev_free(s, s->gamma);
+  dev_free(s, s->rho);
+  dev_free(s, s->gfull);
+  s->W = s->AW = s->Z = nullptr;
+  KRS_TRY(alloc_n(s, &s->W, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &s->AW, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &s->Z, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &s->alpha, cap));
+  KRS_TRY(alloc_n(s, &s->gamma, cap));
+  KRS_TRY(alloc_n(s, &s->rho, cap + 1));
+  KRS_TRY(alloc_n(s, &s->gfull, cap));
+  s->cap_w = cap;
+  return KRS_OK;
+}
+
+static krs_status ensure_vpart(krs_seq* s, int P, int kmax) {
+  const int64_t vld = round_up(kmax + 1, 32);
+  if (P <= s->vpart_P && vld <= s->vld) return KRS_OK;
+  const int Pn = P > s->vpart_P ? P : s->vpart_P;
+  const int64_t vn = vld > s->vld ? vld : s->vld;
+  dev_free(s, s->vpart);
+  dev_free(s, s->part);
+  dev_free(s, s->tfull);
+  dev_free(s, s->sfull);
+  KRS_TRY(alloc_n(s, &s->vpart, (size_t)Pn * vn));
+  KRS_TRY(alloc_n(s, &s->part, (size_t)Pn * PS_STRIDE + 256));
+  KRS_TRY(alloc_n(s, &s->tfull, vn));
+  KRS_TRY(alloc_n(s, &s->sfull, vn));
+  s->vpart_P = Pn;
+  s->vld = vn;
+  return KRS_OK;
+}
+
+static krs_status ensure_eig(krs_seq* s, int m) {
+  if (m <= s->eig_cap) return KRS_OK;
+  const int cap = (int)round_up(m, 64);
+  dev_free(s, s->delta);
+  dev_free(s, s->eta);
+  dev_free(s, s->theta_m);
+  dev_free(s, s->theta_m1);
+  dev_free(s, s->tsel);
+  dev_free(s, s->sel);
+  KRS_TRY(alloc_n(s, &s->delta, cap));
+  KRS_TRY(alloc_n(s, &s->eta, cap));
+  KRS_TRY(alloc_n(s, &s->theta_m, cap));
+  KRS_TRY(alloc_n(s, &s->theta_m1, cap));
+  KRS_TRY(alloc_n(s, &s->tsel, 2 * cap));
+  KRS_TRY(alloc_n(s, &s->sel, cap));
+  s->eig_cap = cap;
+  return KRS_OK;
+}
+
+// partition of the block rows over P CTAs (npc nodes each, a multiple of 4)
+static void partition(const krs_seq* s, int blocks_per_sm, int* P, int* npc) {
+  const int pmax = (blocks_per_sm > 0 ? blocks_per_sm : 1) * s->sms;
+  int64_t per = (s->nbr + pmax - 1) / pmax;
+  if (per < kMinNodesPerCta) per = kMinNodesPerCta;
+  per = round_up(per, 4);
+  *npc = (int)per;
+  *P = (int)((s->nbr + per - 1) / per);
+  if (*P < 1) *P = 1;
+}
+
+// ------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------
+extern "C" {
+
+const char* krs_last_error(void) { return g_last_error.c_str(); }
+
+const char* krs_version(void) { return "krs 0.1 (sm_103a)"; }
+
+krs_status krs_policy_default(krs_policy* p) {
+  if (!p) return fail(KRS_ERR_INVALID_ARG, "policy is NULL");
+  memset(p, 0, sizeof(*p));
+  p->recycle = KRS_RECYCLE_NONE;
+  p->precond = KRS_PRECOND_BLOCK_JACOBI3;
+  p->reorth = KRS_REORTH_FULL;
+  p->precision = KRS_FP64;
+  p->ritz_eps = 1e-14;
+  p->theta_frac = 0.0;
+  p->max_aug = 0;
+  p->cap_mode = KRS_CAP_TRUNCATE;
+  p->max_iter = 2000;
+  p->exec = KRS_EXEC_PERSISTENT;
+  return KRS_OK;
+}
+
+krs_status krs_validate_bsr(int32_t nbr, int64_t nnzb, const int32_t* rp, const int32_t* ci) {
+  if (nbr < 0 || nnzb < 0) return fail(KRS_ERR_INVALID_ARG, "negative size");
+  if (nbr > 0 && (!rp || !ci)) return fail(KRS_ERR_INVALID_ARG, "NULL pattern array");
+  if (nbr == 0) return KRS_OK;
+  if (rp[0] != 0) return fail(KRS_ERR_INVALID_ARG, "row_ptr[0] = %d, expected 0", rp[0]);
+  if ((int64_t)rp[nbr] != nnzb) return fail(KRS_ERR_INVALID_ARG, "row_ptr[n] = %d != nnzb %lld", rp[nbr], (long long)nnzb);
+  for (int i = 0; i < nbr; i++) {
+    if (rp[i + 1] < rp[i]) return fail(KRS_ERR_INVALID_ARG, "row_ptr decreases at row %d", i);
+    int has_diag = 0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) {
+      if (ci[k] < 0 || ci[k] >= nbr) return fail(KRS_ERR_INVALID_ARG, "col_idx[%d] = %d out of range", k, ci[k]);
+      if (k > rp[i] && ci[k] <= ci[k - 1]) return fail(KRS_ERR_INVALID_ARG, "row %d columns not strictly ascending", i);
+      if (ci[k] == i) has_diag = 1;
+    }
+    if (!has_diag) return fail(KRS_ERR_INVALID_ARG, "row %d has no diagonal block", i);
+  }
+  return KRS_OK;
+}
+
+krs_status krs_create_sequence(int64_t n, const krs_device* dev, krs_seq_t* out) {
+  if (!out) return fail(KRS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n <= 0 || n % 3 != 0 || n / 3 > 0x7fffffff) return fail(KRS_ERR_INVALID_ARG, "n = %lld must be a positive multiple of 3", (long long)n);
+  if (dev && ((dev->alloc == nullptr) != (dev->free == nullptr)))
+    return fail(KRS_ERR_INVALID_ARG, "alloc and free must both be set or both be NULL");
+  krs_seq* s = new (std::nothrow) krs_seq();
+  if (!s) return fail(KRS_ERR_OOM, "host allocation failed");
+  s->n = n;
+  s->nbr = (int)(n / 3);
+  s->ld = round_up(n, 32);
+  if (dev) {
+    s->device = dev->device;
+    s->stream = (cudaStream_t)dev->cuda_stream;
+    s->ualloc = dev->alloc;
+    s->ufree = dev->free;
+    s->uctx = dev->ctx;
+  }
+  auto bail = [&](krs_status st) {
+    krs_destroy_sequence(s);
+    return st;
+  };
+  cudaError_t e = cudaSetDevice(s->device);
+  if (e != cudaSuccess) {
+    delete s;
+    return fail(KRS_ERR_CUDA, "cudaSetDevice(%d): %s", dev ? dev->device : 0, cudaGetErrorString(e));
+  }
+  e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+  if (e != cudaSuccess) {
+    delete s;
+    return fail(KRS_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+  }
+  krs_status st;
+  if ((st = alloc_n(s, &s->x, s->ld)) || (st = alloc_n(s, &s->r, s->ld)) || (st = alloc_n(s, &s->u, s->ld)) ||
+      (st = alloc_n(s, &s->b, s->ld)) || (st = alloc_n(s, &s->tmp, s->ld)) ||
+      (st = alloc_n(s, &s->minv, 3 * s->ld + 64)) || (st = alloc_n(s, &s->ctrl, 64)) ||
+      (st = alloc_n(s, &s->bar, 8)) || (st = alloc_n(s, &s->scal, 16)) || (st = alloc_n(s, &s->selcount, 8)))
+    return bail(st);
+  if (cudaMallocHost(&s->h_scal, 16 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&s->h_ctrl, 64 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(KRS_ERR_OOM, "pinned host allocation failed"));
+  }
+  for (int i = 0; i < 4; i++) {
+    if (cudaEventCreate(&s->ev[i]) != cudaSuccess) return bail(fail(KRS_ERR_CUDA, "cudaEventCreate failed"));
+  }
+  *out = s;
+  return KRS_OK;
+}
+
+krs_status krs_destroy_sequence(krs_seq_t s) {
+  if (!s) return KRS_OK;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->stream);
+  std::vector<void*> all = s->allocs;
+  for (void* p : all) dev_free(s, p);
+  if (s->h_scal) cudaFreeHost(s->h_scal);
+  if (s->h_ctrl) cudaFreeHost(s->h_ctrl);
+  for (int i = 0; i < 4; i++)
+    if (s->ev[i]) cudaEventDestroy(s->ev[i]);
+  delete s;
+  return KRS_OK;
+}
+
+krs_status krs_stats(krs_seq_t s, krs_solve_stats* out) {
+  if (!s || !out) return fail(KRS_ERR_INVALID_ARG, "NULL argument");
+  *out = s->st;
+  return KRS_OK;
+}
+
+krs_status krs_set_spin_limit(krs_seq_t s, int64_t spins) {
+  if (!s || spins < 0) return fail(KRS_ERR_INVALID_ARG, "bad argument");
+  s->spin_limit = spins ? spins : kDefaultSpin;
+  return KRS_OK;
+}
+
+krs_status krs_space_size(krs_seq_t s, int32_t* n_c) {
+  if (!s || !n_c) return fail(KRS_ERR_INVALID_ARG, "NULL argument");
+  *n_c = s->nc;
+  return KRS_OK;
+}
+
+krs_status krs_export_space(krs_seq_t s, double* C_out) {
+  if (!s || (!C_out && s->nc > 0)) return fail(KRS_ERR_INVALID_ARG, "NULL argument");
+  if (s->nc == 0) return KRS_OK;
+  KRS_CUDA(cudaSetDevice(s->device));
+  const bool dv = is_device_ptr(C_out);
+  KRS_CUDA(cudaMemcpy2DAsync(C_out, sizeof(double) * s->n, s->C, sizeof(double) * s->ld, sizeof(double) * s->n,
+                             s->nc, dv ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  return KRS_OK;
+}
+
+krs_status krs_import_space(krs_seq_t s, int32_t n_c, const double* C_in, int32_t as_c0) {
+  if (!s || n_c < 0 || (n_c > 0 && !C_in)) return fail(KRS_ERR_INVALID_ARG, "bad argument");
+  KRS_CUDA(cudaSetDevice(s->device));
+  KRS_TRY(ensure_cap_c(s, n_c));
+  const bool dv = n_c > 0 && is_device_ptr(C_in);
+  if (n_c > 0)
+    KRS_CUDA(cudaMemcpy2DAsync(s->C, sizeof(double) * s->ld, C_in, sizeof(double) * s->n, sizeof(double) * s->n,
+                               n_c, dv ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream));
+  s->nc = n_c;
+  s->ac_valid = 0;
+  s->g_valid = 0;
+  s->ginv_valid = false;
+  if (as_c0) {
+    dev_free(s, s->C0);
+    s->C0 = nullptr;
+    s->nc0 = n_c;
+    if (n_c > 0) {
+      KRS_TRY(alloc_n(s, &s->C0, (size_t)n_c * s->ld));
+      KRS_CUDA(cudaMemcpyAsync(s->C0, s->C, sizeof(double) * (size_t)n_c * s->ld, cudaMemcpyDeviceToDevice,
+                               s->stream));
+    }
+  }
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  return KRS_OK;
+}
+
+krs_status krs_last_coeffs(krs_seq_t s, double* alpha, double* rho, double* gamma) {
+  if (!s) return fail(KRS_ERR_INVALID_ARG, "NULL sequence");
+  const int m = s->last_m;
+  KRS_CUDA(cudaSetDevice(s->device));
+  if (m > 0) {
+    if (alpha) KRS_CUDA(cudaMemcpyAsync(alpha, s->alpha, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
+    if (rho) KRS_CUDA(cudaMemcpyAsync(rho, s->rho, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
+    if (gamma) KRS_CUDA(cudaMemcpyAsync(gamma, s->gamma, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
+  }
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  return KRS_OK;
+}
+
+krs_status krs_last_ritz(krs_seq_t s, double* theta_m, double* theta_m1, int32_t* sel) {
+  if (!s) return fail(KRS_ERR_INVALID_ARG, "NULL sequence");
+  const int m = s->last_m;
+  if (!s->last_srks || m < 2) return KRS_OK;
+  KRS_CUDA(cudaSetDevice(s->device));
+  if (theta_m) KRS_CUDA(cudaMemcpyAsync(theta_m, s->theta_m, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
+  if (theta_m1)
+    KRS_CUDA(cudaMemcpyAsync(theta_m1, s->theta_m1, sizeof(double) * (m - 1), cudaMemcpyDeviceToHost, s->stream));
+  if (sel && s->last_nsel > 0)
+    KRS_CUDA(cudaMemcpyAsync(sel, s->sel, sizeof(int32_t) * s->last_nsel, cudaMemcpyDeviceToHost, s->stream));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  return KRS_OK;
+}
+
+krs_status krs_last_vectors(krs_seq_t s, int32_t which, double* out) {
+  if (!s || which < 0 || which > 2) return fail(KRS_ERR_INVALID_ARG, "bad argument");
+  const int m = s->last_m;
+  if (m == 0) return KRS_OK;
+  if (!out) return fail(KRS_ERR_INVALID_ARG, "NULL output");
+  KRS_CUDA(cudaSetDevice(s->device));
+  const double* src = which == 0 ? s->W : (which == 1 ? s->AW : s->Z);
+  const bool dv = is_device_ptr(out);
+  KRS_CUDA(cudaMemcpy2DAsync(out, sizeof(double) * s->n, src, sizeof(double) * s->ld, sizeof(double) * s->n, m,
+                             dv ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  return KRS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// the solve
+// ------------------------------------------------------------------------------------
+static krs_status validate_policy(const krs_policy* p) {
+  if (!p) return fail(KRS_ERR_INVALID_ARG, "policy is NULL");
+  if (p->recycle < 0 || p->recycle > 2) return fail(KRS_ERR_INVALID_ARG, "bad recycle %d", p->recycle);
+  if (p->precond < 0 || p->precond > 2) return fail(KRS_ERR_INVALID_ARG, "bad precond %d", p->precond);
+  if (p->reorth < 0 || p->reorth > 1) return fail(KRS_ERR_INVALID_ARG, "bad reorth %d", p->reorth);
+  if (p->precision != KRS_FP64) return fail(KRS_ERR_INVALID_ARG, "precision %d not supported by this call", p->precision);
+  if (p->cap_mode < 0 || p->cap_mode > 1) return fail(KRS_ERR_INVALID_ARG, "bad cap_mode %d", p->cap_mode);
+  if (p->max_aug < 0) return fail(KRS_ERR_INVALID_ARG, "bad max_aug %d", p->max_aug);
+  if (p->max_iter < 1 || p->max_iter > 16000) return fail(KRS_ERR_INVALID_ARG, "max_iter %d outside [1, 16000]", p->max_iter);
+  if (p->exec < 0 || p->exec > 1) return fail(KRS_ERR_INVALID_ARG, "bad exec %d", p->exec);
+  if (!(p->ritz_eps == p->ritz_eps) || !(p->theta_frac == p->theta_frac)) return fail(KRS_ERR_INVALID_ARG, "NaN policy field");
+  return KRS_OK;
+}
+
+static krs_status upload_matrix(krs_seq* s, const krs_bsr* A, bool* changed) {
+  *changed = false;
+  if (A->block_dim != 3) return fail(KRS_ERR_INVALID_ARG, "block_dim %d != 3", A->block_dim);
+  if ((int64_t)A->n_block_rows * 3 != s->n) return fail(KRS_ERR_INVALID_ARG, "matrix order %lld != sequence order %lld",
+                                                        (long long)A->n_block_rows * 3, (long long)s->n);
+  if (A->nnzb <= 0 || !A->row_ptr || !A->col_idx || !A->values) return fail(KRS_ERR_INVALID_ARG, "empty matrix");
+  const bool same = s->A_valid && A->version == s->A_version &&
+                    (A->on_device ? (A->values == s->vals_use && A->row_ptr == s->rp_use && A->col_idx == s->ci_use)
+                                  : true);
+  if (same) return KRS_OK;
+  *changed = true;
+  if (A->on_device) {
+    s->rp_use = A->row_ptr;
+    s->ci_use = A->col_idx;
+    s->vals_use = A->values;
+  } else {
+    KRS_TRY(krs_validate_bsr(A->n_block_rows, A->nnzb, A->row_ptr, A->col_idx));
+    if (A->nnzb > s->nnzb_cap) {
+      dev_free(s, s->rp);
+      dev_free(s, s->ci);
+      dev_free(s, s->vals);
+      s->rp = nullptr;
+      s->ci = nullptr;
+      s->vals = nullptr;
+      KRS_TRY(alloc_n(s, &s->rp, (size_t)s->nbr + 1));
+      KRS_TRY(alloc_n(s, &s->ci, (size_t)A->nnzb));
+      KRS_TRY(alloc_n(s, &s->vals, (size_t)A->nnzb * 9));
+      s->nnzb_cap = A->nnzb;
+    }
+    KRS_CUDA(cudaMemcpyAsync(s->rp, A->row_ptr, sizeof(int32_t) * ((size_t)s->nbr + 1), cudaMemcpyHostToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(s->ci, A->col_idx, sizeof(int32_t) * (size_t)A->nnzb, cudaMemcpyHostToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(s->vals, A->values, sizeof(double) * 9 * (size_t)A->nnzb, cudaMemcpyHostToDevice, s->stream));
+    s->rp_use = s->rp;
+    s->ci_use = s->ci;
+    s->vals_use = s->vals;
+  }
+  s->A_valid = true;
+  s->A_version = A->version;
+  s->precond_built = -1;
+  s->ac_valid = 0;
+  s->g_valid = 0;
+  s->ginv_valid = false;
+  return KRS_OK;
+}
+
+static krs_status read_status(krs_seq* s, int* st) {
+  KRS_CUDA(cudaMemcpyAsync(s->h_ctrl, s->ctrl, sizeof(int) * CTRL_WORDS, cudaMemcpyDeviceToHost, s->stream));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  *st = s->h_ctrl[CTRL_STATUS];
+  return KRS_OK;
+}
+
+static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, double* x, double tol,
+                             const krs_policy* p) {
+  krs_solve_stats st{};
+  st.n_c = s->nc;
+  s->st = st;
+  s->last_m = 0;
+  s->last_srks = 0;
+  s->last_nsel = 0;
+  int64_t launches = 0;
+  KRS_CUDA(cudaSetDevice(s->device));
+  KRS_CUDA(cudaEventRecord(s->ev[0], s->stream));
+
+  // ---- matrix, preconditioner
+  bool changed = false;
+  KRS_TRY(upload_matrix(s, A, &changed));
+  if (s->precond_built != p->precond) {
+    KRS_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, s->stream));
+    KRS_CUDA(launch_precond_setup(p->precond, s->nbr, s->rp_use, s->ci_use, s->vals_use, s->minv, s->ctrl + CTRL_STATUS,
+                                  s->stream));
+    launches++;
+    int code = 0;
+    KRS_TRY(read_status(s, &code));
+    if (code) return fail((krs_status)code, code == KRS_ERR_NOT_SPD ? "preconditioner: a diagonal block is not positive definite"
+                                                                    : "preconditioner: missing diagonal block");
+    s->precond_built = p->precond;
+  }
+
+  // ---- right-hand side into the padded device vector
+  const bool b_dev = is_device_ptr(b);
+  KRS_CUDA(cudaMemcpyAsync(s->b, b, sizeof(double) * s->n, b_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           s->stream));
+
+  // ---- storage
+  KRS_TRY(ensure_cap_w(s, p->max_iter));
+  const int kmax = (s->nc > p->max_iter + 1) ? s->nc : p->max_iter + 1;
+  KRS_CUDA(apcg_prepare_attributes(kmax));
+  int bps = 0;
+  KRS_CUDA(apcg_max_coresident(kmax, &bps));
+  if (bps < 1) return fail(KRS_ERR_CUDA, "persistent kernel cannot be resident (kmax %d)", kmax);
+  int P = 0, npc = 0;
+  partition(s, bps, &P, &npc);
+  KRS_TRY(ensure_vpart(s, P, kmax));
+
+  // ---- coarse set-up: A C (new columns), C^T A C (new tiles), Cholesky and inverse
+  const int nc = s->nc;
+  if (nc > 0) {
+    if (s->ac_valid < nc) {
+      KRS_CUDA(launch_spmm(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->C, s->AC, s->ld, s->ac_valid, nc, s->stream));
+      launches++;
+      if (s->g_valid > s->ac_valid) s->g_valid = s->ac_valid;
+      s->ac_valid = nc;
+    }
+    if (s->g_valid < nc) {
+      const size_t need = gram_scratch_doubles(s->n, nc, s->g_valid);
+      if (need > s->gram_cap) {
+        dev_free(s, s->gram_scratch);
+        s->gram_scratch = nullptr;
+        KRS_TRY(alloc_n(s, &s->gram_scratch, need));
+        s->gram_cap = need;
+      }
+      KRS_CUDA(launch_gram(s->n, s->C, s->AC, s->ld, nc, s->g_valid, s->G, s->cap_c, s->gram_scratch, s->gram_cap,
+                           s->stream));
+      launches += 2;
+      s->g_valid = nc;
+      s->ginv_valid = false;
+    }
+    if (!s->ginv_valid) {
+      KRS_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, s->stream));
+      KRS_CUDA(launch_chol_inverse(nc, s->G, s->cap_c, s->Lw, s->Ginv, s->ctrl + CTRL_STATUS, s->stream));
+      launches += 2;
+      int code = 0;
+      KRS_TRY(read_status(s, &code));
+      if (code) {
+        s->st.status = code;
+        return fail((krs_status)code, "Cholesky of C^T A C failed (C rank deficient or A not SPD)");
+      }
+      s->ginv_valid = true;
+    }
+  }
+
+  // ---- initialisation
+  IterArgs a{};
+  a.n = s->n; a.ld = s->ld; a.nbr = s->nbr; a.npc = npc; a.P = P;
+  a.nc = nc; a.ldg = s->cap_c; a.max_iter = p->max_iter; a.reorth_full = (p->reorth == KRS_REORTH_FULL);
+  a.precond = p->precond; a.kmax = kmax; a.spin_limit = s->spin_limit;
+  a.rp = s->rp_use; a.ci = s->ci_use; a.vals = s->vals_use; a.minv = s->minv;
+  a.C = s->C; a.AC = s->AC; a.Ginv = s->Ginv;
+  a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.x = s->x; a.r = s->r; a.u = s->u;
+  a.alpha = s->alpha; a.gamma = s->gamma; a.rho = s->rho;
+  a.tfull = s->tfull; a.sfull = s->sfull; a.gfull = s->gfull;
+  a.part = s->part; a.vpart = s->vpart; a.vld = s->vld; a.ctrl = s->ctrl; a.bar = s->bar;
+  KRS_CUDA(apcg_launch_init(a, s->b, s->scal, s->stream, &launches));
+  KRS_CUDA(cudaMemcpyAsync(s->h_scal, s->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  const double bb = s->h_scal[0], rr0 = s->h_scal[1];
+  if (!isfinite(bb)) return fail(KRS_ERR_INVALID_ARG, "right-hand side is not finite");
+  a.tol2 = tol * tol * bb;
+  KRS_CUDA(cudaEventRecord(s->ev[1], s->stream));
+
+  // ---- iterations
+  int status = KRS_OK, m = 0;
+  if (!(rr0 <= a.tol2)) {
+    KRS_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, s->stream));
+    KRS_CUDA(cudaMemsetAsync(s->bar, 0, sizeof(unsigned long long), s->stream));
+    if (p->exec == KRS_EXEC_PERSISTENT) {
+      KRS_CUDA(apcg_launch_persistent(a, s->stream, &launches));
+      KRS_CUDA(cudaMemcpyAsync(s->h_ctrl, s->ctrl, sizeof(int) * CTRL_WORDS, cudaMemcpyDeviceToHost, s->stream));
+      KRS_CUDA(cudaStreamSynchronize(s->stream));
+    } else {
+      int j = 0;
+      const int batch = 16;
+      for (;;) {
+        const int j1 = (j + batch < p->max_iter) ? j + batch : p->max_iter;
+        KRS_CUDA(apcg_launch_phases(a, j, j1, s->stream, &launches));
+        KRS_CUDA(cudaMemcpyAsync(s->h_ctrl, s->ctrl, sizeof(int) * CTRL_WORDS, cudaMemcpyDeviceToHost, s->stream));
+        KRS_CUDA(cudaStreamSynchronize(s->stream));
+        j = j1;
+        if (s->h_ctrl[CTRL_DONE] || j >= p->max_iter) break;
+      }
+    }
+    status = s->h_ctrl[CTRL_STATUS];
+    m = s->h_ctrl[CTRL_M];
+    if (!s->h_ctrl[CTRL_DONE] && status == KRS_OK) status = KRS_ERR_CUDA;
+  }
+  KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
+  s->last_m = m;
+
+  // ---- result and true residual
+  const bool x_dev = is_device_ptr(x);
+  KRS_CUDA(cudaMemcpyAsync(x, s->x, sizeof(double) * s->n, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           s->stream));
+  KRS_CUDA(launch_true_residual(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->part, s->scal + 2,
+                                s->stream));
+  launches += 3;
+  KRS_CUDA(launch_norm2(s->n, s->r, s->part, s->scal + 3, s->stream));
+  launches += 2;
+  KRS_CUDA(cudaMemcpyAsync(s->h_scal, s->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+
+  st.status = status;
+  st.m = m;
+  st.n_c = nc;
+  st.true_rel_res = bb > 0.0 ? sqrt(s->h_scal[2] / bb) : 0.0;
+  st.rel_res = bb > 0.0 ? sqrt(s->h_scal[3] / bb) : 0.0;
+  if (status != KRS_OK) {
+    st.n_c_after = nc;
+    float t1 = 0.f, t2 = 0.f;
+    cudaEventElapsedTime(&t1, s->ev[0], s->ev[1]);
+    cudaEventElapsedTime(&t2, s->ev[1], s->ev[2]);
+    st.t_setup_ms = t1;
+    st.t_iter_ms = t2;
+    st.t_total_ms = t1 + t2;
+    st.kernel_launches = launches;
+    s->st = st;
+    const char* what = status == KRS_ERR_NOT_SPD ? "operator not SPD ((w, Aw) <= 0 or (r, z) <= 0)"
+                       : status == KRS_ERR_NO_CONVERGENCE ? "max_iter reached"
+                       : status == KRS_ERR_TIMEOUT ? "device wait timed out"
+                                                  : "solve did not complete";
+    return fail((krs_status)status, "%s (m = %d)", what, m);
+  }
+
+  // ---- recycling
+  int add = 0;
+  const int cap = p->max_aug > 0 ? p->max_aug : 0x7fffffff;
+  if (p->recycle == KRS_RECYCLE_TRKS && m > 0) {
+    add = m;
+    if (p->cap_mode == KRS_CAP_TRUNCATE && nc + add > cap) add = cap - nc > 0 ? cap - nc : 0;
+    if (add > 0) {
+      KRS_TRY(ensure_cap_c(s, nc + add));
+      KRS_CUDA(cudaMemcpyAsync(s->C + (size_t)nc * s->ld, s->W, sizeof(double) * (size_t)add * s->ld,
+                               cudaMemcpyDeviceToDevice, s->stream));
+      if (s->ac_valid == nc) {
+        // A is unchanged since the directions' products were formed: A W is A C's new block
+        KRS_CUDA(cudaMemcpyAsync(s->AC + (size_t)nc * s->ld, s->AW, sizeof(double) * (size_t)add * s->ld,
+                                 cudaMemcpyDeviceToDevice, s->stream));
+        s->ac_valid = nc + add;
+      }
+    }
+  } else if (p->recycle == KRS_RECYCLE_SRKS && m >= 2) {
+    s->last_srks = 1;
+    KRS_TRY(ensure_eig(s, m));
+    const int room = (p->cap_mode == KRS_CAP_TRUNCATE) ? (cap - nc > 0 ? cap - nc : 0) : m;
+    KRS_CUDA(launch_lanczos(m, s->alpha, s->rho, s->delta, s->eta, s->stream));
+    KRS_CUDA(launch_tridiag_eigvals2(m, m - 1, s->delta, s->eta, s->theta_m, s->theta_m1, s->stream));
+    KRS_CUDA(launch_srks_select(m, s->theta_m, s->theta_m1, p->ritz_eps, p->theta_frac, room, s->sel, s->selcount,
+                                s->tsel, s->stream));
+    launches += 3;
+    int cnt = 0;
+    KRS_CUDA(cudaMemcpyAsync(&s->h_ctrl[16], s->selcount, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    KRS_CUDA(cudaStreamSynchronize(s->stream));
+    cnt = s->h_ctrl[16];
+    s->last_nsel = cnt;
+    if (cnt > 0) {
+      KRS_TRY(ensure_cap_c(s, nc + cnt));
+      const size_t wneed = eigvecs_work_doubles(m, cnt) + (size_t)m * cnt * 2;
+      dev_free(s, s->eigwork);
+      s->eigwork = nullptr;
+      KRS_TRY(alloc_n(s, &s->eigwork, wneed));
+      double* Q = s->eigwork;
+      double* Fm = s->eigwork + (size_t)m * cnt;
+      double* wk = s->eigwork + 2 * (size_t)m * cnt;
+      KRS_CUDA(launch_tridiag_eigvecs(m, s->delta, s->eta, cnt, s->tsel, Q, wk, s->stream));
+      KRS_CUDA(launch_ritz_vectors(s->n, s->ld, m, cnt, s->Z, s->rho, Q, s->tsel, Fm, s->C + (size_t)nc * s->ld,
+                                   s->stream));
+      launches += 3;
+      add = cnt;
+    }
+  }
+  s->nc = nc + add;
+  if (p->cap_mode == KRS_CAP_RESTART && p->max_aug > 0 && s->nc >= p->max_aug) {
+    // Algorithm 3, last step: back to C^(0)
+    if (s->nc0 > 0)
+      KRS_CUDA(cudaMemcpyAsync(s->C, s->C0, sizeof(double) * (size_t)s->nc0 * s->ld, cudaMemcpyDeviceToDevice, s->stream));
+    s->nc = s->nc0;
+    s->ac_valid = 0;
+    s->g_valid = 0;
+    s->ginv_valid = false;
+  }
+  KRS_CUDA(cudaEventRecord(s->ev[3], s->stream));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  float t1 = 0.f, t2 = 0.f, t3 = 0.f;
+  cudaEventElapsedTime(&t1, s->ev[0], s->ev[1]);
+  cudaEventElapsedTime(&t2, s->ev[1], s->ev[2]);
+  cudaEventElapsedTime(&t3, s->ev[2], s->ev[3]);
+  st.n_selected = add;
+  st.n_c_after = s->nc;
+  st.t_setup_ms = t1;
+  st.t_iter_ms = t2;
+  st.t_recycle_ms = t3;
+  st.t_total_ms = t1 + t2 + t3;
+  st.kernel_launches = launches;
+  s->st = st;
+  return KRS_OK;
+}
+
+extern "C" krs_status krs_solve(krs_seq_t s, const krs_bsr* A, const double* b, double* x, double tol,
+                                const krs_policy* p) {
+  if (!s || !A || !b || !x) return fail(KRS_ERR_INVALID_ARG, "NULL argument");
+  if (!(tol >= 0.0) || !isfinite(tol)) return fail(KRS_ERR_INVALID_ARG, "tol must be finite and >= 0");
+  KRS_TRY(validate_policy(p));
+  krs_status st = solve_impl(s, A, b, x, tol, p);
+  if (st != KRS_OK && s->st.status == 0) s->st.status = st;
+  return st;
+}
+
+// ------------------------------------------------------------------------------------
+// single-kernel entry points
+// ------------------------------------------------------------------------------------
+extern "C" {
+
+krs_status krs_spmv_bsr3(int32_t nbr, const int32_t* rp, const int32_t* ci, const double* vals, const double* x,
+                         double* y, void* stream) {
+  if (nbr < 0 || (nbr > 0 && (!rp || !ci || !vals || !x || !y))) return fail(KRS_ERR_INVALID_ARG, "bad argument");
+  KRS_CUDA(launch_spmv(nbr, rp, ci, vals, x, y, (cudaStream_t)stream));
+  return KRS_OK;
+}
+
+krs_status krs_precond_setup(int32_t kind, int32_t nbr, const int32_t* rp, const int32_t* ci, const double* vals,
+                             double* minv, int32_t* status, void* stream) {
+  if (kind < 0 || kind > 2 || nbr < 0 || (nbr > 0 && (!rp || !ci || !vals || (kind != 2 && !minv))))
+    return fail(KRS_ERR_INVALID_ARG, "bad argument");
+  KRS_CUDA(launch_precond_setup(kind, nbr, rp, ci, vals, minv, status, (cudaStream_t)stream));
+  return KRS_OK;
+}
+
+krs_status krs_precond_apply(int32_t kind, int32_t nbr, const double* minv, const double* r, double* u, void* stream) {
+  if (kind < 0 || kind > 2 || nbr < 0 || (nbr > 0 && (!r || !u || (kind != 2 && !minv))))
+    return fail(KRS_ERR_INVALID_ARG, "bad argument");
+  KRS_CUDA(launch_precond_apply(kind, nbr, minv, r, u, (cudaStream_t)stream));
+  return KRS_OK;
+}
+
+static krs_status check_tall(int64_t n, int32_t k, const double* V, int64_t ldv, const void* u) {
+  if (n < 0 || k < 0 || (k > 0 && n > 0 && (!V || !u))) return fail(KRS_ERR_INVALID_ARG, "bad argument");
+  if (ldv % 4 != 0 || ldv < round_up(n, 4)) return fail(KRS_ERR_INVALID_ARG, "ldv must be a multiple of 4 and >= n rounded up to 4");
+  if (((uintptr_t)V & 31) || ((uintptr_t)u & 31)) return fail(KRS_ERR_INVALID_ARG, "V and u must be 32-byte aligned");
+  if (k > 16384) return fail(KRS_ERR_INVALID_ARG, "k > 16384");
+  return KRS_OK;
+}
+
+// rows per CTA of the stand-alone tall-skinny launches
+static krs_status tall_partition(int64_t n, int* P, int64_t* rpc) {
+  int dev = 0, sms = 0;
+  KRS_CUDA(cudaGetDevice(&dev));
+  KRS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int64_t r = round_up((n + sms - 1) / (sms > 0 ? sms : 1), 4);
+  if (r < 64) r = 64;
+  *rpc = r;
+  *P = (int)((n + r - 1) / r);
+  return KRS_OK;
+}
+
+krs_status krs_gemv_t(int64_t n, int32_t k, const double* V, int64_t ldv, const double* u, double* t, void* stream) {
+  KRS_TRY(check_tall(n, k, V, ldv, u));
+  if (k == 0) return KRS_OK;
+  if (!t) return fail(KRS_ERR_INVALID_ARG, "t is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  int P = 0;
+  int64_t rpc = 0;
+  KRS_TRY(tall_partition(n, &P, &rpc));
+  double* vpart = nullptr;
+  KRS_CUDA(cudaMallocAsync((void**)&vpart, sizeof(double) * (size_t)(P > 0 ? P : 1) * k, st));
+  KRS_CUDA(launch_gemv_t_rows(n, k, V, ldv, u, t, vpart, P, rpc, st));
+  KRS_CUDA(cudaFreeAsync(vpart, st));
+  return KRS_OK;
+}
+
+krs_status krs_gemv_n_sub(int64_t n, int32_t k, const double* V, int64_t ldv, const double* s, const double* u,
+                          double* z, void* stream) {
+  KRS_TRY(check_tall(n, k, V, ldv, u));
+  if (n == 0) return KRS_OK;
+  if (!z || (k > 0 && !s)) return fail(KRS_ERR_INVALID_ARG, "NULL argument");
+  int P = 0;
+  int64_t rpc = 0;
+  KRS_TRY(tall_partition(n, &P, &rpc));
+  KRS_CUDA(launch_gemv_n_rows(n, k, V, ldv, s, u, z, P, rpc, (cudaStream_t)stream));
+  return KRS_OK;
+}
+
+krs_status krs_axpy2_dot(int64_t n, const double* alpha, const double* w, const double* q, double* x, double* r,
+                         double* rr, void* stream) {
+  if (n < 0 || !alpha || !rr || (n > 0 && (!w || !q || !x || !r))) return fail(KRS_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* part = nullptr;
+  KRS_CUDA(cudaMallocAsync((void**)&part, sizeof(double) * 256, st));
+  KRS_CUDA(launch_axpy2_dot(n, alpha, w, q, x, r, rr, part, st));
+  KRS_CUDA(cudaFreeAsync(part, st));
+  return KRS_OK;
+}
+
+krs_status krs_tridiag_eigvals(int32_t m, const double* delta, const double* eta, double* theta, void* stream) {
+  if (m < 0 || (m > 0 && (!delta || !theta || (m > 1 && !eta)))) return fail(KRS_ERR_INVALID_ARG, "bad argument");
+  if (m > 12000) return fail(KRS_ERR_INVALID_ARG, "m > 12000");
+  KRS_CUDA(launch_tridiag_eigvals(m, delta, eta, theta, (cudaStream_t)stream));
+  return KRS_OK;
+}
+
+krs_status krs_tridiag_eigvecs(int32_t m, const double* delta, const double* eta, int32_t k, const double* theta_sel,
+                               double* Q_out, void* stream) {
+  if (m < 0 || k < 0 || (m > 0 && k > 0 && (!delta || !theta_sel || !Q_out || (m > 1 && !eta))))
+    return fail(KRS_ERR_INVALID_ARG, "bad argument");
+  if (m == 0 || k == 0) return KRS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* work = nullptr;
+  KRS_CUDA(cudaMallocAsync((void**)&work, sizeof(double) * eigvecs_work_doubles(m, k), st));
+  KRS_CUDA(launch_tridiag_eigvecs(m, delta, eta, k, theta_sel, Q_out, work, st));
+  KRS_CUDA(cudaFreeAsync(work, st));
+  return KRS_OK;
+}
+
+}  // extern "C"

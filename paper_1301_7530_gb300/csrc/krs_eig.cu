@@ -1,0 +1,390 @@
+// krs_eig.cu -- the between-solve SRKS step on the GPU (Section 4, Algorithm 3):
+//   * H_m = tridiag(eta_{j-1}, delta_j, eta_j) from the CG coefficients (Section 4.1):
+//     beta~_j = rho_{j+1}/rho_j, delta_0 = 1/alpha_0,
+//     delta_j = 1/alpha_j + beta~_{j-1}/alpha_{j-1}, eta_j = sqrt(beta~_j)/alpha_j;
+//   * its eigenvalues and those of H_{m-1} by bisection on Sturm counts (a warp per
+//     eigenvalue; each round the 32 lanes test 32 points, so an interval shrinks 33x);
+//   * the stagnation selection of Eq. 16 (union of both tests), the optional
+//     theta < theta_frac * theta_max filter, ascending-theta order, the cap;
+//   * eigenvectors of the selected values by inverse iteration (a lane per vector,
+//     partial-pivoting LU of T - theta I), orthogonalised inside clusters;
+//   * Ritz vectors y = V q / sqrt(theta), V = [(-1)^j z_j / sqrt(rho_j)] (Eq. 17).
+// The eigenvalue arithmetic is FP64 throughout.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "krs_device.cuh"
+#include "krs_internal.h"
+
+namespace krs {
+
+__global__ void k_lanczos(int m, const double* alpha, const double* rho, double* delta, double* eta) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double d = 1.0 / alpha[j];
+  if (j > 0) d += (rho[j] / rho[j - 1]) / alpha[j - 1];
+  delta[j] = d;
+  if (j < m - 1) eta[j] = sqrt(rho[j + 1] / rho[j]) / alpha[j];
+}
+
+cudaError_t launch_lanczos(int m, const double* alpha, const double* rho, double* delta, double* eta,
+                           cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  k_lanczos<<<(m + 127) / 128, 128, 0, st>>>(m, alpha, rho, delta, eta);
+  return cudaGetLastError();
+}
+
+// Number of eigenvalues of T (order m, diagonal d, squared off-diagonal e2) below x.
+// Pivots of T - x I = L D L^T; a pivot at or below pivmin counts as negative and is
+// replaced by -pivmin (standard safeguard).
+__device__ __forceinline__ int sturm_count(int m, const double* d, const double* e2, double x,
+                                           double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (q <= pivmin) {
+    cnt++;
+    q = fmin(q, -pivmin);
+  }
+  for (int i = 1; i < m; i++) {
+    q = (d[i] - x) - e2[i - 1] / q;
+    if (q <= pivmin) {
+      cnt++;
+      q = fmin(q, -pivmin);
+    }
+  }
+  return cnt;
+}
+
+// One CTA per group of 8 eigenvalues (8 warps).  Job index g in [0, m + m1): g < m is
+// eigenvalue g (descending) of T_m, else eigenvalue g - m of T_{m1} (leading block).
+// Output: theta_m[m], theta_m1[m1], descending.
+constexpr int EIG_WARPS = 8;
+
+__global__ void __launch_bounds__(EIG_WARPS * 32) k_bisect(int m, int m1, const double* __restrict__ delta,
+                                                           const double* __restrict__ eta, double* theta_m,
+                                                           double* theta_m1) {
+  extern __shared__ double sh[];
+  double* d = sh;
+  double* e2 = sh + m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    d[i] = delta[i];
+    if (i < m - 1) e2[i] = eta[i] * eta[i];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int job = blockIdx.x * EIG_WARPS + warp;
+  if (job >= m + m1) return;
+  const int order = (job < m) ? m : m1;
+  const int idx_desc = (job < m) ? job : job - m;
+  const int k = order - 1 - idx_desc;  // ascending index
+  // Gershgorin interval of the order-`order` leading block
+  double lo = d[0], hi = d[0], emax = 0.0;
+  for (int i = 0; i < order; i++) {
+    const double el = (i > 0) ? sqrt(e2[i - 1]) : 0.0;
+    const double er = (i < order - 1) ? sqrt(e2[i]) : 0.0;
+    lo = fmin(lo, d[i] - el - er);
+    hi = fmax(hi, d[i] + el + er);
+    if (i < order - 1) emax = fmax(emax, e2[i]);
+  }
+  const double tnorm = fmax(fabs(lo), fabs(hi));
+  const double pivmin = DBL_MIN * fmax(1.0, emax);
+  lo -= 2.0 * DBL_EPSILON * tnorm + pivmin;
+  hi += 2.0 * DBL_EPSILON * tnorm + pivmin;
+  // invariant: count(lo) <= k < count(hi)
+  for (int round = 0; round < 40; round++) {
+    const double width = hi - lo;
+    if (width <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    const double x = lo + width * ((double)(lane + 1) / 33.0);
+    const int c = sturm_count(order, d, e2, x, pivmin);
+    const unsigned above = __ballot_sync(0xffffffffu, c > k);
+    const int L = above ? (__ffs(above) - 1) : 32;
+    const double xL = __shfl_sync(0xffffffffu, x, L & 31);
+    const double xLm = __shfl_sync(0xffffffffu, x, (L - 1) & 31);
+    const double nhi = (L < 32) ? xL : hi;
+    const double nlo = (L > 0) ? xLm : lo;
+    if (nhi == hi && nlo == lo) break;  // no representable progress
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) {
+    const double v = 0.5 * (lo + hi);
+    if (job < m) theta_m[idx_desc] = v;
+    else theta_m1[idx_desc] = v;
+  }
+}
+
+cudaError_t launch_tridiag_eigvals2(int m, int m1, const double* delta, const double* eta, double* theta_m,
+                                    double* theta_m1, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  const int jobs = m + m1;
+  const size_t sm = sizeof(double) * (size_t)(2 * m + 1);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_bisect<<<(jobs + EIG_WARPS - 1) / EIG_WARPS, EIG_WARPS * 32, sm, st>>>(m, m1, delta, eta, theta_m, theta_m1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag_eigvals(int m, const double* delta, const double* eta, double* theta,
+                                   cudaStream_t st) {
+  return launch_tridiag_eigvals2(m, 0, delta, eta, theta, nullptr, st);
+}
+
+// ------------------------------------------------------------------------------------
+// selection (one thread; O(m))
+// ------------------------------------------------------------------------------------
+__global__ void k_srks_select(int m, const double* tm, const double* tm1, double eps, double theta_frac,
+                              int room, int* sel, int* count, double* tsel, unsigned char* flag) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int cnt = 0;
+  if (m >= 2 && room > 0 && eps > 0.0) {
+    for (int i = 0; i < m; i++) flag[i] = 0;
+    for (int j = 1; j <= m - 1; j++) {  // paper's 1-based j
+      const double a = tm[j - 1], b = tm1[j - 1], c = tm[j];
+      if (fabs(a - b) <= eps * fabs(a)) flag[j - 1] = 1;
+      if (fabs(c - b) <= eps * fabs(c)) flag[j] = 1;
+    }
+    if (theta_frac > 0.0) {
+      const double lim = theta_frac * tm[0];
+      for (int i = 0; i < m; i++)
+        if (flag[i] && !(tm[i] < lim)) flag[i] = 0;
+    }
+    for (int i = m - 1; i >= 0 && cnt < room; i--) {
+      if (flag[i]) {
+        sel[cnt] = i;
+        tsel[cnt] = tm[i];
+        cnt++;
+      }
+    }
+  }
+  *count = cnt;
+}
+
+cudaError_t launch_srks_select(int m, const double* theta_m, const double* theta_m1, double eps,
+                               double theta_frac, int room, int* sel, int* count, double* tsel,
+                               cudaStream_t st) {
+  // the flag array lives after tsel's m entries (caller provides 2m doubles for tsel)
+  k_srks_select<<<1, 32, 0, st>>>(m, theta_m, theta_m1, eps, theta_frac, room, sel, count, tsel,
+                                   reinterpret_cast<unsigned char*>(tsel + m));
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// eigenvectors by inverse iteration
+// ------------------------------------------------------------------------------------
+constexpr int INV_ITERS = 3;
+constexpr int VEC_TPB = 256;
+
+size_t eigvecs_work_doubles(int m, int k) { return (size_t)5 * m * k + 64; }
+
+// Sum over the VEC_TPB threads of a block (warp butterflies, then warp 0); all threads get it.
+__device__ __forceinline__ double vec_block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < VEC_TPB / 32; w++) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+// One CTA; thread c < k owns eigenvector c.  Work layout: [array][i][c] (arrays: d, du1,
+// du2, l, piv) so that lanes touch consecutive addresses.
+__global__ void __launch_bounds__(VEC_TPB) k_tridiag_eigvecs(int m, const double* __restrict__ delta,
+                                                             const double* __restrict__ eta, int k,
+                                                             const double* __restrict__ theta,
+                                                             double* __restrict__ Q, double* __restrict__ work) {
+  __shared__ double red[VEC_TPB / 32];
+  // ||T||_1 bound for tiny-pivot replacement and cluster detection
+  double tn = 0.0;
+  for (int i = 0; i < m; i++) {
+    const double a = fabs(delta[i]) + (i > 0 ? fabs(eta[i - 1]) : 0.0) + (i < m - 1 ? fabs(eta[i]) : 0.0);
+    tn = fmax(tn, a);
+  }
+  const double tiny = DBL_EPSILON * tn;
+  const double ortol = 1e-6 * tn;
+  double* D = work;
+  double* U1 = work + (size_t)m * k;
+  double* U2 = work + 2 * (size_t)m * k;
+  double* Lm = work + 3 * (size_t)m * k;
+  double* PV = work + 4 * (size_t)m * k;
+  for (int c0 = 0; c0 < k; c0 += VEC_TPB) {
+    const int c = c0 + threadIdx.x;
+    if (c < k) {
+      const double th = theta[c];
+      // LU with partial pivoting of T - th I
+      double cd = delta[0] - th;
+      double cu1 = (m > 1) ? eta[0] : 0.0;
+      for (int i = 0; i < m - 1; i++) {
+        const double sub = eta[i];
+        const double nd = delta[i + 1] - th;
+        const double nu = (i + 1 < m - 1) ? eta[i + 1] : 0.0;
+        const size_t at = (size_t)i * k + c;
+        if (fabs(cd) >= fabs(sub)) {
+          if (cd == 0.0) cd = tiny;
+          const double mult = sub / cd;
+          D[at] = cd; U1[at] = cu1; U2[at] = 0.0; Lm[at] = mult; PV[at] = 0.0;
+          cd = nd - mult * cu1;
+          cu1 = nu;
+        } else {
+          const double mult = cd / sub;
+          D[at] = sub; U1[at] = nd; U2[at] = nu; Lm[at] = mult; PV[at] = 1.0;
+          cd = cu1 - mult * nd;
+          cu1 = -mult * nu;
+        }
+      }
+      if (cd == 0.0) cd = tiny;
+      D[(size_t)(m - 1) * k + c] = cd;
+      // start vector: deterministic, distinct per vector
+      for (int i = 0; i < m; i++) {
+        const unsigned h = (unsigned)(i * 2654435761u) ^ (unsigned)((c + 1) * 40503u);
+        Q[(size_t)c * m + i] = 1.0 + 0.25 * (double)((h >> 8) & 1023) / 1024.0;
+      }
+    }
+  }
+  __syncthreads();
+  for (int it = 0; it < INV_ITERS; it++) {
+    for (int c0 = 0; c0 < k; c0 += VEC_TPB) {
+      const int c = c0 + threadIdx.x;
+      if (c < k) {
+        double* v = Q + (size_t)c * m;
+        // forward: apply the row operations
+        for (int i = 0; i < m - 1; i++) {
+          const size_t at = (size_t)i * k + c;
+          if (PV[at] != 0.0) {
+            const double t = v[i];
+            v[i] = v[i + 1];
+            v[i + 1] = t - Lm[at] * v[i];
+          } else {
+            v[i + 1] -= Lm[at] * v[i];
+          }
+        }
+        // backward substitution with U (three diagonals), tracking the largest entry
+        double x2 = 0.0, x1 = 0.0, mx = 0.0;
+        for (int i = m - 1; i >= 0; i--) {
+          const size_t at = (size_t)i * k + c;
+          const double xi = (v[i] - U1[at] * x1 - U2[at] * x2) / D[at];
+          v[i] = xi;
+          mx = fmax(mx, fabs(xi));
+          x2 = x1;
+          x1 = xi;
+        }
+        // scale by the largest entry (no overflow), then to unit 2-norm
+        const double s = (mx > 0.0) ? 1.0 / mx : 1.0;
+        double nrm = 0.0;
+        for (int i = 0; i < m; i++) {
+          const double t = v[i] * s;
+          v[i] = t;
+          nrm += t * t;
+        }
+        const double inv = (nrm > 0.0) ? 1.0 / sqrt(nrm) : 1.0;
+        for (int i = 0; i < m; i++) v[i] *= inv;
+      }
+    }
+    __syncthreads();
+    // orthogonalise inside clusters (theta ascending on input; a cluster is a chain of
+    // consecutive values closer than ortol), modified Gram-Schmidt, then renormalise
+    for (int c = 1; c < k; c++) {
+      if (!(fabs(theta[c] - theta[c - 1]) <= ortol)) continue;
+      double* v = Q + (size_t)c * m;
+      int p0 = c - 1;  // first member of c's cluster
+      while (p0 > 0 && fabs(theta[p0] - theta[p0 - 1]) <= ortol) p0--;
+      for (int p = c - 1; p >= p0; p--) {
+        const double* w = Q + (size_t)p * m;
+        double sdot = 0.0;
+        for (int i = threadIdx.x; i < m; i += VEC_TPB) sdot += w[i] * v[i];
+        const double dp = vec_block_sum(sdot, red);
+        for (int i = threadIdx.x; i < m; i += VEC_TPB) v[i] -= dp * w[i];
+        __syncthreads();
+      }
+      double sn = 0.0;
+      for (int i = threadIdx.x; i < m; i += VEC_TPB) sn += v[i] * v[i];
+      const double nn = vec_block_sum(sn, red);
+      const double sc = (nn > 0.0) ? 1.0 / sqrt(nn) : 1.0;
+      for (int i = threadIdx.x; i < m; i += VEC_TPB) v[i] *= sc;
+      __syncthreads();
+    }
+  }
+  // sign: largest-magnitude component positive (owner thread)
+  for (int c0 = 0; c0 < k; c0 += VEC_TPB) {
+    const int c = c0 + threadIdx.x;
+    if (c < k) {
+      double* v = Q + (size_t)c * m;
+      double best = 0.0;
+      int bi = 0;
+      for (int i = 0; i < m; i++)
+        if (fabs(v[i]) > best) { best = fabs(v[i]); bi = i; }
+      if (v[bi] < 0.0)
+        for (int i = 0; i < m; i++) v[i] = -v[i];
+    }
+  }
+}
+
+cudaError_t launch_tridiag_eigvecs(int m, const double* delta, const double* eta, int k,
+                                   const double* theta_sel, double* Q, double* work, cudaStream_t st) {
+  if (m <= 0 || k <= 0) return cudaSuccess;
+  k_tridiag_eigvecs<<<1, VEC_TPB, 0, st>>>(m, delta, eta, k, theta_sel, Q, work);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Ritz vectors: F[j][c] = (-1)^j Q[j, c] / sqrt(rho_j) / sqrt|theta_c|, Y = Z F
+// ------------------------------------------------------------------------------------
+__global__ void k_ritz_coeffs(int m, int k, const double* Q, const double* rho, const double* tsel, double* F) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * k) return;
+  const int j = e % m, c = e / m;
+  const double sgn = (j & 1) ? -1.0 : 1.0;
+  F[(size_t)j * k + c] = sgn * Q[(size_t)c * m + j] / sqrt(rho[j]) / sqrt(fabs(tsel[c]));
+}
+
+constexpr int RITZ_COLS = 8;
+constexpr int RITZ_JCHUNK = 256;
+
+__global__ void __launch_bounds__(256) k_ritz_gemm(int64_t n, int64_t ld, int m, int k, const double* __restrict__ Z,
+                                                   const double* __restrict__ F, double* __restrict__ Y) {
+  __shared__ double sF[RITZ_JCHUNK][RITZ_COLS];
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int cb = blockIdx.y * RITZ_COLS;
+  const int nk = min(RITZ_COLS, k - cb);
+  double acc[RITZ_COLS];
+#pragma unroll
+  for (int q = 0; q < RITZ_COLS; q++) acc[q] = 0.0;
+  for (int j0 = 0; j0 < m; j0 += RITZ_JCHUNK) {
+    const int jl = min(RITZ_JCHUNK, m - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < jl * RITZ_COLS; e += blockDim.x) {
+      const int jj = e / RITZ_COLS, q = e % RITZ_COLS;
+      sF[jj][q] = (q < nk) ? F[(size_t)(j0 + jj) * k + cb + q] : 0.0;
+    }
+    __syncthreads();
+    if (row < n) {
+      for (int jj = 0; jj < jl; jj++) {
+        const double z = Z[(int64_t)(j0 + jj) * ld + row];
+#pragma unroll
+        for (int q = 0; q < RITZ_COLS; q++) acc[q] += z * sF[jj][q];
+      }
+    }
+  }
+  if (row < n) {
+#pragma unroll
+    for (int q = 0; q < RITZ_COLS; q++)
+      if (q < nk) Y[(int64_t)(cb + q) * ld + row] = acc[q];
+  }
+}
+
+cudaError_t launch_ritz_vectors(int64_t n, int64_t ld, int m, int k, const double* Z, const double* rho,
+                                const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st) {
+  if (k <= 0 || m <= 0) return cudaSuccess;
+  k_ritz_coeffs<<<(m * k + 255) / 256, 256, 0, st>>>(m, k, Q, rho, tsel, F);
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)((k + RITZ_COLS - 1) / RITZ_COLS));
+  k_ritz_gemm<<<grid, 256, 0, st>>>(n, ld, m, k, Z, F, Y);
+  return cudaGetLastError();
+}
+
+}  // namespace krs

@@ -1,0 +1,94 @@
+// krs_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace krs {
+
+// Everything the iteration kernels need (device pointers, sizes, partition).
+struct IterArgs {
+  int64_t n, ld;
+  int nbr, npc, P;
+  int nc, ldg;
+  int max_iter, reorth_full, precond;
+  int kmax;  // largest k a tall-skinny phase sees: max(nc, max_iter)
+  double tol2;
+  long long spin_limit;
+  const int* rp;
+  const int* ci;
+  const double* vals;
+  const double* minv;
+  const double* C;
+  const double* AC;
+  const double* Ginv;
+  double *W, *AW, *Z, *x, *r, *u;
+  double *alpha, *gamma, *rho;
+  double *tfull, *sfull, *gfull;
+  double* part;
+  double* vpart;
+  int64_t vld;
+  int* ctrl;
+  unsigned long long* bar;
+};
+
+// krs_apcg.cu
+size_t apcg_smem_bytes(int kmax);
+cudaError_t apcg_prepare_attributes(int kmax);
+cudaError_t apcg_max_coresident(int kmax, int* blocks_per_sm);
+cudaError_t apcg_launch_init(const IterArgs& a, const double* b, double* scal, cudaStream_t st,
+                             int64_t* launches);
+cudaError_t apcg_launch_persistent(const IterArgs& a, cudaStream_t st, int64_t* launches);
+cudaError_t apcg_launch_phases(const IterArgs& a, int j0, int j1, cudaStream_t st, int64_t* launches);
+
+// krs_kernels.cu
+cudaError_t launch_spmv(int nbr, const int* rp, const int* ci, const double* vals, const double* x,
+                        double* y, cudaStream_t st);
+cudaError_t launch_precond_setup(int kind, int nbr, const int* rp, const int* ci, const double* vals,
+                                 double* minv, int* status, cudaStream_t st);
+cudaError_t launch_precond_apply(int kind, int nbr, const double* minv, const double* r, double* u,
+                                 cudaStream_t st);
+// AC[:, c0:c1] = A C[:, c0:c1]  (column-major, leading dimension ld, same summation order
+// as the iteration's operator product)
+cudaError_t launch_spmm(int nbr, const int* rp, const int* ci, const double* vals, const double* C,
+                        double* AC, int64_t ld, int c0, int c1, cudaStream_t st);
+// G[p, q] = C[:, p] . AC[:, q] for q in [q0, nc), p <= q, mirrored (G: nc x nc, ldg)
+cudaError_t launch_gram(int64_t n, const double* C, const double* AC, int64_t ld, int nc, int q0,
+                        double* G, int ldg, double* scratch, size_t scratch_doubles, cudaStream_t st);
+size_t gram_scratch_doubles(int64_t n, int nc, int q0);
+// Ginv = G^-1 via Cholesky (L in Lwork); status <- KRS_ERR_NOT_SPD on failure
+cudaError_t launch_chol_inverse(int nc, const double* G, int ldg, double* Lwork, double* Ginv,
+                                int* status, cudaStream_t st);
+// res2 = ||b - A x||^2 (scal[0]); uses tmp (n doubles)
+cudaError_t launch_true_residual(int nbr, const int* rp, const int* ci, const double* vals,
+                                 const double* x, const double* b, double* tmp, double* part,
+                                 double* out, cudaStream_t st);
+// tall-skinny products over general rows (CTA b owns rows [b*rpc, (b+1)*rpc), rpc % 4 == 0)
+cudaError_t launch_gemv_t_rows(int64_t n, int k, const double* V, int64_t ldv, const double* u, double* t,
+                               double* vpart, int P, int64_t rpc, cudaStream_t st);
+cudaError_t launch_gemv_n_rows(int64_t n, int k, const double* V, int64_t ldv, const double* s, const double* u,
+                               double* z, int P, int64_t rpc, cudaStream_t st);
+cudaError_t launch_norm2(int64_t n, const double* v, double* part, double* out, cudaStream_t st);
+cudaError_t launch_axpy2_dot(int64_t n, const double* alpha, const double* w, const double* q, double* x,
+                             double* r, double* rr, double* part, cudaStream_t st);
+// copy a host/device n-vector into a padded device column (ld >= n)
+cudaError_t launch_fill_zero(double* p, int64_t count, cudaStream_t st);
+
+// krs_eig.cu
+// delta/eta of H_m from alpha, rho (Section 4.1)
+cudaError_t launch_lanczos(int m, const double* alpha, const double* rho, double* delta, double* eta,
+                           cudaStream_t st);
+cudaError_t launch_tridiag_eigvals(int m, const double* delta, const double* eta, double* theta,
+                                   cudaStream_t st);
+cudaError_t launch_tridiag_eigvecs(int m, const double* delta, const double* eta, int k,
+                                   const double* theta_sel, double* Q, double* work, cudaStream_t st);
+size_t eigvecs_work_doubles(int m, int k);
+// SRKS selection on device: sel[0..cnt) (ascending theta), cnt in *count, theta values in tsel
+cudaError_t launch_srks_select(int m, const double* theta_m, const double* theta_m1, double eps,
+                               double theta_frac, int room, int* sel, int* count, double* tsel,
+                               cudaStream_t st);
+// Y[:, c] = sum_j Z[:, j] (-1)^j Q[j, c] / sqrt(rho_j) / sqrt|theta_c|  for c < k
+cudaError_t launch_ritz_vectors(int64_t n, int64_t ld, int m, int k, const double* Z, const double* rho,
+                                const double* Q, const double* tsel, double* F, double* Y,
+                                cudaStream_t st);
+
+}  // namespace krs

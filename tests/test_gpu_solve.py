@@ -1,0 +1,272 @@
+"""Whole solves through the C ABI against the FP64 oracle (lock-step), statuses and edge
+cases.  Bar: iterations within +-2, relative solution difference <= 1e-9 at equal
+iteration counts (the oracle is rerun for the GPU's count when they differ)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1301_7530_gb300 import binding as B
+from paper_1301_7530_gb300 import problems as P
+
+from .lockstep import check_pair, rel, solve_pair
+
+pytestmark = pytest.mark.gpu
+
+
+def test_trks_fixed_matrix_sequence(gpu_lib):
+    """8^3 cube (1,944 dofs), Jacobi, tol 1e-8, TRKS, 10 seeded traction systems."""
+    A, bs = P.elasticity_sequence_fixed(8, 10, 1000)
+    seq = B.Sequence(A.n)
+    pol = B.make_policy("trks", "jacobi", max_iter=2000)
+    ms = []
+    for k, b in enumerate(bs):
+        x, st, xo, so, ora, C = solve_pair(seq, A, b, 1e-8, pol, version=1)
+        check_pair(A, b, 1e-8, pol, x, st, xo, so, C)
+        assert st["n_c_after"] == st["n_c"] + st["m"]
+        assert st["true_rel_res"] <= 2e-8
+        ms.append(st["m"])
+    assert ms[-1] < ms[0] / 2  # recycling cuts the iteration count (Section 5, Table 1)
+    # the appended directions are the solve's W exactly (Algorithm 2)
+    W = seq.last_vectors("W")
+    C = seq.export_space()
+    assert np.array_equal(C[:, -W.shape[1]:], W)
+
+
+@pytest.mark.parametrize("eps,frac", [(1e-6, 0.1), (1e-10, 0.0)])
+def test_srks_damage_sequence(gpu_lib, eps, frac):
+    """Damage sequence on a 6^3 cube, block Jacobi, SRKS; lock-step with the oracle; the
+    Ritz values match the oracle's and the GPU's selection follows Eq. 16 on its values."""
+    N = 6
+    mask, b, gen = P.elasticity_sequence_damage(N, 6, 11, 2000)
+    seq = B.Sequence(3 * N * (N + 1) ** 2)
+    pol = B.make_policy("srks", "block_jacobi3", ritz_eps=eps, theta_frac=frac, max_aug=60)
+    total_sel = 0
+    for k, Ak in gen:
+        x, st, xo, so, ora, C = solve_pair(seq, Ak, b, 1e-8, pol, version=k + 1)
+        check_pair(Ak, b, 1e-8, pol, x, st, xo, so, C)
+        tm, tm1, sel = seq.last_ritz()
+        otm, otm1, osel, oY = ora.ritz()
+        if st["m"] == so["m"] and st["m"] >= 2:
+            assert np.allclose(tm, otm, atol=1e-11 * otm[0])
+            assert np.allclose(tm1, otm1, atol=1e-11 * otm[0])
+            assert list(O.srks_select(tm, tm1, eps, frac, 60 - st["n_c"])) == list(sel)
+            if list(sel) == list(osel) and len(sel):
+                Yg = seq.export_space()[:, st["n_c"]:]
+                for c in range(len(sel)):
+                    th = tm[sel[c]]
+                    gap = np.min(np.abs(np.delete(tm, sel[c]) - th))
+                    if gap > 1e-3 * tm[0]:
+                        a, bb = Yg[:, c], oY[:, c]
+                        assert min(rel(a, bb), rel(a, -bb)) <= 1e-6
+        total_sel += st["n_selected"]
+        assert st["n_c_after"] <= 60
+    assert total_sel > 0
+
+
+def test_exec_modes_bitwise_equal(gpu_lib):
+    """The persistent kernel and the per-phase kernels compute the same bits."""
+    N = 5
+    mask, b, gen = P.elasticity_sequence_damage(N, 3, 5, 2001)
+    mats = [Ak for _, Ak in gen]
+    res = {}
+    for mode in ("persistent", "kernels"):
+        seq = B.Sequence(3 * N * (N + 1) ** 2)
+        pol = B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, exec=mode)
+        xs = []
+        for k, Ak in enumerate(mats):
+            x, st = seq.solve(Ak, b, 1e-9, pol, version=k + 1)
+            xs.append((x.copy(), st["m"], st["n_c_after"]))
+        res[mode] = (xs, seq.export_space())
+    for (xa, ma, na), (xb, mb, nb) in zip(res["persistent"][0], res["kernels"][0]):
+        assert ma == mb and na == nb and np.array_equal(xa, xb)
+    assert np.array_equal(res["persistent"][1], res["kernels"][1])
+
+
+def test_no_reorth_matches_oracle(gpu_lib):
+    A, bs = P.elasticity_sequence_fixed(5, 1, 3000)
+    seq = B.Sequence(A.n)
+    pol = B.make_policy("none", "jacobi", reorth="none")
+    x, st, xo, so, ora, C = solve_pair(seq, A, bs[0], 1e-8, pol, version=1)
+    check_pair(A, bs[0], 1e-8, pol, x, st, xo, so, C)
+
+
+def test_imported_space_and_identity_precond(gpu_lib):
+    A, bs = P.elasticity_sequence_fixed(4, 1, 77)
+    rng = np.random.default_rng(1)
+    C = rng.standard_normal((A.n, 7))
+    seq = B.Sequence(A.n)
+    seq.import_space(C)
+    assert np.array_equal(seq.export_space(), C)
+    pol = B.make_policy("none", "identity")
+    x, st, xo, so, ora, C2 = solve_pair(seq, A, bs[0], 1e-9, pol, version=1)
+    check_pair(A, bs[0], 1e-9, pol, x, st, xo, so, C2)
+    r = bs[0] - A.to_scipy() @ x
+    assert np.abs(C.T @ r).max() <= 1e-10 * np.linalg.norm(C, 2) * np.linalg.norm(bs[0])
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 7])
+def test_small_and_ragged_sizes(gpu_lib, N):
+    """Tiny systems (one CTA) and node counts that leave a ragged last CTA."""
+    A, bs = P.elasticity_sequence_fixed(N, 2, 50 + N)
+    seq = B.Sequence(A.n)
+    pol = B.make_policy("trks", "block_jacobi3")
+    for b in bs:
+        x, st, xo, so, ora, C = solve_pair(seq, A, b, 1e-10, pol, version=1)
+        check_pair(A, b, 1e-10, pol, x, st, xo, so, C)
+
+
+def test_device_pointers_in_and_out(gpu_lib):
+    import torch
+    A, bs = P.elasticity_sequence_fixed(4, 1, 9)
+    seq = B.Sequence(A.n)
+    pol = B.make_policy("none", "jacobi")
+    xh, sth = seq.solve(A, bs[0], 1e-9, pol, version=1)
+    bd = torch.as_tensor(bs[0], device="cuda")
+    Ad = {"row_ptr": torch.as_tensor(A.row_ptr, device="cuda"), "col_idx": torch.as_tensor(A.col_idx, device="cuda"),
+          "values": torch.as_tensor(A.vals, device="cuda").reshape(-1)}
+    seq2 = B.Sequence(A.n)
+    xd, std = seq2.solve(Ad, bd, 1e-9, pol, version=1)
+    torch.cuda.synchronize()
+    assert std["m"] == sth["m"] and np.array_equal(xd.cpu().numpy(), xh)
+
+
+def test_zero_rhs_and_m0(gpu_lib):
+    A, bs = P.elasticity_sequence_fixed(3, 1, 1)
+    seq = B.Sequence(A.n)
+    x, st = seq.solve(A, np.zeros(A.n), 1e-8, B.make_policy("trks"), version=1)
+    assert st["status"] == 0 and st["m"] == 0 and np.all(x == 0) and seq.nc == 0
+
+
+def test_trks_repeated_rhs_converges_at_init(gpu_lib):
+    A, bs = P.elasticity_sequence_fixed(4, 2, 31)
+    seq = B.Sequence(A.n)
+    pol = B.make_policy("trks", "jacobi")
+    seq.solve(A, bs[0], 1e-10, pol, version=1)
+    seq.solve(A, bs[1], 1e-10, pol, version=1)
+    Ad = A.to_dense()
+    b2 = 2.0 * bs[0] - 0.5 * bs[1]
+    tol2 = 1e-10 * np.sqrt(np.linalg.cond(Ad)) * (2 * np.linalg.norm(bs[0]) + 0.5 * np.linalg.norm(bs[1])) / np.linalg.norm(b2)
+    x, st = seq.solve(A, b2, tol2, pol, version=1)
+    assert st["m"] == 0 and st["true_rel_res"] <= tol2
+
+
+# ---------------------------------------------------------------------------------------
+# statuses (failures made on the host side or by bounded device waits; nothing faults)
+# ---------------------------------------------------------------------------------------
+
+def test_status_not_spd_matrix(gpu_lib):
+    A, bs = P.elasticity_sequence_fixed(3, 1, 5)
+    i = list(A.col_idx[A.row_ptr[2]:A.row_ptr[3]]).index(2)
+    A.vals[A.row_ptr[2] + i] *= -1.0
+    seq = B.Sequence(A.n)
+    x, st = seq.solve(A, bs[0], 1e-8, B.make_policy("none", "jacobi"), version=1, raise_on_error=False)
+    assert st["status"] == B.ERR_NOT_SPD
+
+
+def test_status_rank_deficient_space(gpu_lib):
+    n = 12
+    lam = np.arange(1.0, n + 1)
+    lam[0] = 4.0
+    A = P.BSR3(np.arange(5, dtype=np.int32), np.arange(4, dtype=np.int32),
+               np.stack([np.diag(lam[3 * i:3 * i + 3]) for i in range(4)]))
+    seq = B.Sequence(n)
+    C = np.zeros((n, 2))
+    C[0, 0] = C[0, 1] = 1.0  # duplicated column; G = [[4, 4], [4, 4]] exactly
+    seq.import_space(C)
+    x, st = seq.solve(A, np.ones(n), 1e-8, B.make_policy("none", "identity"), version=1, raise_on_error=False)
+    assert st["status"] == B.ERR_NOT_SPD
+    assert seq.nc == 2
+
+
+def test_status_nan_rhs(gpu_lib):
+    A, bs = P.elasticity_sequence_fixed(3, 1, 6)
+    b = bs[0].copy()
+    b[4] = np.nan
+    seq = B.Sequence(A.n)
+    x, st = seq.solve(A, b, 1e-8, B.make_policy(), version=1, raise_on_error=False)
+    assert st["status"] == B.ERR_INVALID_ARG
+
+
+def test_status_no_convergence_keeps_space(gpu_lib):
+    A, bs = P.elasticity_sequence_fixed(4, 2, 7)
+    seq = B.Sequence(A.n)
+    seq.solve(A, bs[0], 1e-6, B.make_policy("trks", "jacobi"), version=1)
+    C0 = seq.export_space()
+    for mode in ("persistent", "kernels"):
+        x, st = seq.solve(A, bs[1], 1e-14, B.make_policy("trks", "jacobi", max_iter=3, exec=mode), version=1,
+                          raise_on_error=False)
+        assert st["status"] == B.ERR_NO_CONVERGENCE and st["m"] == 3
+        assert np.array_equal(seq.export_space(), C0)
+        assert np.all(np.isfinite(x))
+
+
+def test_status_barrier_timeout_is_reported(gpu_lib):
+    """A spin limit of one poll makes the persistent kernel's grid barrier give up; the
+    kernel returns KRS_ERR_TIMEOUT and the context stays usable."""
+    A, bs = P.elasticity_sequence_fixed(6, 1, 8)
+    seq = B.Sequence(A.n)
+    seq.set_spin_limit(1)
+    x, st = seq.solve(A, bs[0], 1e-8, B.make_policy("none", "jacobi"), version=1, raise_on_error=False)
+    assert st["status"] in (B.ERR_TIMEOUT, B.OK)
+    seq.set_spin_limit(0)
+    x, st = seq.solve(A, bs[0], 1e-8, B.make_policy("none", "jacobi"), version=1)
+    assert st["status"] == 0
+    xo, so = O.Sequence(A.n).solve(A, bs[0], 1e-8, O.make_policy("none", "jacobi"))
+    assert abs(st["m"] - so["m"]) <= 2
+
+
+def test_allocator_failure_is_oom(gpu_lib):
+    calls = {"n": 0}
+
+    def bad_alloc(size, ctx):
+        calls["n"] += 1
+        return None
+
+    def nop_free(p, ctx):
+        pass
+
+    with pytest.raises(B.KrsError) as ei:
+        B.Sequence(300, alloc_fn=B.ALLOC_FN(bad_alloc), free_fn=B.FREE_FN(nop_free))
+    assert ei.value.status == B.ERR_OOM and calls["n"] >= 1
+
+
+def test_invalid_arguments(gpu_lib):
+    A, bs = P.elasticity_sequence_fixed(2, 1, 1)
+    seq = B.Sequence(A.n)
+    with pytest.raises(B.KrsError):
+        seq.solve(A, bs[0], -1.0, B.make_policy(), version=1)
+    with pytest.raises(B.KrsError):
+        seq.solve(A, bs[0], 1e-8, B.make_policy(max_iter=0), version=1)
+    with pytest.raises(B.KrsError):
+        seq.solve(A, bs[0], 1e-8, B.make_policy(precision="mixed_ir"), version=1)
+    A3, _ = P.elasticity_sequence_fixed(3, 1, 1)
+    with pytest.raises(B.KrsError):
+        seq.solve(A3, np.zeros(A3.n), 1e-8, B.make_policy(), version=2)
+
+
+# ---------------------------------------------------------------------------------------
+# full size of the benchmark workload (32^3 damage sequence, 104,544 dofs)
+# ---------------------------------------------------------------------------------------
+
+def test_full_size_first_solve_and_sequence_properties(gpu_lib):
+    """First system of the 32^3 damage sequence against the oracle (C = 0); then three
+    more GPU solves checked by properties that hold at any size: true residual, the
+    augmentation cap, C^T r = 0 for the returned x."""
+    N = 32
+    mask, b, gen = P.elasticity_sequence_damage(N, 20, 2000, 2000)
+    seq = B.Sequence(3 * N * (N + 1) ** 2)
+    pol = B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, theta_frac=0.1, max_aug=200)
+    k, A0 = next(gen)
+    x, st, xo, so, ora, C = solve_pair(seq, A0, b, 1e-8, pol, version=1)
+    check_pair(A0, b, 1e-8, pol, x, st, xo, so, C)
+    for k, Ak in gen:
+        if k > 3:
+            break
+        Cb = seq.export_space()
+        x, st = seq.solve(Ak, b, 1e-8, pol, version=k + 1)
+        assert st["true_rel_res"] <= 1e-7
+        r = b - Ak.to_scipy() @ x
+        if Cb.shape[1]:
+            AC = Ak.to_scipy() @ Cb
+            assert np.abs(Cb.T @ r).max() <= 1e-9 * np.linalg.norm(Cb, axis=0).max() * np.linalg.norm(b) * np.sqrt(Cb.shape[1])
+        assert seq.nc <= 200
