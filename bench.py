@@ -1,0 +1,444 @@
+#!/usr/bin/env python3
+"""Benchmark: solves/s and p50/p99 latency at relative residual 1e-8, and the achieved
+throughput of the dominant kernel (the persistent APCG iteration kernel) against its roof.
+
+Workload (one "step"): the 32^3 Q1 elasticity damage sequence -- 20 secant systems on
+104,544 FP64 dofs in 3x3 BSR; elements inside a seeded ellipsoid get E * d_k,
+d_k = 0.05^(k/19); fixed seeded traction right-hand side; block-Jacobi preconditioner;
+SRKS (Algorithm 3) with theta < 0.1 theta_max, at most 200 augmentation vectors, starting
+from an empty augmentation space.  All 20 matrices are resident on the device when the
+timed region starts (1.35 GB per step, larger than L2).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl krs|reference]
+
+Multi-GPU (torchrun): every rank solves its own sequence (independent problems, no data
+collective); value = all ranks' solves / the slowest rank's time ("weak" scaling).
+--impl reference times the FP64 CPU oracle (rank 0 only) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1301_7530_gb300 import problems as P  # noqa: E402
+
+METRIC = "solves/s and p50/p99 latency at rel. residual 1e-8; SpMV+proj HBM GB/s vs 8 TB/s"
+UNIT = "solves/s"
+TOL = 1e-8
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "apcg_persistent_32cube_damage_fp64.md")
+CSRC = os.path.join(ROOT, "paper_1301_7530_gb300", "csrc")
+
+# FP64 ALU roof of GB300: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz
+# (NVIDIA's 1.25 TFLOP/s FP64 figure; the unit count measured 1.9 FMA/clk/SM).
+SMS, FP64_FMA_PER_CLK_SM, SM_MAX_MHZ = 152, 2, 2070.0
+FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["krs", "reference"], default="krs")
+    ap.add_argument("--N", type=int, default=32)
+    ap.add_argument("--systems", type=int, default=20)
+    ap.add_argument("--exec", choices=["persistent", "kernels"], default="persistent")
+    ap.add_argument("--ritz-eps", type=float, default=1e-6)
+    ap.add_argument("--theta-frac", type=float, default=0.1)
+    ap.add_argument("--max-aug", type=int, default=200)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--max-iter", type=int, default=2000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------------------
+# distributed plumbing
+# ----------------------------------------------------------------------------------------
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def all_max(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def all_sum(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------------------
+
+def workload(N, systems, rank):
+    mask, b, gen = P.elasticity_sequence_damage(N, systems, 2000, 2000 + rank)
+    mats = [A for _, A in gen]
+    return mats, b
+
+
+def alg_counts(N, precond_bytes_per_dof, m, nc):
+    """Algorithmic FP64 flops and bytes of one launch of the iteration kernel
+    (m iterations, augmentation size nc); see the design doc for the derivation."""
+    s = P.sizes(N)
+    n, nb, nodes = s["n"], s["nb"], s["free_nodes"]
+    flops = 0.0
+    byts = 0.0
+    for j in range(m):
+        # P1-P2 (every iteration): SpMV, (w,q), (r,w), x/r update, (r,r), M^-1 r, (AC)^T u
+        flops += 18 * nb + 4 * n + 6 * n + 6 * n + 2 * n * nc
+        byts += 76 * nb + 4 * (nodes + 1) + precond_bytes_per_dof * n + 8 * n * nc + 48 * n
+        if j < m - 1:
+            # P4-P7: s = G^-1 t, z = u - C s, (r,z), g = (AW)^T z, w = z - W g
+            flops += 2 * nc * nc + 2 * n * nc + 2 * n + 4 * n * (j + 1)
+            byts += 8 * n * nc + 16 * n * (j + 1) + 16 * n
+    return flops, byts
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def csrc_digest():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None, None
+    txt = open(PROFILE_SUMMARY).read()
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "algorithmic_bytes_per_launch",
+                                                    "csrc_sha256")):
+            k, v = line.strip().split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("csrc_sha256") != csrc_digest():
+        return None, None
+    try:
+        return float(vals["traffic_bytes_per_launch"]), float(vals["algorithmic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None, None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index, enabled=True):
+        self.proc = None
+        self.path = None
+        if not enabled:
+            return
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="krs_clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = [nm for i, nm in enumerate(names) if any(r[5 + i].lower().startswith("active") for r in rows)]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------------------
+# the GPU arm
+# ----------------------------------------------------------------------------------------
+
+def run_krs(args, rank, world, local):
+    import torch
+    from paper_1301_7530_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    mats, b = workload(args.N, args.systems, rank)
+    n = mats[0].n
+    # device-resident inputs
+    dmats = []
+    for A in mats:
+        dmats.append({"row_ptr": torch.as_tensor(A.row_ptr, device=dev),
+                      "col_idx": torch.as_tensor(A.col_idx, device=dev),
+                      "values": torch.as_tensor(A.vals, device=dev).reshape(-1)})
+    b_d = torch.as_tensor(b, device=dev)
+    x_d = torch.zeros(n, dtype=torch.float64, device=dev)
+    pol = B.make_policy("srks", "block_jacobi3", ritz_eps=args.ritz_eps, theta_frac=args.theta_frac,
+                        max_aug=args.max_aug, max_iter=args.max_iter, exec=args.exec)
+    seq = B.Sequence(n, device=local, stream=stream)
+
+    def one_step(record=None, lat=None):
+        seq.import_space(np.zeros((n, 0)))
+        for k, Ad in enumerate(dmats):
+            t0 = time.perf_counter()
+            _, st = seq.solve(Ad, b_d, TOL, pol, x=x_d, version=k + 1)
+            if lat is not None:
+                lat.append((time.perf_counter() - t0) * 1e3)
+            if st["status"] != 0:
+                raise RuntimeError(f"solve {k} failed: {st}")
+            if record is not None:
+                record.append(st)
+
+    for _ in range(args.warmup):
+        one_step()
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        try:
+            gpu_index = int(cvd.split(",")[local])
+        except (ValueError, IndexError):
+            gpu_index = local
+    stats, lat = [], []
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_index, enabled=not args.no_clocks)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one_step(stats, lat)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = all_max(ms, world)
+    solves = args.steps * args.systems
+    total_solves = all_sum(solves, world)
+    value = total_solves / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (persistent iteration kernel)
+    flops = byts = t_iter = 0.0
+    for st in stats:
+        f, bb = alg_counts(args.N, 24, st["m"], st["n_c"])
+        flops += f
+        byts += bb
+        t_iter += st["t_iter_ms"]
+    launches = sum(1 for st in stats if st["m"] > 0)
+    achieved_tflops = flops / (t_iter / 1e3) / 1e12
+    achieved_gbs = byts / (t_iter / 1e3) / 1e9
+    hbm_peak, hbm_kind = measured_peaks()
+    traffic, traffic_alg = profiled_traffic()
+    iter_share = t_iter / ms
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pin = []
+        for A in mats:
+            rp = torch.as_tensor(A.row_ptr).pin_memory()
+            ci = torch.as_tensor(A.col_idx).pin_memory()
+            vv = torch.as_tensor(A.vals).pin_memory()
+            pin.append(P.BSR3(rp.numpy(), ci.numpy(), vv.numpy()))
+        b_h = torch.as_tensor(b).pin_memory().numpy()
+        x_h = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+        seq2 = B.Sequence(n, device=local, stream=stream)
+
+        def host_step():
+            seq2.import_space(np.zeros((n, 0)))
+            for k, A in enumerate(pin):
+                _, st = seq2.solve(A, b_h, TOL, pol, x=x_h, version=k + 1)
+                if st["status"] != 0:
+                    raise RuntimeError(f"e2e solve {k} failed: {st}")
+
+        host_step()  # warm-up (allocations)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            host_step()
+        torch.cuda.synchronize()
+        e_ms = all_max((time.perf_counter() - t0) * 1e3, world)
+        e_solves = all_sum(args.e2e_steps * args.systems, world)
+        s0 = P.sizes(args.N)
+        h2d = sum(4 * (A.n_block_rows + 1) + 4 * A.nnzb + 72 * A.nnzb + 8 * n for A in mats)
+        d2h = 8 * n * len(mats)
+        e2e = {"value": e_solves / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps, "n": s0["n"]}
+        seq2.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mats, b)
+
+    if rank == 0:
+        ms_per_step = ms_max / args.steps
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {
+                "workload": f"{args.N}^3 Q1 elasticity damage sequence, {args.systems} systems per step, SRKS",
+                "n": n, "nnzb": mats[0].nnzb, "systems_per_step": args.systems, "precond": "block_jacobi3",
+                "recycle": "srks", "ritz_eps": args.ritz_eps, "theta_frac": args.theta_frac,
+                "max_aug": args.max_aug, "tol": TOL, "exec": args.exec, "reorth": "full",
+                "parallelism": f"{world} independent sequence(s), one per GPU",
+                "l2": "inputs larger than L2: 20 resident matrices, 1.35 GB per step"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(np.mean(lat))},
+            "solves": {"m_mean": float(np.mean([s["m"] for s in stats])),
+                       "n_c_mean": float(np.mean([s["n_c"] for s in stats])),
+                       "n_c_max": int(max(s["n_c_after"] for s in stats)),
+                       "true_rel_res_max": float(max(s["true_rel_res"] for s in stats)),
+                       "t_setup_ms_mean": float(np.mean([s["t_setup_ms"] for s in stats])),
+                       "t_iter_ms_mean": float(np.mean([s["t_iter_ms"] for s in stats])),
+                       "t_recycle_ms_mean": float(np.mean([s["t_recycle_ms"] for s in stats]))},
+            "roofline": {"kernel": "k_apcg_persistent", "bound": "alu", "achieved": achieved_tflops,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                         "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                         "traffic": traffic, "traffic_alg_bytes": traffic_alg,
+                         "launches": launches, "share_of_step_time": iter_share},
+            "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                    "peak_kind": hbm_kind, "what": "algorithmic bytes of the iteration kernel / its time"},
+            "e2e": e2e,
+            "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    seq.close()
+
+
+# ----------------------------------------------------------------------------------------
+# the oracle: cpu_baseline of the GPU arm, and the reference arm
+# ----------------------------------------------------------------------------------------
+
+def oracle_one_solve(mats, b):
+    import oracle as O
+    s = O.Sequence(mats[0].n)
+    pol = O.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, theta_frac=0.1, max_aug=200, max_iter=2000)
+    t0 = time.perf_counter()
+    x, st = s.solve(mats[0], b, TOL, pol)
+    return time.perf_counter() - t0, st
+
+
+def cpu_baseline(mats, b):
+    sec, st = oracle_one_solve(mats, b)
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle solve (system 0 of the sequence, empty C, m = {st['m']}) "
+                      f"timed single-threaded: {sec:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    mats, b = workload(args.N, 1, 0)
+    for _ in range(args.warmup):
+        oracle_one_solve(mats, b)
+    t0 = time.perf_counter()
+    ms_list = []
+    for _ in range(args.steps):
+        sec, st = oracle_one_solve(mats, b)
+        ms_list.append(sec * 1e3)
+    total = time.perf_counter() - t0
+    value = args.steps / total
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.N}^3 Q1 elasticity damage sequence, {args.systems} systems per step, SRKS",
+                   "n": mats[0].n, "tol": TOL, "precond": "block_jacobi3", "recycle": "srks"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one FP64 oracle solve of system 0 (empty C, m = {st['m']}), "
+                                   "single-threaded"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "latency_ms": {"p50": float(np.percentile(ms_list, 50)), "p99": float(np.percentile(ms_list, 99))},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        run_reference(args, rank, world)
+        return
+    rank, world, local = dist_setup()
+    run_krs(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -58,8 +58,10 @@ typedef struct krs_seq* krs_seq_t;
 /* 3x3 block-CSR matrix (the systems of Eq. 1 / Eq. 11).
  *   row_ptr: int32[n_block_rows + 1]; col_idx: int32[nnzb], ascending within a row, the
  *   diagonal block present; values: float64[nnzb * 9], each block row-major.
- *   on_device = 1: the three arrays are device pointers (read in place, must stay valid
- *   and unchanged for the duration of the call); 0: host pointers (copied).
+ *   on_device = 1: the three arrays are device pointers, read in place (they must stay
+ *   valid and unchanged for the duration of the call) when values is 16-byte and col_idx
+ *   8-byte aligned, copied to the sequence's own buffers otherwise; 0: host pointers
+ *   (validated with krs_validate_bsr and copied).
  *   version: the sequence re-reads values (and rebuilds the preconditioner and A C) when
  *   version differs from the previous call's; the sparsity pattern must not change within
  *   a sequence unless version changes too. */
@@ -123,9 +125,11 @@ typedef struct {
   int32_t n_c_after;      /* columns of C after the recycling step */
   double rel_res;         /* ||r_m|| / ||b|| (recursive residual) */
   double true_rel_res;    /* ||b - A x|| / ||b|| recomputed on the device */
+  /* Times from CUDA events on the sequence's stream: */
   double t_setup_ms;      /* upload, preconditioner, A C, C^T A C, Cholesky, x_0, z_0 */
-  double t_iter_ms;       /* the iterations */
-  double t_recycle_ms;    /* Lanczos, eigensolve, selection, Ritz vectors, concatenation */
+  double t_iter_ms;       /* exactly the iteration kernel launch(es) */
+  double t_recycle_ms;    /* x copy-out, true residual, Lanczos, eigensolve, selection,
+                             Ritz vectors, concatenation */
   double t_total_ms;
   int64_t kernel_launches;/* kernels this library launched for the solve */
 } krs_solve_stats;

@@ -55,7 +55,8 @@ struct ApcgCtx {
   double* sfull;
   double* gfull;
   double* part;        // [P * PS_STRIDE]
-  double* vpart;       // [P * vld]
+  double* vpart;       // [P * vld]  partials of t = (AC)^T u
+  double* gpart;       // [P * vld]  partials of g = (AW)^T z (separate: no phase overlap hazard)
   int64_t vld;
   int* ctrl;
   unsigned long long* bar;
@@ -98,6 +99,23 @@ __device__ __forceinline__ double grid_scalar(const ApcgCtx& c, int slot, double
   return v;
 }
 
+// Two scalars at once (warps 0 and 1 in parallel).
+__device__ __forceinline__ void grid_scalar2(const ApcgCtx& c, int slot_a, int slot_b, double* red, double& va,
+                                             double& vb) {
+  const int warp = threadIdx.x >> 5;
+  if (warp < 2) {
+    const double v = warp_sum_strided(c.part + (warp == 0 ? slot_a : slot_b), c.P, PS_STRIDE);
+    if ((threadIdx.x & 31) == 0) red[warp] = v;
+  }
+  __syncthreads();
+  va = red[0];
+  vb = red[1];
+  __syncthreads();
+}
+
+// Augmentation sizes up to this are reduced by every CTA redundantly (no extra barriers).
+constexpr int SMALL_NC = 16;
+
 __device__ __forceinline__ void phase1(const ApcgCtx& c, int j, Smem& sm) {
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
@@ -113,8 +131,8 @@ __device__ __forceinline__ void phase1(const ApcgCtx& c, int j, Smem& sm) {
 }
 
 __device__ __forceinline__ int phase2(const ApcgCtx& c, int j, Smem& sm) {
-  const double gam = grid_scalar(c, PS_WQ, sm.red);
-  const double rws = grid_scalar(c, PS_RW, sm.red);
+  double gam, rws;
+  grid_scalar2(c, PS_WQ, PS_RW, sm.red, gam, rws);
   if (!(gam > 0.0)) {
     finish(c, 2 /* KRS_ERR_NOT_SPD */, j);
     return PH_STOP;
@@ -161,14 +179,34 @@ __device__ __forceinline__ int phase3(const ApcgCtx& c, int j, Smem& sm) {
     finish(c, 3 /* KRS_ERR_NO_CONVERGENCE */, j + 1);
     return PH_STOP;
   }
-  if (c.nc > 0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (c.nc > SMALL_NC) {
+    // slice of t reduced here; s follows in phase 4 after a barrier
     int a, e;
     col_slice(c.nc, c.P, blockIdx.x, a, e);
-    const int warp = threadIdx.x >> 5;
     for (int col = a + warp; col < e; col += TPB / 32) {
       const double v = warp_sum_strided(c.vpart + col, c.P, c.vld);
-      if ((threadIdx.x & 31) == 0) c.tfull[col] = v;
+      if (lane == 0) c.tfull[col] = v;
     }
+  } else if (c.nc > 0) {
+    // every CTA: t = sum of all partials (fixed order), s = Ginv t into shared memory
+    for (int col = warp; col < c.nc; col += TPB / 32) {
+      const double v = warp_sum_strided(c.vpart + col, c.P, c.vld);
+      if (lane == 0) sm.red[col] = v;
+    }
+    __syncthreads();
+    for (int col = warp; col < c.nc; col += TPB / 32) {
+      const double* g = c.Ginv + (int64_t)col * c.ldg;
+      double sacc = 0.0;
+      for (int k = lane; k < c.nc; k += 32) sacc += g[k] * sm.red[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) {
+        sm.sv[col] = sacc;
+        if (blockIdx.x == 0) c.sfull[col] = sacc;  // for the per-phase kernel mode
+      }
+    }
+    __syncthreads();
   }
   return PH_CONTINUE;
 }
@@ -187,12 +225,16 @@ __device__ __forceinline__ void phase4(const ApcgCtx& c) {
   }
 }
 
-__device__ __forceinline__ void phase5(const ApcgCtx& c, int j, Smem& sm) {
+// s_in_smem: s = Ginv t is already in sm.sv (small-augmentation path of phase 3 in the
+// same kernel); otherwise it is read from sfull.
+__device__ __forceinline__ void phase5(const ApcgCtx& c, int j, Smem& sm, bool s_in_smem) {
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
   double* z = c.Z + (int64_t)(j + 1) * c.ld;
   if (c.nc > 0) {
-    for (int k = threadIdx.x; k < c.nc; k += TPB) sm.sv[k] = c.sfull[k];
+    if (!s_in_smem) {
+      for (int k = threadIdx.x; k < c.nc; k += TPB) sm.sv[k] = c.sfull[k];
+    }
     __syncthreads();
     cta_gemv_n<true>(c.C, c.ld, c.nc, sm.sv, -1.0, c.u, z, r0, r1, sm.red);
   } else {
@@ -205,7 +247,7 @@ __device__ __forceinline__ void phase5(const ApcgCtx& c, int j, Smem& sm) {
   if (threadIdx.x == 0) c.part[blockIdx.x * PS_STRIDE + PS_RZ] = rz;
   const int base = c.reorth_full ? 0 : j;
   const int kk = j + 1 - base;
-  cta_gemv_t<false>(c.AW + (int64_t)base * c.ld, c.ld, kk, z, r0, r1, c.vpart + blockIdx.x * c.vld,
+  cta_gemv_t<false>(c.AW + (int64_t)base * c.ld, c.ld, kk, z, r0, r1, c.gpart + blockIdx.x * c.vld,
                     sm.su, sm.red);
 }
 
@@ -222,7 +264,7 @@ __device__ __forceinline__ int phase6(const ApcgCtx& c, int j, Smem& sm) {
   col_slice(kk, c.P, blockIdx.x, a, e);
   const int warp = threadIdx.x >> 5;
   for (int col = a + warp; col < e; col += TPB / 32) {
-    const double v = warp_sum_strided(c.vpart + col, c.P, c.vld);
+    const double v = warp_sum_strided(c.gpart + col, c.P, c.vld);
     if ((threadIdx.x & 31) == 0) c.gfull[col] = v / c.gamma[base + col];
   }
   return PH_CONTINUE;
@@ -258,12 +300,14 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx c) {
     if (phase2(c, j, sm) == PH_STOP) return;
     KRS_SYNC();
     if (phase3(c, j, sm) == PH_STOP) return;
-    if (c.nc > 0) {
+    if (c.nc > SMALL_NC) {
       KRS_SYNC();
       phase4(c);
+      KRS_SYNC();
+      phase5(c, j, sm, false);
+    } else {
+      phase5(c, j, sm, true);  // nothing written in phase 3 is read by another CTA here
     }
-    KRS_SYNC();
-    phase5(c, j, sm);
     KRS_SYNC();
     if (phase6(c, j, sm) == PH_STOP) return;
     KRS_SYNC();
@@ -293,7 +337,7 @@ KRS_PHASE_KERNEL(k_phase1, phase1(c, j, sm))
 KRS_PHASE_KERNEL(k_phase2, phase2(c, j, sm))
 KRS_PHASE_KERNEL(k_phase3, phase3(c, j, sm))
 KRS_PHASE_KERNEL(k_phase4, phase4(c))
-KRS_PHASE_KERNEL(k_phase5, phase5(c, j, sm))
+KRS_PHASE_KERNEL(k_phase5, phase5(c, j, sm, false))
 KRS_PHASE_KERNEL(k_phase6, phase6(c, j, sm))
 KRS_PHASE_KERNEL(k_phase7, phase7(c, j, sm))
 
@@ -422,7 +466,7 @@ static ApcgCtx make_ctx(const IterArgs& a) {
   c.W = a.W; c.AW = a.AW; c.Z = a.Z; c.x = a.x; c.r = a.r; c.u = a.u;
   c.alpha = a.alpha; c.gamma = a.gamma; c.rho = a.rho;
   c.tfull = a.tfull; c.sfull = a.sfull; c.gfull = a.gfull;
-  c.part = a.part; c.vpart = a.vpart; c.vld = a.vld; c.ctrl = a.ctrl; c.bar = a.bar;
+  c.part = a.part; c.vpart = a.vpart; c.gpart = a.gpart; c.vld = a.vld; c.ctrl = a.ctrl; c.bar = a.bar;
   return c;
 }
 
@@ -487,7 +531,7 @@ cudaError_t apcg_launch_phases(const IterArgs& a, int j0, int j1, cudaStream_t s
     k_phase1<<<a.P, TPB, sm, st>>>(c, j);
     k_phase2<<<a.P, TPB, sm, st>>>(c, j);
     k_phase3<<<a.P, TPB, sm, st>>>(c, j);
-    if (a.nc > 0) {
+    if (a.nc > SMALL_NC) {
       k_phase4<<<a.P, TPB, sm, st>>>(c, j);
       *launches += 1;
     }

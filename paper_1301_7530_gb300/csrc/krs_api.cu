@@ -105,6 +105,7 @@ struct krs_seq {
   double *tfull = nullptr, *sfull = nullptr, *gfull = nullptr;
   double* part = nullptr;
   double* vpart = nullptr;
+  double* gpart = nullptr;
   int64_t vld = 0;
   int vpart_P = 0;
   int* ctrl = nullptr;
@@ -262,10 +263,12 @@ static krs_status ensure_vpart(krs_seq* s, int P, int kmax) {
   const int Pn = P > s->vpart_P ? P : s->vpart_P;
   const int64_t vn = vld > s->vld ? vld : s->vld;
   dev_free(s, s->vpart);
+  dev_free(s, s->gpart);
   dev_free(s, s->part);
   dev_free(s, s->tfull);
   dev_free(s, s->sfull);
   KRS_TRY(alloc_n(s, &s->vpart, (size_t)Pn * vn));
+  KRS_TRY(alloc_n(s, &s->gpart, (size_t)Pn * vn));
   KRS_TRY(alloc_n(s, &s->part, (size_t)Pn * PS_STRIDE + 256));
   KRS_TRY(alloc_n(s, &s->tfull, vn));
   KRS_TRY(alloc_n(s, &s->sfull, vn));
@@ -538,12 +541,15 @@ static krs_status upload_matrix(krs_seq* s, const krs_bsr* A, bool* changed) {
                                   : true);
   if (same) return KRS_OK;
   *changed = true;
-  if (A->on_device) {
+  // the iteration's product reads block pairs with 16-byte loads: a caller's device matrix
+  // is used in place when values are 16-byte and col_idx 8-byte aligned, copied otherwise
+  const bool aligned = ((uintptr_t)A->values % 16 == 0) && ((uintptr_t)A->col_idx % 8 == 0);
+  if (A->on_device && aligned) {
     s->rp_use = A->row_ptr;
     s->ci_use = A->col_idx;
     s->vals_use = A->values;
   } else {
-    KRS_TRY(krs_validate_bsr(A->n_block_rows, A->nnzb, A->row_ptr, A->col_idx));
+    if (!A->on_device) KRS_TRY(krs_validate_bsr(A->n_block_rows, A->nnzb, A->row_ptr, A->col_idx));
     if (A->nnzb > s->nnzb_cap) {
       dev_free(s, s->rp);
       dev_free(s, s->ci);
@@ -556,9 +562,10 @@ static krs_status upload_matrix(krs_seq* s, const krs_bsr* A, bool* changed) {
       KRS_TRY(alloc_n(s, &s->vals, (size_t)A->nnzb * 9));
       s->nnzb_cap = A->nnzb;
     }
-    KRS_CUDA(cudaMemcpyAsync(s->rp, A->row_ptr, sizeof(int32_t) * ((size_t)s->nbr + 1), cudaMemcpyHostToDevice, s->stream));
-    KRS_CUDA(cudaMemcpyAsync(s->ci, A->col_idx, sizeof(int32_t) * (size_t)A->nnzb, cudaMemcpyHostToDevice, s->stream));
-    KRS_CUDA(cudaMemcpyAsync(s->vals, A->values, sizeof(double) * 9 * (size_t)A->nnzb, cudaMemcpyHostToDevice, s->stream));
+    const cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    KRS_CUDA(cudaMemcpyAsync(s->rp, A->row_ptr, sizeof(int32_t) * ((size_t)s->nbr + 1), kind, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(s->ci, A->col_idx, sizeof(int32_t) * (size_t)A->nnzb, kind, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(s->vals, A->values, sizeof(double) * 9 * (size_t)A->nnzb, kind, s->stream));
     s->rp_use = s->rp;
     s->ci_use = s->ci;
     s->vals_use = s->vals;
@@ -669,22 +676,25 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
   a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.x = s->x; a.r = s->r; a.u = s->u;
   a.alpha = s->alpha; a.gamma = s->gamma; a.rho = s->rho;
   a.tfull = s->tfull; a.sfull = s->sfull; a.gfull = s->gfull;
-  a.part = s->part; a.vpart = s->vpart; a.vld = s->vld; a.ctrl = s->ctrl; a.bar = s->bar;
+  a.part = s->part; a.vpart = s->vpart; a.gpart = s->gpart; a.vld = s->vld; a.ctrl = s->ctrl; a.bar = s->bar;
   KRS_CUDA(apcg_launch_init(a, s->b, s->scal, s->stream, &launches));
   KRS_CUDA(cudaMemcpyAsync(s->h_scal, s->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   KRS_CUDA(cudaStreamSynchronize(s->stream));
   const double bb = s->h_scal[0], rr0 = s->h_scal[1];
   if (!isfinite(bb)) return fail(KRS_ERR_INVALID_ARG, "right-hand side is not finite");
   a.tol2 = tol * tol * bb;
-  KRS_CUDA(cudaEventRecord(s->ev[1], s->stream));
 
-  // ---- iterations
+  // ---- iterations (events bracket exactly the iteration kernel launch(es))
   int status = KRS_OK, m = 0;
+  bool iter_timed = false;
   if (!(rr0 <= a.tol2)) {
     KRS_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, s->stream));
     KRS_CUDA(cudaMemsetAsync(s->bar, 0, sizeof(unsigned long long), s->stream));
+    KRS_CUDA(cudaEventRecord(s->ev[1], s->stream));
+    iter_timed = true;
     if (p->exec == KRS_EXEC_PERSISTENT) {
       KRS_CUDA(apcg_launch_persistent(a, s->stream, &launches));
+      KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
       KRS_CUDA(cudaMemcpyAsync(s->h_ctrl, s->ctrl, sizeof(int) * CTRL_WORDS, cudaMemcpyDeviceToHost, s->stream));
       KRS_CUDA(cudaStreamSynchronize(s->stream));
     } else {
@@ -698,12 +708,16 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
         j = j1;
         if (s->h_ctrl[CTRL_DONE] || j >= p->max_iter) break;
       }
+      KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
     }
     status = s->h_ctrl[CTRL_STATUS];
     m = s->h_ctrl[CTRL_M];
     if (!s->h_ctrl[CTRL_DONE] && status == KRS_OK) status = KRS_ERR_CUDA;
   }
-  KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
+  if (!iter_timed) {
+    KRS_CUDA(cudaEventRecord(s->ev[1], s->stream));
+    KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
+  }
   s->last_m = m;
 
   // ---- result and true residual

@@ -169,9 +169,11 @@ __device__ __forceinline__ double4_32a ld4(const double* p) {
   return *reinterpret_cast<const double4_32a*>(p);
 }
 
-// out[c] = sum_{i in [r0, r1)} V[c*ld + i] * u[i], c in [0, k).  Thread per column:
-// each thread streams its column with 32-byte loads and keeps one accumulator; several
-// row groups share the columns when k < TPB and are combined in shared memory.
+// out[c] = sum_{i in [r0, r1)} V[c*ld + i] * u[i], c in [0, k).  Thread per column: each
+// thread streams its column with 32-byte loads into four independent accumulators (no
+// dependent FMA chain).  Columns are taken in blocks of kc with G = ceil(TPB / rem) row
+// groups each (kc = TPB / G), so that all threads stay busy whatever k is; the groups are
+// combined in shared memory in a fixed order.
 // u: global vector (zero padded past n).  su: shared (ROW_CHUNK doubles); red: shared
 // (TPB doubles).
 template <bool NC>
@@ -180,50 +182,66 @@ __device__ __forceinline__ void cta_gemv_t(const double* __restrict__ V, int64_t
                                            double* __restrict__ out, double* su, double* red) {
   const int t = threadIdx.x;
   const int64_t rows4 = ((r1 - r0) + 3) & ~int64_t(3);  // padded to a multiple of 4
-  for (int cb = 0; cb < k; cb += TPB) {
-    const int kc = min(k - cb, TPB);
-    const int G = TPB / kc;  // row groups
+  const bool one_chunk = rows4 <= ROW_CHUNK;
+  if (one_chunk) {
+    __syncthreads();
+    for (int i = t; i < (int)rows4; i += TPB) su[i] = u[r0 + i];
+    __syncthreads();
+  }
+  int cb = 0;
+  while (cb < k) {
+    const int rem = k - cb;
+    const int G = (rem >= TPB) ? 1 : (TPB + rem - 1) / rem;  // row groups
+    const int kc = min(rem, TPB / G);
     const int c = t % kc;
     const int g = t / kc;
-    double acc = 0.0;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     for (int64_t ch = 0; ch < rows4; ch += ROW_CHUNK) {
       const int len = (int)kmin64(ROW_CHUNK, rows4 - ch);
-      __syncthreads();
-      for (int i = t; i < len; i += TPB) su[i] = u[r0 + ch + i];
-      __syncthreads();
+      if (!one_chunk) {
+        __syncthreads();
+        for (int i = t; i < len; i += TPB) su[i] = u[r0 + ch + i];
+        __syncthreads();
+      }
       if (g < G) {
         const int q4 = len >> 2;
         const int qa = (int)((int64_t)q4 * g / G), qb = (int)((int64_t)q4 * (g + 1) / G);
         const double* col = V + (int64_t)(cb + c) * ld + r0 + ch;
         const double4_32a* s4 = reinterpret_cast<const double4_32a*>(su);
         int q = qa;
-        for (; q + 2 <= qb; q += 2) {
-          const double4_32a a0 = ld4<NC>(col + 4 * q), a1 = ld4<NC>(col + 4 * q + 4);
-          const double4_32a b0 = s4[q], b1 = s4[q + 1];
-          acc += a0.x * b0.x; acc += a0.y * b0.y; acc += a0.z * b0.z; acc += a0.w * b0.w;
-          acc += a1.x * b1.x; acc += a1.y * b1.y; acc += a1.z * b1.z; acc += a1.w * b1.w;
+        for (; q + 4 <= qb; q += 4) {
+          const double4_32a x0 = ld4<NC>(col + 4 * q), x1 = ld4<NC>(col + 4 * q + 4);
+          const double4_32a x2 = ld4<NC>(col + 4 * q + 8), x3 = ld4<NC>(col + 4 * q + 12);
+          const double4_32a y0 = s4[q], y1 = s4[q + 1], y2 = s4[q + 2], y3 = s4[q + 3];
+          a0 += x0.x * y0.x; a1 += x0.y * y0.y; a2 += x0.z * y0.z; a3 += x0.w * y0.w;
+          a0 += x1.x * y1.x; a1 += x1.y * y1.y; a2 += x1.z * y1.z; a3 += x1.w * y1.w;
+          a0 += x2.x * y2.x; a1 += x2.y * y2.y; a2 += x2.z * y2.z; a3 += x2.w * y2.w;
+          a0 += x3.x * y3.x; a1 += x3.y * y3.y; a2 += x3.z * y3.z; a3 += x3.w * y3.w;
         }
         for (; q < qb; q++) {
-          const double4_32a a0 = ld4<NC>(col + 4 * q), b0 = s4[q];
-          acc += a0.x * b0.x; acc += a0.y * b0.y; acc += a0.z * b0.z; acc += a0.w * b0.w;
+          const double4_32a x0 = ld4<NC>(col + 4 * q), y0 = s4[q];
+          a0 += x0.x * y0.x; a1 += x0.y * y0.y; a2 += x0.z * y0.z; a3 += x0.w * y0.w;
         }
       }
     }
     __syncthreads();
-    if (g < G) red[g * kc + c] = acc;
+    if (g < G) red[g * kc + c] = (a0 + a1) + (a2 + a3);
     __syncthreads();
-    if (t < kc) {
-      double sum = red[t];
-      for (int gg = 1; gg < G; gg++) sum += red[gg * kc + t];
-      out[cb + t] = sum;
+    // combine the G row groups: pairwise tree (fixed order), log2(G) parallel rounds
+    for (int st = 1; st < G; st <<= 1) {
+      if (g < G && (g % (2 * st)) == 0 && g + st < G) red[g * kc + c] += red[(g + st) * kc + c];
+      __syncthreads();
     }
+    if (t < kc) out[cb + t] = red[t];
+    cb += kc;
   }
   __syncthreads();
 }
 
 // z[i] = u[i] + sgn * sum_{c<k} V[c*ld + i] * s[c] for i in [r0, r1) (u == nullptr: 0).
-// Thread per 4 rows; when the CTA has few rows, column groups split the k columns and
-// are combined in shared memory.  s: shared (k doubles).  red: shared (4*TPB doubles).
+// Thread per 4 rows (four independent accumulators); quads are taken in blocks of qc with
+// G = ceil(TPB / remaining quads) column groups each (qc = TPB / G), combined in shared
+// memory in a fixed order.  s: shared (k doubles).  red: shared (4*TPB doubles).
 template <bool NC>
 __device__ __forceinline__ void cta_gemv_n(const double* __restrict__ V, int64_t ld, int k,
                                            const double* s, double sgn, const double* u,
@@ -231,9 +249,12 @@ __device__ __forceinline__ void cta_gemv_n(const double* __restrict__ V, int64_t
   const int t = threadIdx.x;
   const int64_t L = r1 - r0;
   const int64_t q4 = (L + 3) >> 2;
-  for (int64_t qb0 = 0; qb0 < q4; qb0 += TPB) {
-    const int nq = (int)kmin64(TPB, q4 - qb0);
-    const int G = (k > 0) ? max(1, min(TPB / nq, k)) : 1;  // column groups
+  int64_t qb0 = 0;
+  while (qb0 < q4) {
+    const int64_t remq = q4 - qb0;
+    int G = (remq >= TPB) ? 1 : (int)((TPB + remq - 1) / remq);  // column groups
+    if (G > k) G = (k > 0) ? k : 1;
+    const int nq = (int)kmin64(remq, TPB / G);
     const int q = t % nq;
     const int g = t / nq;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -241,12 +262,16 @@ __device__ __forceinline__ void cta_gemv_n(const double* __restrict__ V, int64_t
       const int ca = (int)((int64_t)k * g / G), cbnd = (int)((int64_t)k * (g + 1) / G);
       const int64_t row = r0 + 4 * (qb0 + q);
       int c = ca;
-      for (; c + 2 <= cbnd; c += 2) {
+      for (; c + 4 <= cbnd; c += 4) {
         const double4_32a v0 = ld4<NC>(V + (int64_t)c * ld + row);
         const double4_32a v1 = ld4<NC>(V + (int64_t)(c + 1) * ld + row);
-        const double s0 = s[c], s1 = s[c + 1];
+        const double4_32a v2 = ld4<NC>(V + (int64_t)(c + 2) * ld + row);
+        const double4_32a v3 = ld4<NC>(V + (int64_t)(c + 3) * ld + row);
+        const double s0 = s[c], s1 = s[c + 1], s2 = s[c + 2], s3 = s[c + 3];
         a0 += v0.x * s0; a1 += v0.y * s0; a2 += v0.z * s0; a3 += v0.w * s0;
         a0 += v1.x * s1; a1 += v1.y * s1; a2 += v1.z * s1; a3 += v1.w * s1;
+        a0 += v2.x * s2; a1 += v2.y * s2; a2 += v2.z * s2; a3 += v2.w * s2;
+        a0 += v3.x * s3; a1 += v3.y * s3; a2 += v3.z * s3; a3 += v3.w * s3;
       }
       for (; c < cbnd; c++) {
         const double4_32a v0 = ld4<NC>(V + (int64_t)c * ld + row);
@@ -259,12 +284,18 @@ __device__ __forceinline__ void cta_gemv_n(const double* __restrict__ V, int64_t
       double4_32a* r4 = reinterpret_cast<double4_32a*>(red);
       if (g < G) r4[g * nq + q] = make_double4_32a(a0, a1, a2, a3);
       __syncthreads();
-      if (t < nq) {
-        double4_32a acc = r4[t];
-        for (int gg = 1; gg < G; gg++) {
-          const double4_32a v = r4[gg * nq + t];
+      // pairwise tree over the G column groups (fixed order), log2(G) parallel rounds
+      for (int st = 1; st < G; st <<= 1) {
+        if (g < G && (g % (2 * st)) == 0 && g + st < G) {
+          const double4_32a v = r4[(g + st) * nq + q];
+          double4_32a acc = r4[g * nq + q];
           acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+          r4[g * nq + q] = acc;
         }
+        __syncthreads();
+      }
+      if (t < nq) {
+        const double4_32a acc = r4[t];
         a0 = acc.x; a1 = acc.y; a2 = acc.z; a3 = acc.w;
       }
     }
@@ -276,35 +307,93 @@ __device__ __forceinline__ void cta_gemv_n(const double* __restrict__ V, int64_t
         if (row + e < r1) z[row + e] = (u ? u[row + e] : 0.0) + sgn * aa[e];
       }
     }
+    qb0 += nq;
   }
   __syncthreads();
 }
 
-// q = A w on one CTA's nodes (thread per scalar row: 3 FMAs per stored block, no
-// reduction), adds the thread's (w, q) and (r, w) contributions to wq / rw.  The matrix
-// is read through the non-coherent path; w (written by other CTAs of a persistent kernel)
-// is not.
+// q = A w on one CTA's nodes [r0/3, r1/3).  Two threads per node: each takes half of the
+// node's blocks and all three rows (three independent accumulators, 9 FMAs per block),
+// the odd thread's partial sums reach its even neighbour by register shuffle, and the
+// even thread writes q and adds its nodes' (w, q) and (r, w) terms to wq / rw.  Every
+// thread gets ~half a node, so the FP64 pipe is not idled by uneven rows per thread.
+// Blocks are read in pairs starting at an even block index, 144 bytes as nine 16-byte
+// loads (values must be 16-byte aligned; col_idx 8-byte aligned).  The matrix goes
+// through the non-coherent path; w (written by other CTAs of a persistent kernel) does not.
 __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* __restrict__ ci,
                                          const double* __restrict__ vals,
                                          const double* __restrict__ w, double* __restrict__ q,
                                          const double* __restrict__ r, int64_t r0, int64_t r1,
                                          double& wq, double& rw) {
-  for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
-    const int64_t node = row / 3;
-    const int d = (int)(row - 3 * node);
-    const int ka = __ldg(rp + node), kb = __ldg(rp + node + 1);
-    double acc = 0.0;
-    for (int k = ka; k < kb; k++) {
-      const int64_t cc = 3 * (int64_t)__ldg(ci + k);
-      const double* a = vals + 9 * (int64_t)k + 3 * d;
-      acc += __ldg(a + 0) * w[cc + 0];
-      acc += __ldg(a + 1) * w[cc + 1];
-      acc += __ldg(a + 2) * w[cc + 2];
+  const int64_t n0 = r0 / 3;
+  const int64_t items = 2 * ((r1 - r0) / 3);
+  for (int64_t base = 0; base < items; base += TPB) {
+    const int64_t it = base + threadIdx.x;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    const bool active = it < items;
+    int64_t node = 0;
+    if (active) {
+      node = n0 + (it >> 1);
+      const int ka = __ldg(rp + node), kb = __ldg(rp + node + 1);
+      const int mid = ka + ((kb - ka) >> 1);
+      const int kbeg = (it & 1) ? mid : ka, kend = (it & 1) ? kb : mid;
+      int k = kbeg;
+      if ((k & 1) && k < kend) {  // a leading odd block alone (its 72 bytes are not 16-aligned)
+        const int64_t cc = 3 * (int64_t)__ldg(ci + k);
+        const double* v = vals + 9 * (int64_t)k;
+        const double w0 = w[cc], w1 = w[cc + 1], w2 = w[cc + 2];
+        a0 += __ldg(v + 0) * w0; a1 += __ldg(v + 3) * w0; a2 += __ldg(v + 6) * w0;
+        a0 += __ldg(v + 1) * w1; a1 += __ldg(v + 4) * w1; a2 += __ldg(v + 7) * w1;
+        a0 += __ldg(v + 2) * w2; a1 += __ldg(v + 5) * w2; a2 += __ldg(v + 8) * w2;
+        k++;
+      }
+#pragma unroll 1
+      for (; k + 2 <= kend; k += 2) {  // block pairs (k even): 144 bytes, nine 16-byte loads
+        const int2 cp = __ldg(reinterpret_cast<const int2*>(ci + k));
+        const int64_t c0 = 3 * (int64_t)cp.x, c1 = 3 * (int64_t)cp.y;
+        const double2* v2 = reinterpret_cast<const double2*>(vals + 9 * (int64_t)k);
+        const double2 p0 = __ldg(v2 + 0), p1 = __ldg(v2 + 1), p2 = __ldg(v2 + 2), p3 = __ldg(v2 + 3);
+        const double2 p4 = __ldg(v2 + 4), p5 = __ldg(v2 + 5), p6 = __ldg(v2 + 6), p7 = __ldg(v2 + 7);
+        const double2 p8 = __ldg(v2 + 8);
+        const double x0 = w[c0], x1 = w[c0 + 1], x2 = w[c0 + 2];
+        const double y0 = w[c1], y1 = w[c1 + 1], y2 = w[c1 + 2];
+        // block k: (p0.x p0.y p1.x / p1.y p2.x p2.y / p3.x p3.y p4.x); block k+1: p4.y ... p8.y
+        a0 += p0.x * x0; a1 += p1.y * x0; a2 += p3.x * x0;
+        a0 += p0.y * x1; a1 += p2.x * x1; a2 += p3.y * x1;
+        a0 += p1.x * x2; a1 += p2.y * x2; a2 += p4.x * x2;
+        a0 += p4.y * y0; a1 += p6.x * y0; a2 += p7.y * y0;
+        a0 += p5.x * y1; a1 += p6.y * y1; a2 += p8.x * y1;
+        a0 += p5.y * y2; a1 += p7.x * y2; a2 += p8.y * y2;
+      }
+      if (k < kend) {  // a trailing single block
+        const int64_t cc = 3 * (int64_t)__ldg(ci + k);
+        const double* v = vals + 9 * (int64_t)k;
+        const double w0 = w[cc], w1 = w[cc + 1], w2 = w[cc + 2];
+        a0 += __ldg(v + 0) * w0; a1 += __ldg(v + 3) * w0; a2 += __ldg(v + 6) * w0;
+        a0 += __ldg(v + 1) * w1; a1 += __ldg(v + 4) * w1; a2 += __ldg(v + 7) * w1;
+        a0 += __ldg(v + 2) * w2; a1 += __ldg(v + 5) * w2; a2 += __ldg(v + 8) * w2;
+      }
     }
-    q[row] = acc;
-    const double wr = w[row];
-    wq += wr * acc;
-    if (r) rw += r[row] * wr;
+    // pairs (2i, 2i+1) share a warp (TPB and base are even); every lane takes part
+    const double b0 = __shfl_xor_sync(0xffffffffu, a0, 1);
+    const double b1 = __shfl_xor_sync(0xffffffffu, a1, 1);
+    const double b2 = __shfl_xor_sync(0xffffffffu, a2, 1);
+    if (active && !(it & 1)) {
+      const double q0 = a0 + b0, q1 = a1 + b1, q2 = a2 + b2;
+      const int64_t row = 3 * node;
+      q[row] = q0;
+      q[row + 1] = q1;
+      q[row + 2] = q2;
+      const double w0 = w[row], w1 = w[row + 1], w2 = w[row + 2];
+      wq += w0 * q0;
+      wq += w1 * q1;
+      wq += w2 * q2;
+      if (r) {
+        rw += r[row] * w0;
+        rw += r[row + 1] * w1;
+        rw += r[row + 2] * w2;
+      }
+    }
   }
 }
 

@@ -26,6 +26,7 @@ struct IterArgs {
   double *tfull, *sfull, *gfull;
   double* part;
   double* vpart;
+  double* gpart;
   int64_t vld;
   int* ctrl;
   unsigned long long* bar;

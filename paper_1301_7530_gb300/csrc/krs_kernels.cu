@@ -12,7 +12,7 @@
 namespace krs {
 
 // ------------------------------------------------------------------------------------
-// y = A x, thread per scalar row (same summation order as the iteration's product)
+// y = A x, thread per scalar row (stand-alone product: set-up, true residual)
 // ------------------------------------------------------------------------------------
 __global__ void k_spmv(int nbr, const int* __restrict__ rp, const int* __restrict__ ci,
                        const double* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y) {
@@ -21,15 +21,15 @@ __global__ void k_spmv(int nbr, const int* __restrict__ rp, const int* __restric
   const int64_t node = row / 3;
   const int d = (int)(row - 3 * node);
   const int ka = __ldg(rp + node), kb = __ldg(rp + node + 1);
-  double acc = 0.0;
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
   for (int k = ka; k < kb; k++) {
     const int64_t cc = 3 * (int64_t)__ldg(ci + k);
     const double* a = vals + 9 * (int64_t)k + 3 * d;
-    acc += __ldg(a + 0) * x[cc + 0];
-    acc += __ldg(a + 1) * x[cc + 1];
-    acc += __ldg(a + 2) * x[cc + 2];
+    acc0 += __ldg(a + 0) * x[cc + 0];
+    acc1 += __ldg(a + 1) * x[cc + 1];
+    acc2 += __ldg(a + 2) * x[cc + 2];
   }
-  y[row] = acc;
+  y[row] = (acc0 + acc1) + acc2;
 }
 
 cudaError_t launch_spmv(int nbr, const int* rp, const int* ci, const double* vals, const double* x,
@@ -103,7 +103,8 @@ cudaError_t launch_precond_apply(int kind, int nbr, const double* minv, const do
 
 // ------------------------------------------------------------------------------------
 // AC = A C for columns [c0, c1): thread per scalar row and 8 columns; A's block row is
-// read once for the 8 columns.  Per column the summation order equals k_spmv's.
+// read once for the 8 columns.  Per column the summation order equals k_spmv's.  (Columns
+// recycled from a solve's directions keep the iteration's own products A w instead.)
 // ------------------------------------------------------------------------------------
 constexpr int SPMM_COLS = 8;
 
@@ -116,9 +117,9 @@ __global__ void k_spmm(int nbr, const int* __restrict__ rp, const int* __restric
   const int nk = min(SPMM_COLS, c1 - cb);
   const int64_t node = row / 3;
   const int d = (int)(row - 3 * node);
-  double acc[SPMM_COLS];
+  double acc[SPMM_COLS][3];
 #pragma unroll
-  for (int q = 0; q < SPMM_COLS; q++) acc[q] = 0.0;
+  for (int q = 0; q < SPMM_COLS; q++) acc[q][0] = acc[q][1] = acc[q][2] = 0.0;
   const int ka = __ldg(rp + node), kb = __ldg(rp + node + 1);
   for (int k = ka; k < kb; k++) {
     const int64_t cc = 3 * (int64_t)__ldg(ci + k);
@@ -128,15 +129,15 @@ __global__ void k_spmm(int nbr, const int* __restrict__ rp, const int* __restric
     for (int q = 0; q < SPMM_COLS; q++) {
       if (q < nk) {
         const double* x = C + (int64_t)(cb + q) * ld + cc;
-        acc[q] += a0 * __ldg(x);
-        acc[q] += a1 * __ldg(x + 1);
-        acc[q] += a2 * __ldg(x + 2);
+        acc[q][0] += a0 * __ldg(x);
+        acc[q][1] += a1 * __ldg(x + 1);
+        acc[q][2] += a2 * __ldg(x + 2);
       }
     }
   }
 #pragma unroll
   for (int q = 0; q < SPMM_COLS; q++)
-    if (q < nk) AC[(int64_t)(cb + q) * ld + row] = acc[q];
+    if (q < nk) AC[(int64_t)(cb + q) * ld + row] = (acc[q][0] + acc[q][1]) + acc[q][2];
 }
 
 cudaError_t launch_spmm(int nbr, const int* rp, const int* ci, const double* vals, const double* C,

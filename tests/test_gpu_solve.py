@@ -270,3 +270,20 @@ def test_full_size_first_solve_and_sequence_properties(gpu_lib):
             AC = Ak.to_scipy() @ Cb
             assert np.abs(Cb.T @ r).max() <= 1e-9 * np.linalg.norm(Cb, axis=0).max() * np.linalg.norm(b) * np.sqrt(Cb.shape[1])
         assert seq.nc <= 200
+
+
+def test_misaligned_device_matrix_is_copied(gpu_lib):
+    """A caller's device matrix whose values are only 8-byte aligned gives the same result
+    (the library copies it into aligned storage)."""
+    import torch
+    A, bs = P.elasticity_sequence_fixed(3, 1, 12)
+    pol = B.make_policy("none", "jacobi")
+    x_ref, st_ref = B.Sequence(A.n).solve(A, bs[0], 1e-10, pol, version=1)
+    big = torch.zeros(A.vals.size + 1, dtype=torch.float64, device="cuda")
+    big[1:] = torch.as_tensor(A.vals.reshape(-1), device="cuda")
+    Ad = {"row_ptr": torch.as_tensor(A.row_ptr, device="cuda"), "col_idx": torch.as_tensor(A.col_idx, device="cuda"),
+          "values": big[1:]}
+    assert Ad["values"].data_ptr() % 16 == 8
+    x, st = B.Sequence(A.n).solve(Ad, torch.as_tensor(bs[0], device="cuda"), 1e-10, pol, version=1)
+    torch.cuda.synchronize()
+    assert st["m"] == st_ref["m"] and np.array_equal(x.cpu().numpy(), x_ref)
