@@ -234,6 +234,22 @@ krs_status krs_tridiag_eigvals(int32_t m, const double* delta, const double* eta
 krs_status krs_tridiag_eigvecs(int32_t m, const double* delta, const double* eta, int32_t k,
                                const double* theta_sel, double* Q_out, void* stream);
 
+/* t = V^T u exactly as krs_gemv_t computes it (same partition, same summation order), but
+ * allocating no device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate -- a framework that has reserved the device memory for its
+ * own pool, a latency-bound loop that cannot pay for an allocation or its implicit
+ * synchronisation, code where another component owns every allocation.  Its per-block
+ * partial sums live in a fixed 2 MiB array in device global memory that every GPU loading
+ * the library holds until the process exits.  Limits: k <= 1024 (larger k returns
+ * KRS_ERR_INVALID_ARG with a message); the row blocks follow krs_gemv_t's partition (at
+ * most one per SM).  The first call on each device looks up the array's device address on
+ * that device; make that first call before any stream capture.  All calls share the array
+ * and it keeps the previous call's contents (nothing needs clearing: every value read is
+ * written first by the same call); calls whose kernels overlap on the GPU race.
+ * Arguments, layout and alignment as for krs_gemv_t; asynchronous on `stream`. */
+krs_status krs_gemv_t_noalloc(int64_t n, int32_t k, const double* V, int64_t ldv, const double* u,
+                              double* t, void* stream);
+
 /* Host-only validation of a BSR pattern (no GPU needed): sizes, monotone row_ptr, column
  * indices in range and strictly ascending per row, diagonal block present.  Host arrays. */
 krs_status krs_validate_bsr(int32_t n_block_rows, int64_t nnzb, const int32_t* row_ptr,

@@ -84,6 +84,7 @@ SIGNATURES = {
     "krs_precond_apply": (ct.c_int, [_I32, _I32, _P, _P, _P, _P]),
     "krs_gemv_t": (ct.c_int, [_I64, _I32, _P, _I64, _P, _P, _P]),
     "krs_gemv_n_sub": (ct.c_int, [_I64, _I32, _P, _I64, _P, _P, _P, _P]),
+    "krs_gemv_t_noalloc": (ct.c_int, [_I64, _I32, _P, _I64, _P, _P, _P]),
     "krs_axpy2_dot": (ct.c_int, [_I64, _P, _P, _P, _P, _P, _P, _P]),
     "krs_tridiag_eigvals": (ct.c_int, [_I32, _P, _P, _P, _P]),
     "krs_tridiag_eigvecs": (ct.c_int, [_I32, _P, _P, _I32, _P, _P, _P]),

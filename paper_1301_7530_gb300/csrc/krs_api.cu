@@ -40,6 +40,11 @@ static krs_status fail(krs_status st, const char* fmt, ...) {
   return st;
 }
 
+krs_status krs::set_error(krs_status st, const char* msg) {
+  g_last_error = msg;
+  return st;
+}
+
 #define KRS_CUDA(call)                                                                     \
   do {                                                                                     \
     cudaError_t e_ = (call);                                                               \

@@ -3,7 +3,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "krs.h"
+
 namespace krs {
+
+// Records msg as the calling thread's krs_last_error() and returns st.
+krs_status set_error(krs_status st, const char* msg);
 
 // Everything the iteration kernels need (device pointers, sizes, partition).
 struct IterArgs {
