@@ -146,9 +146,13 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("krs_device.cuh", "krs_apcg.cu")  # everything k_apcg_persistent is built from
+
+
 def csrc_digest():
+    """Digest of the persistent kernel's sources: a profile taken on other sources is stale."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

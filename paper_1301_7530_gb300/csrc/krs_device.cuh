@@ -130,11 +130,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* counter, unsign
   if (threadIdx.x == 0) {
     target += P;
     int ok = 1;
-    __threadfence();
-    atomicAdd(counter, 1ull);
+    // release: this CTA's writes (ordered before by __syncthreads) become visible with the
+    // arrival; acquire on the polls: the other CTAs' writes are visible after the exit
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(counter), "l"(1ull) : "memory");
     long long spins = 0;
     for (;;) {
-      unsigned long long v = *((volatile unsigned long long*)counter);
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(counter) : "memory");
       if (v >= target) break;
       if (*((volatile int*)(ctrl + CTRL_ABORT)) != 0) { ok = 0; break; }
       if (++spins > spin_limit) {
@@ -145,7 +147,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* counter, unsign
       }
       if (spins > 64) __nanosleep(32);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -176,10 +177,51 @@ __device__ __forceinline__ double4_32a ld4(const double* p) {
 // combined in shared memory in a fixed order.
 // u: global vector (zero padded past n).  su: shared (ROW_CHUNK doubles); red: shared
 // (TPB doubles).
+// Few columns (k <= TPB/32): warps instead of threads own the columns -- Gw = (TPB/32)/k
+// warps per column split the rows, lanes read consecutive 32-byte pieces of the column
+// (contiguous 1 KB per warp load), each warp folds its lanes with one shuffle tree, and
+// the Gw warp partials are summed in a fixed order.  Used by cta_gemv_t.
+template <bool NC>
+__device__ __forceinline__ void cta_gemv_t_few(const double* __restrict__ V, int64_t ld, int k,
+                                               const double* __restrict__ u, int64_t r0, int64_t r1,
+                                               double* __restrict__ out, double* red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int W = TPB / 32;
+  const int Gw = W / k;
+  const int q4 = (int)(((r1 - r0) + 3) >> 2);
+  if (warp < Gw * k) {
+    const int c = warp / Gw, g = warp % Gw;
+    const int qa = (int)((int64_t)q4 * g / Gw), qb = (int)((int64_t)q4 * (g + 1) / Gw);
+    const double* col = V + (int64_t)c * ld + r0;
+    const double* uu = u + r0;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int q = qa + lane; q < qb; q += 32) {
+      const double4_32a x = ld4<NC>(col + 4 * q);
+      const double4_32a y = *reinterpret_cast<const double4_32a*>(uu + 4 * q);
+      a0 += x.x * y.x; a1 += x.y * y.y; a2 += x.z * y.z; a3 += x.w * y.w;
+    }
+    double v = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double s = red[threadIdx.x * Gw];
+    for (int g = 1; g < Gw; g++) s += red[threadIdx.x * Gw + g];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
 template <bool NC>
 __device__ __forceinline__ void cta_gemv_t(const double* __restrict__ V, int64_t ld, int k,
                                            const double* __restrict__ u, int64_t r0, int64_t r1,
                                            double* __restrict__ out, double* su, double* red) {
+  if (k <= TPB / 32) {
+    cta_gemv_t_few<NC>(V, ld, k, u, r0, r1, out, red);
+    return;
+  }
   const int t = threadIdx.x;
   const int64_t rows4 = ((r1 - r0) + 3) & ~int64_t(3);  // padded to a multiple of 4
   const bool one_chunk = rows4 <= ROW_CHUNK;
@@ -347,23 +389,35 @@ __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* 
         a0 += __ldg(v + 2) * w2; a1 += __ldg(v + 5) * w2; a2 += __ldg(v + 8) * w2;
         k++;
       }
-#pragma unroll 1
-      for (; k + 2 <= kend; k += 2) {  // block pairs (k even): 144 bytes, nine 16-byte loads
-        const int2 cp = __ldg(reinterpret_cast<const int2*>(ci + k));
-        const int64_t c0 = 3 * (int64_t)cp.x, c1 = 3 * (int64_t)cp.y;
+      // block pairs (k even): 144 bytes as nine 16-byte loads; the next pair's indices and
+      // values are loaded before the current pair is used (two-stage software pipeline)
+      if (k + 2 <= kend) {
+        int2 cp = __ldg(reinterpret_cast<const int2*>(ci + k));
         const double2* v2 = reinterpret_cast<const double2*>(vals + 9 * (int64_t)k);
-        const double2 p0 = __ldg(v2 + 0), p1 = __ldg(v2 + 1), p2 = __ldg(v2 + 2), p3 = __ldg(v2 + 3);
-        const double2 p4 = __ldg(v2 + 4), p5 = __ldg(v2 + 5), p6 = __ldg(v2 + 6), p7 = __ldg(v2 + 7);
-        const double2 p8 = __ldg(v2 + 8);
-        const double x0 = w[c0], x1 = w[c0 + 1], x2 = w[c0 + 2];
-        const double y0 = w[c1], y1 = w[c1 + 1], y2 = w[c1 + 2];
-        // block k: (p0.x p0.y p1.x / p1.y p2.x p2.y / p3.x p3.y p4.x); block k+1: p4.y ... p8.y
-        a0 += p0.x * x0; a1 += p1.y * x0; a2 += p3.x * x0;
-        a0 += p0.y * x1; a1 += p2.x * x1; a2 += p3.y * x1;
-        a0 += p1.x * x2; a1 += p2.y * x2; a2 += p4.x * x2;
-        a0 += p4.y * y0; a1 += p6.x * y0; a2 += p7.y * y0;
-        a0 += p5.x * y1; a1 += p6.y * y1; a2 += p8.x * y1;
-        a0 += p5.y * y2; a1 += p7.x * y2; a2 += p8.y * y2;
+        double2 p0 = __ldg(v2 + 0), p1 = __ldg(v2 + 1), p2 = __ldg(v2 + 2), p3 = __ldg(v2 + 3);
+        double2 p4 = __ldg(v2 + 4), p5 = __ldg(v2 + 5), p6 = __ldg(v2 + 6), p7 = __ldg(v2 + 7);
+        double2 p8 = __ldg(v2 + 8);
+#pragma unroll 1
+        for (; k + 2 <= kend; k += 2) {
+          const int64_t c0 = 3 * (int64_t)cp.x, c1 = 3 * (int64_t)cp.y;
+          const double x0 = w[c0], x1 = w[c0 + 1], x2 = w[c0 + 2];
+          const double y0 = w[c1], y1 = w[c1 + 1], y2 = w[c1 + 2];
+          const double2 q0 = p0, q1 = p1, q2 = p2, q3 = p3, q4 = p4, q5 = p5, q6 = p6, q7 = p7, q8 = p8;
+          if (k + 4 <= kend) {
+            cp = __ldg(reinterpret_cast<const int2*>(ci + k + 2));
+            const double2* n2 = reinterpret_cast<const double2*>(vals + 9 * (int64_t)(k + 2));
+            p0 = __ldg(n2 + 0); p1 = __ldg(n2 + 1); p2 = __ldg(n2 + 2); p3 = __ldg(n2 + 3);
+            p4 = __ldg(n2 + 4); p5 = __ldg(n2 + 5); p6 = __ldg(n2 + 6); p7 = __ldg(n2 + 7);
+            p8 = __ldg(n2 + 8);
+          }
+          // block k: (q0.x q0.y q1.x / q1.y q2.x q2.y / q3.x q3.y q4.x); block k+1: q4.y ... q8.y
+          a0 += q0.x * x0; a1 += q1.y * x0; a2 += q3.x * x0;
+          a0 += q0.y * x1; a1 += q2.x * x1; a2 += q3.y * x1;
+          a0 += q1.x * x2; a1 += q2.y * x2; a2 += q4.x * x2;
+          a0 += q4.y * y0; a1 += q6.x * y0; a2 += q7.y * y0;
+          a0 += q5.x * y1; a1 += q6.y * y1; a2 += q8.x * y1;
+          a0 += q5.y * y2; a1 += q7.x * y2; a2 += q8.y * y2;
+        }
       }
       if (k < kend) {  // a trailing single block
         const int64_t cc = 3 * (int64_t)__ldg(ci + k);
