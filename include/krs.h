@@ -89,7 +89,21 @@ typedef struct {
  *   exec:       KRS_EXEC_PERSISTENT runs a whole solve in one cooperative kernel with
  *               grid-wide barriers; KRS_EXEC_KERNELS launches one kernel per phase.  Both
  *               compute the same arithmetic in the same order.
- *   precision:  KRS_FP64 only in this version (others return KRS_ERR_INVALID_ARG). */
+ *   precision:  KRS_FP64: the whole solve in FP64.  KRS_MIXED_IR: iterative refinement --
+ *               an FP64 outer loop (x += d, r = b - A x in FP64) around inner APCG solves
+ *               A d = r whose SpMV, preconditioner, projections and reorthogonalisation run
+ *               in FP32 (FP32 copies of A, M^-1, C, AC; FP32 directions), while C^T A C, its
+ *               Cholesky factor and inverse, the Lanczos tridiagonal and its eigensolve stay
+ *               FP64.  Within one system every inner solve after the first is augmented
+ *               by the directions of the earlier ones (same operator: they are A-conjugate
+ *               to C and to each other, so their coarse block is diagonal), so refinement
+ *               does not restart the Krylov space.  The recycling step (TRKS / SRKS) between
+ *               systems uses the first inner solve.  An FP32 breakdown ((w, Aw) <= 0 or
+ *               (r, z) <= 0) after some progress ends that inner solve only.
+ *   inner_tol:  KRS_MIXED_IR: relative residual each inner solve aims for (<= 0: 0.1);
+ *               the last one is loosened to what the outer tolerance still needs.
+ *   max_outer:  KRS_MIXED_IR: limit of refinement steps (<= 0: 30).  max_iter bounds the
+ *               total of inner iterations. */
 typedef struct {
   int32_t recycle;
   int32_t precond;
@@ -101,6 +115,9 @@ typedef struct {
   int32_t cap_mode;
   int32_t max_iter;
   int32_t exec;
+  double inner_tol;
+  int32_t max_outer;
+  int32_t reserved;
 } krs_policy;
 
 /* Device memory and stream.  alloc/free may be NULL (cudaMalloc/cudaFree are used);
@@ -119,7 +136,7 @@ typedef struct {
  * augmentation -- coarse preparation, initialisation -- and iterations, Section 5). */
 typedef struct {
   int32_t status;
-  int32_t m;              /* iterations of the solve */
+  int32_t m;              /* iterations of the solve (KRS_MIXED_IR: all inner solves) */
   int32_t n_c;            /* columns of C used by the solve */
   int32_t n_selected;     /* columns appended after the solve */
   int32_t n_c_after;      /* columns of C after the recycling step */
@@ -132,6 +149,8 @@ typedef struct {
                              Ritz vectors, concatenation */
   double t_total_ms;
   int64_t kernel_launches;/* kernels this library launched for the solve */
+  int32_t outer_iters;    /* refinement steps (KRS_MIXED_IR; 0 for KRS_FP64) */
+  int32_t inner_m_first;  /* iterations of the first inner solve (KRS_MIXED_IR) */
 } krs_solve_stats;
 
 /* --- sequence life cycle -------------------------------------------------------------- */
@@ -159,7 +178,8 @@ krs_status krs_destroy_sequence(krs_seq_t s);
 const char* krs_last_error(void);
 
 /* Default policy: FP64, block-Jacobi, full reorthogonalisation, no recycling,
- * ritz_eps 1e-14, no theta filter, no cap, max_iter 2000, persistent execution. */
+ * ritz_eps 1e-14, no theta filter, no cap, max_iter 2000, persistent execution,
+ * inner_tol 0.1 and max_outer 30 (used by KRS_MIXED_IR only). */
 krs_status krs_policy_default(krs_policy* p);
 
 /* --- recycled space (checkpoint, eviction, lock-step comparison) ----------------------- */

@@ -37,7 +37,8 @@ class krs_policy(ct.Structure):
     _fields_ = [("recycle", ct.c_int32), ("precond", ct.c_int32), ("reorth", ct.c_int32),
                 ("precision", ct.c_int32), ("ritz_eps", ct.c_double), ("theta_frac", ct.c_double),
                 ("max_aug", ct.c_int32), ("cap_mode", ct.c_int32), ("max_iter", ct.c_int32),
-                ("exec", ct.c_int32)]
+                ("exec", ct.c_int32), ("inner_tol", ct.c_double), ("max_outer", ct.c_int32),
+                ("reserved", ct.c_int32)]
 
 
 ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p)
@@ -54,7 +55,7 @@ class krs_solve_stats(ct.Structure):
                 ("n_selected", ct.c_int32), ("n_c_after", ct.c_int32), ("rel_res", ct.c_double),
                 ("true_rel_res", ct.c_double), ("t_setup_ms", ct.c_double), ("t_iter_ms", ct.c_double),
                 ("t_recycle_ms", ct.c_double), ("t_total_ms", ct.c_double),
-                ("kernel_launches", ct.c_int64)]
+                ("kernel_launches", ct.c_int64), ("outer_iters", ct.c_int32), ("inner_m_first", ct.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -141,10 +142,10 @@ def ptr(a) -> int:
 
 def make_policy(recycle="none", precond="block_jacobi3", reorth="full", precision="fp64",
                 ritz_eps=1e-14, theta_frac=0.0, max_aug=0, cap_mode="truncate", max_iter=2000,
-                exec="persistent") -> krs_policy:
+                exec="persistent", inner_tol=0.0, max_outer=0) -> krs_policy:
     return krs_policy(RECYCLE[recycle], PRECOND[precond], REORTH[reorth], PRECISION[precision],
                       float(ritz_eps), float(theta_frac), int(max_aug), CAP[cap_mode], int(max_iter),
-                      EXEC[exec])
+                      EXEC[exec], float(inner_tol), int(max_outer), 0)
 
 
 _versions = itertools.count(1)

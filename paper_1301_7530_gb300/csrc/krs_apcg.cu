@@ -4,7 +4,10 @@
 //     phases are separated by bounded grid barriers;
 //   * kernels:    one kernel launch per phase (the launch boundary is the barrier).
 // Both use the same CTA partition and the same reduction order, so they produce the same
-// bits.
+// bits.  Everything is templated on the value type T of the vectors, multi-vectors and
+// matrix: T = double for the FP64 solve, T = float for the inner solve of the
+// mixed-precision refinement.  Scalars (alpha, gamma, rho, the coarse coefficients) and
+// every partial sum that crosses CTAs are doubles in both.
 //
 // One iteration j (literal order of Algorithm 1 with the readings: z_j = P M^-1 r_j, the
 // Gram-Schmidt beta computed before use, classical Gram-Schmidt over all stored
@@ -12,8 +15,8 @@
 //   P1  q = A w_j (stored as AW[:, j]); partials (w_j, q), (r_j, w_j)
 //   P2  gamma_j, alpha_j = (r_j, w_j)/gamma_j; x += alpha w_j; r -= alpha q; (r, r);
 //       u = M^-1 r; partials t = (AC)^T u
-//   P3  convergence ||r||^2 <= tol^2 ||b||^2; slice of t reduced
-//   P4  slice of s = (C^T A C)^-1 t
+//   P3  convergence ||r||^2 <= tol^2 ||b||^2; t reduced (slice, or whole when n_c is small)
+//   P4  slice of s = (C^T A C)^-1 t (only when n_c is not small)
 //   P5  z = u - C s (stored as Z[:, j+1]); partials (r, z), g = (AW)^T z
 //   P6  rho_{j+1} = (r, z); slice of g_i / gamma_i
 //   P7  w_{j+1} = z - W g (stored as W[:, j+1])
@@ -27,27 +30,30 @@
 
 namespace krs {
 
+template <typename T>
 struct ApcgCtx {
   int64_t n, ld;       // order, leading dimension of multi-vectors and vector padding
   int nbr, npc, P;     // block rows, nodes per CTA, CTAs
   int nc, ldg;         // columns of C, leading dimension of Ginv
+  int nc_dense;        // columns [0, nc_dense) use Ginv; columns [nc_dense, nc) are mutually
+                       // A-conjugate directions whose coarse block is diag(dinv)
   int max_iter, reorth_full, precond;
-  int j0;              // first iteration of this launch (persistent mode)
   double tol2;         // tol^2 * ||b||^2
   long long spin_limit;
+  const double* dinv;  // 1/(w_i, A w_i) of the tail columns
   const int* rp;
   const int* ci;
-  const double* vals;
-  const double* minv;
-  const double* C;
-  const double* AC;
+  const T* vals;
+  const T* minv;
+  const T* C;
+  const T* AC;
   const double* Ginv;
-  double* W;
-  double* AW;
-  double* Z;
-  double* x;
-  double* r;
-  double* u;
+  T* W;
+  T* AW;
+  T* Z;
+  T* x;
+  T* r;
+  T* u;
   double* alpha;
   double* gamma;
   double* rho;
@@ -62,24 +68,28 @@ struct ApcgCtx {
   unsigned long long* bar;
 };
 
-// shared-memory layout (doubles): su[ROW_CHUNK] | red[4*TPB] | sv[kmax]
+// shared-memory layout (in doubles): su[ROW_CHUNK] | red[4*TPB] | sv[kmax]
+// (su and sv hold values of T)
+template <typename T>
 struct Smem {
-  double* su;
+  T* su;
   double* red;
-  double* sv;
+  T* sv;
 };
 
-__device__ __forceinline__ Smem smem_layout(double* base) {
-  Smem s;
-  s.su = base;
+template <typename T>
+__device__ __forceinline__ Smem<T> smem_layout(double* base) {
+  Smem<T> s;
+  s.su = reinterpret_cast<T*>(base);
   s.red = base + ROW_CHUNK;
-  s.sv = base + ROW_CHUNK + 4 * TPB;
+  s.sv = reinterpret_cast<T*>(base + ROW_CHUNK + 4 * TPB);
   return s;
 }
 
 enum PhaseResult { PH_CONTINUE = 0, PH_STOP = 1 };
 
-__device__ __forceinline__ void finish(const ApcgCtx& c, int status, int m) {
+template <typename T>
+__device__ __forceinline__ void finish(const ApcgCtx<T>& c, int status, int m) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (status) atomicCAS(c.ctrl + CTRL_STATUS, 0, status);
     c.ctrl[CTRL_M] = m;
@@ -88,9 +98,9 @@ __device__ __forceinline__ void finish(const ApcgCtx& c, int status, int m) {
 }
 
 // Reduce a scalar partial over all CTAs (warp 0, fixed order) and broadcast it.
-__device__ __forceinline__ double grid_scalar(const ApcgCtx& c, int slot, double* red) {
+__device__ __forceinline__ double grid_scalar(const double* part, int P, int slot, double* red) {
   if (threadIdx.x < 32) {
-    double v = warp_sum_strided(c.part + slot, c.P, PS_STRIDE);
+    double v = warp_sum_strided(part + slot, P, PS_STRIDE);
     if (threadIdx.x == 0) red[0] = v;
   }
   __syncthreads();
@@ -100,11 +110,11 @@ __device__ __forceinline__ double grid_scalar(const ApcgCtx& c, int slot, double
 }
 
 // Two scalars at once (warps 0 and 1 in parallel).
-__device__ __forceinline__ void grid_scalar2(const ApcgCtx& c, int slot_a, int slot_b, double* red, double& va,
-                                             double& vb) {
+__device__ __forceinline__ void grid_scalar2(const double* part, int P, int slot_a, int slot_b, double* red,
+                                             double& va, double& vb) {
   const int warp = threadIdx.x >> 5;
   if (warp < 2) {
-    const double v = warp_sum_strided(c.part + (warp == 0 ? slot_a : slot_b), c.P, PS_STRIDE);
+    const double v = warp_sum_strided(part + (warp == 0 ? slot_a : slot_b), P, PS_STRIDE);
     if ((threadIdx.x & 31) == 0) red[warp] = v;
   }
   __syncthreads();
@@ -116,13 +126,29 @@ __device__ __forceinline__ void grid_scalar2(const ApcgCtx& c, int slot_a, int s
 // Augmentation sizes up to this are reduced by every CTA redundantly (no extra barriers).
 constexpr int SMALL_NC = 16;
 
-__device__ __forceinline__ void phase1(const ApcgCtx& c, int j, Smem& sm) {
+// s[col] = (G^-1 t)[col]: the dense block G^-1 (nc_dense x nc_dense) for the first columns,
+// 1/(w, Aw) for the tail of mutually A-conjugate directions.  Computed by one warp; the
+// result is returned to every lane.
+__device__ __forceinline__ double coarse_coef(const double* Ginv, int ldg, int nc_dense, const double* dinv, int col,
+                                              const double* t) {
+  const int lane = threadIdx.x & 31;
+  if (col >= nc_dense) return t[col] * dinv[col - nc_dense];
+  const double* g = Ginv + (int64_t)col * ldg;
+  double s = 0.0;
+  for (int k = lane; k < nc_dense; k += 32) s += g[k] * t[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ void phase1(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
-  const double* w = c.W + (int64_t)j * c.ld;
-  double* q = c.AW + (int64_t)j * c.ld;
+  const T* w = c.W + (int64_t)j * c.ld;
+  T* q = c.AW + (int64_t)j * c.ld;
   double wq = 0.0, rw = 0.0;
-  cta_spmv(c.rp, c.ci, c.vals, w, q, c.r, r0, r1, wq, rw);
+  cta_spmv<T>(c.rp, c.ci, c.vals, w, q, c.r, r0, r1, wq, rw);
   block_sum2(wq, rw, sm.red);
   if (threadIdx.x == 0) {
     c.part[blockIdx.x * PS_STRIDE + PS_WQ] = wq;
@@ -130,9 +156,10 @@ __device__ __forceinline__ void phase1(const ApcgCtx& c, int j, Smem& sm) {
   }
 }
 
-__device__ __forceinline__ int phase2(const ApcgCtx& c, int j, Smem& sm) {
+template <typename T>
+__device__ __forceinline__ int phase2(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
   double gam, rws;
-  grid_scalar2(c, PS_WQ, PS_RW, sm.red, gam, rws);
+  grid_scalar2(c.part, c.P, PS_WQ, PS_RW, sm.red, gam, rws);
   if (!(gam > 0.0)) {
     finish(c, 2 /* KRS_ERR_NOT_SPD */, j);
     return PH_STOP;
@@ -142,23 +169,25 @@ __device__ __forceinline__ int phase2(const ApcgCtx& c, int j, Smem& sm) {
     c.alpha[j] = al;
     c.gamma[j] = gam;
   }
+  const T alT = (T)al;
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
-  const double* w = c.W + (int64_t)j * c.ld;
-  const double* q = c.AW + (int64_t)j * c.ld;
+  const T* w = c.W + (int64_t)j * c.ld;
+  const T* q = c.AW + (int64_t)j * c.ld;
   double rr = 0.0;
   for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
-    c.x[row] += al * w[row];
-    const double rn = c.r[row] - al * q[row];
+    c.x[row] += alT * w[row];
+    const T rn = c.r[row] - alT * q[row];
     c.r[row] = rn;
-    rr += rn * rn;
+    rr += (double)rn * (double)rn;
   }
   __syncthreads();
   for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB)
-    c.u[row] = precond_row(c.precond, c.minv, c.r, row);
+    c.u[row] = precond_row<T>(c.precond, c.minv, c.r, row);
   rr = block_sum(rr, sm.red);
   if (threadIdx.x == 0) c.part[blockIdx.x * PS_STRIDE + PS_RR] = rr;
-  if (c.nc > 0) cta_gemv_t<true>(c.AC, c.ld, c.nc, c.u, r0, r1, c.vpart + blockIdx.x * c.vld, sm.su, sm.red);
+  if (c.nc > 0)
+    cta_gemv_t<true, T>(c.AC, c.ld, c.nc, c.u, r0, r1, c.vpart + blockIdx.x * c.vld, sm.su, sm.red);
   return PH_CONTINUE;
 }
 
@@ -169,8 +198,9 @@ __device__ __forceinline__ void col_slice(int k, int P, int b, int& a, int& e) {
   e = min(k, a + per);
 }
 
-__device__ __forceinline__ int phase3(const ApcgCtx& c, int j, Smem& sm) {
-  const double rr = grid_scalar(c, PS_RR, sm.red);
+template <typename T>
+__device__ __forceinline__ int phase3(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
+  const double rr = grid_scalar(c.part, c.P, PS_RR, sm.red);
   if (rr <= c.tol2) {
     finish(c, 0, j + 1);
     return PH_STOP;
@@ -196,13 +226,9 @@ __device__ __forceinline__ int phase3(const ApcgCtx& c, int j, Smem& sm) {
     }
     __syncthreads();
     for (int col = warp; col < c.nc; col += TPB / 32) {
-      const double* g = c.Ginv + (int64_t)col * c.ldg;
-      double sacc = 0.0;
-      for (int k = lane; k < c.nc; k += 32) sacc += g[k] * sm.red[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      const double sacc = coarse_coef(c.Ginv, c.ldg, c.nc_dense, c.dinv, col, sm.red);
       if (lane == 0) {
-        sm.sv[col] = sacc;
+        sm.sv[col] = (T)sacc;
         if (blockIdx.x == 0) c.sfull[col] = sacc;  // for the per-phase kernel mode
       }
     }
@@ -211,48 +237,47 @@ __device__ __forceinline__ int phase3(const ApcgCtx& c, int j, Smem& sm) {
   return PH_CONTINUE;
 }
 
-__device__ __forceinline__ void phase4(const ApcgCtx& c) {
+template <typename T>
+__device__ __forceinline__ void phase4(const ApcgCtx<T>& c) {
   int a, e;
   col_slice(c.nc, c.P, blockIdx.x, a, e);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int col = a + warp; col < e; col += TPB / 32) {
-    const double* g = c.Ginv + (int64_t)col * c.ldg;
-    double s = 0.0;
-    for (int k = lane; k < c.nc; k += 32) s += g[k] * c.tfull[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double s = coarse_coef(c.Ginv, c.ldg, c.nc_dense, c.dinv, col, c.tfull);
     if (lane == 0) c.sfull[col] = s;
   }
 }
 
 // s_in_smem: s = Ginv t is already in sm.sv (small-augmentation path of phase 3 in the
 // same kernel); otherwise it is read from sfull.
-__device__ __forceinline__ void phase5(const ApcgCtx& c, int j, Smem& sm, bool s_in_smem) {
+template <typename T>
+__device__ __forceinline__ void phase5(const ApcgCtx<T>& c, int j, Smem<T>& sm, bool s_in_smem) {
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
-  double* z = c.Z + (int64_t)(j + 1) * c.ld;
+  T* z = c.Z + (int64_t)(j + 1) * c.ld;
   if (c.nc > 0) {
     if (!s_in_smem) {
-      for (int k = threadIdx.x; k < c.nc; k += TPB) sm.sv[k] = c.sfull[k];
+      for (int k = threadIdx.x; k < c.nc; k += TPB) sm.sv[k] = (T)c.sfull[k];
     }
     __syncthreads();
-    cta_gemv_n<true>(c.C, c.ld, c.nc, sm.sv, -1.0, c.u, z, r0, r1, sm.red);
+    cta_gemv_n<true, T>(c.C, c.ld, c.nc, sm.sv, T(-1), c.u, z, r0, r1, sm.red);
   } else {
     for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) z[row] = c.u[row];
     __syncthreads();
   }
   double rz = 0.0;
-  for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) rz += c.r[row] * z[row];
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) rz += (double)c.r[row] * (double)z[row];
   rz = block_sum(rz, sm.red);
   if (threadIdx.x == 0) c.part[blockIdx.x * PS_STRIDE + PS_RZ] = rz;
   const int base = c.reorth_full ? 0 : j;
   const int kk = j + 1 - base;
-  cta_gemv_t<false>(c.AW + (int64_t)base * c.ld, c.ld, kk, z, r0, r1, c.gpart + blockIdx.x * c.vld,
-                    sm.su, sm.red);
+  cta_gemv_t<false, T>(c.AW + (int64_t)base * c.ld, c.ld, kk, z, r0, r1, c.gpart + blockIdx.x * c.vld,
+                       sm.su, sm.red);
 }
 
-__device__ __forceinline__ int phase6(const ApcgCtx& c, int j, Smem& sm) {
-  const double rz = grid_scalar(c, PS_RZ, sm.red);
+template <typename T>
+__device__ __forceinline__ int phase6(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
+  const double rz = grid_scalar(c.part, c.P, PS_RZ, sm.red);
   if (!(rz > 0.0)) {
     finish(c, 2 /* KRS_ERR_NOT_SPD */, j + 1);
     return PH_STOP;
@@ -270,31 +295,33 @@ __device__ __forceinline__ int phase6(const ApcgCtx& c, int j, Smem& sm) {
   return PH_CONTINUE;
 }
 
-__device__ __forceinline__ void phase7(const ApcgCtx& c, int j, Smem& sm) {
+template <typename T>
+__device__ __forceinline__ void phase7(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
   const int base = c.reorth_full ? 0 : j;
   const int kk = j + 1 - base;
-  for (int k = threadIdx.x; k < kk; k += TPB) sm.sv[k] = c.gfull[k];
+  for (int k = threadIdx.x; k < kk; k += TPB) sm.sv[k] = (T)c.gfull[k];
   __syncthreads();
-  const double* z = c.Z + (int64_t)(j + 1) * c.ld;
-  double* wn = c.W + (int64_t)(j + 1) * c.ld;
-  cta_gemv_n<false>(c.W + (int64_t)base * c.ld, c.ld, kk, sm.sv, -1.0, z, wn, r0, r1, sm.red);
+  const T* z = c.Z + (int64_t)(j + 1) * c.ld;
+  T* wn = c.W + (int64_t)(j + 1) * c.ld;
+  cta_gemv_n<false, T>(c.W + (int64_t)base * c.ld, c.ld, kk, sm.sv, T(-1), z, wn, r0, r1, sm.red);
 }
 
 // ------------------------------------------------------------------------------------
 // persistent kernel: the whole iteration loop of one solve
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx c) {
+template <typename T>
+__global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx<T> c) {
   extern __shared__ double4_32a smem_raw4[];
-  Smem sm = smem_layout(reinterpret_cast<double*>(smem_raw4));
+  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
   unsigned long long target = 0;
   const int TO = 6;  // KRS_ERR_TIMEOUT
 #define KRS_SYNC()                                                                   \
   do {                                                                               \
     if (!grid_barrier(c.bar, target, (unsigned)c.P, c.ctrl, c.spin_limit, TO)) return; \
   } while (0)
-  for (int j = c.j0;; j++) {
+  for (int j = 0;; j++) {
     phase1(c, j, sm);
     KRS_SYNC();
     if (phase2(c, j, sm) == PH_STOP) return;
@@ -320,14 +347,16 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx c) {
 // ------------------------------------------------------------------------------------
 // per-phase kernels (kernels mode).  Each returns at once when the solve has ended.
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ bool ended(const ApcgCtx& c) {
+template <typename T>
+__device__ __forceinline__ bool ended(const ApcgCtx<T>& c) {
   return *((volatile int*)(c.ctrl + CTRL_DONE)) != 0;
 }
 
 #define KRS_PHASE_KERNEL(NAME, BODY)                                          \
-  __global__ void __launch_bounds__(TPB, 1) NAME(ApcgCtx c, int j) {         \
-    extern __shared__ double4_32a smem_raw4[];                                    \
-    Smem sm = smem_layout(reinterpret_cast<double*>(smem_raw4));              \
+  template <typename T>                                                       \
+  __global__ void __launch_bounds__(TPB, 1) NAME(ApcgCtx<T> c, int j) {      \
+    extern __shared__ double4_32a smem_raw4[];                                \
+    Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));       \
     if (ended(c)) return;                                                     \
     (void)sm;                                                                 \
     BODY;                                                                     \
@@ -346,16 +375,17 @@ KRS_PHASE_KERNEL(k_phase7, phase7(c, j, sm))
 // ------------------------------------------------------------------------------------
 
 // partial t = V^T y over the CTA's rows (y global)
-__global__ void __launch_bounds__(TPB, 1) k_gemv_t_part(const double* V, int64_t ld, int k, const double* y,
-                                                        int nbr, int npc, double* vpart, int64_t vld) {
+template <typename T>
+__global__ void __launch_bounds__(TPB, 1) k_gemv_t_part(const T* V, int64_t ld, int k, const T* y, int nbr,
+                                                        int npc, double* vpart, int64_t vld) {
   extern __shared__ double4_32a smem_raw4[];
-  Smem sm = smem_layout(reinterpret_cast<double*>(smem_raw4));
+  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
   int64_t r0, r1;
   cta_rows(nbr, npc, blockIdx.x, r0, r1);
-  cta_gemv_t<false>(V, ld, k, y, r0, r1, vpart + blockIdx.x * vld, sm.su, sm.red);
+  cta_gemv_t<false, T>(V, ld, k, y, r0, r1, vpart + blockIdx.x * vld, sm.su, sm.red);
 }
 
-// out[c] = sum_b vpart[b*vld + c]  (c < k), then (optional) s = Ginv * out
+// out[c] = sum_b vpart[b*vld + c]  (c < k)
 __global__ void k_reduce_cols(const double* vpart, int64_t vld, int P, int k, double* out) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= k) return;
@@ -363,41 +393,38 @@ __global__ void k_reduce_cols(const double* vpart, int64_t vld, int P, int k, do
   if ((threadIdx.x & 31) == 0) out[warp] = v;
 }
 
-__global__ void k_small_gemv(const double* G, int ldg, int k, const double* t, double* s) {
+__global__ void k_small_gemv(const double* G, int ldg, int k, int k_dense, const double* dinv, const double* t,
+                             double* s) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= k) return;
-  const double* g = G + (int64_t)warp * ldg;
-  double a = 0.0;
-  for (int i = lane; i < k; i += 32) a += g[i] * t[i];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  const double a = coarse_coef(G, ldg, k_dense, dinv, warp, t);
   if (lane == 0) s[warp] = a;
 }
 
 // x = C s, r = b - AC s (or x = 0, r = b when k == 0); partials (b, b) and (r, r)
-__global__ void __launch_bounds__(TPB, 1) k_init_xr(const double* C, const double* AC, int64_t ld, int k,
-                                                    const double* s, const double* b, double* x, double* r,
-                                                    int nbr, int npc, double* part) {
+template <typename T>
+__global__ void __launch_bounds__(TPB, 1) k_init_xr(const T* C, const T* AC, int64_t ld, int k, const double* s,
+                                                    const T* b, T* x, T* r, int nbr, int npc, double* part) {
   extern __shared__ double4_32a smem_raw4[];
-  Smem sm = smem_layout(reinterpret_cast<double*>(smem_raw4));
+  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
   int64_t r0, r1;
   cta_rows(nbr, npc, blockIdx.x, r0, r1);
   if (k > 0) {
-    for (int i = threadIdx.x; i < k; i += TPB) sm.sv[i] = s[i];
+    for (int i = threadIdx.x; i < k; i += TPB) sm.sv[i] = (T)s[i];
     __syncthreads();
-    cta_gemv_n<false>(C, ld, k, sm.sv, 1.0, nullptr, x, r0, r1, sm.red);
-    cta_gemv_n<false>(AC, ld, k, sm.sv, -1.0, b, r, r0, r1, sm.red);
+    cta_gemv_n<false, T>(C, ld, k, sm.sv, T(1), nullptr, x, r0, r1, sm.red);
+    cta_gemv_n<false, T>(AC, ld, k, sm.sv, T(-1), b, r, r0, r1, sm.red);
   } else {
     for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
-      x[row] = 0.0;
+      x[row] = T(0);
       r[row] = b[row];
     }
     __syncthreads();
   }
   double bb = 0.0, rr = 0.0;
   for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
-    bb += b[row] * b[row];
-    rr += r[row] * r[row];
+    bb += (double)b[row] * (double)b[row];
+    rr += (double)r[row] * (double)r[row];
   }
   block_sum2(bb, rr, sm.red);
   if (threadIdx.x == 0) {
@@ -407,23 +434,24 @@ __global__ void __launch_bounds__(TPB, 1) k_init_xr(const double* C, const doubl
 }
 
 // u = M^-1 r
-__global__ void k_precond_rows(int kind, const double* minv, const double* r, double* u, int64_t n) {
+template <typename T>
+__global__ void k_precond_rows(int kind, const T* minv, const T* r, T* u, int64_t n) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row < n) u[row] = precond_row(kind, minv, r, row);
+  if (row < n) u[row] = precond_row<T>(kind, minv, r, row);
 }
 
 // z0 = u - C s (or u), W[:,0] = Z[:,0] = z0, partial (r, z0)
-__global__ void __launch_bounds__(TPB, 1) k_init_z(const double* C, int64_t ld, int k, const double* s,
-                                                   const double* u, const double* r, double* Z, double* W,
-                                                   int nbr, int npc, double* part) {
+template <typename T>
+__global__ void __launch_bounds__(TPB, 1) k_init_z(const T* C, int64_t ld, int k, const double* s, const T* u,
+                                                   const T* r, T* Z, T* W, int nbr, int npc, double* part) {
   extern __shared__ double4_32a smem_raw4[];
-  Smem sm = smem_layout(reinterpret_cast<double*>(smem_raw4));
+  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
   int64_t r0, r1;
   cta_rows(nbr, npc, blockIdx.x, r0, r1);
   if (k > 0) {
-    for (int i = threadIdx.x; i < k; i += TPB) sm.sv[i] = s[i];
+    for (int i = threadIdx.x; i < k; i += TPB) sm.sv[i] = (T)s[i];
     __syncthreads();
-    cta_gemv_n<false>(C, ld, k, sm.sv, -1.0, u, Z, r0, r1, sm.red);
+    cta_gemv_n<false, T>(C, ld, k, sm.sv, T(-1), u, Z, r0, r1, sm.red);
   } else {
     for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) Z[row] = u[row];
     __syncthreads();
@@ -431,7 +459,7 @@ __global__ void __launch_bounds__(TPB, 1) k_init_z(const double* C, int64_t ld, 
   double rz = 0.0;
   for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
     W[row] = Z[row];
-    rz += r[row] * Z[row];
+    rz += (double)r[row] * (double)Z[row];
   }
   rz = block_sum(rz, sm.red);
   if (threadIdx.x == 0) part[blockIdx.x * PS_STRIDE + 2] = rz;
@@ -456,91 +484,126 @@ size_t apcg_smem_bytes(int kmax) {
   return sizeof(double) * (size_t)(ROW_CHUNK + 4 * TPB + ((kmax + 3) & ~3));
 }
 
-static ApcgCtx make_ctx(const IterArgs& a) {
-  ApcgCtx c;
+template <typename T>
+static ApcgCtx<T> make_ctx(const IterArgs& a) {
+  ApcgCtx<T> c;
   c.n = a.n; c.ld = a.ld; c.nbr = a.nbr; c.npc = a.npc; c.P = a.P;
   c.nc = a.nc; c.ldg = a.ldg; c.max_iter = a.max_iter; c.reorth_full = a.reorth_full;
-  c.precond = a.precond; c.j0 = 0; c.tol2 = a.tol2; c.spin_limit = a.spin_limit;
-  c.rp = a.rp; c.ci = a.ci; c.vals = a.vals; c.minv = a.minv;
-  c.C = a.C; c.AC = a.AC; c.Ginv = a.Ginv;
-  c.W = a.W; c.AW = a.AW; c.Z = a.Z; c.x = a.x; c.r = a.r; c.u = a.u;
+  c.nc_dense = a.nc_dense; c.dinv = a.dinv;
+  c.precond = a.precond; c.tol2 = a.tol2; c.spin_limit = a.spin_limit;
+  c.rp = a.rp; c.ci = a.ci;
+  c.vals = static_cast<const T*>(a.vals); c.minv = static_cast<const T*>(a.minv);
+  c.C = static_cast<const T*>(a.C); c.AC = static_cast<const T*>(a.AC); c.Ginv = a.Ginv;
+  c.W = static_cast<T*>(a.W); c.AW = static_cast<T*>(a.AW); c.Z = static_cast<T*>(a.Z);
+  c.x = static_cast<T*>(a.x); c.r = static_cast<T*>(a.r); c.u = static_cast<T*>(a.u);
   c.alpha = a.alpha; c.gamma = a.gamma; c.rho = a.rho;
   c.tfull = a.tfull; c.sfull = a.sfull; c.gfull = a.gfull;
   c.part = a.part; c.vpart = a.vpart; c.gpart = a.gpart; c.vld = a.vld; c.ctrl = a.ctrl; c.bar = a.bar;
   return c;
 }
 
-cudaError_t apcg_prepare_attributes(int kmax) {
-  const size_t sm = apcg_smem_bytes(kmax);
-  cudaError_t e = cudaSuccess;
-  const void* fns[] = {(const void*)k_apcg_persistent, (const void*)k_phase1, (const void*)k_phase2,
-                       (const void*)k_phase3, (const void*)k_phase4, (const void*)k_phase5,
-                       (const void*)k_phase6, (const void*)k_phase7, (const void*)k_gemv_t_part,
-                       (const void*)k_init_xr, (const void*)k_init_z};
+template <typename T>
+static cudaError_t prepare_attributes_t(size_t sm) {
+  const void* fns[] = {(const void*)k_apcg_persistent<T>, (const void*)k_phase1<T>, (const void*)k_phase2<T>,
+                       (const void*)k_phase3<T>, (const void*)k_phase4<T>, (const void*)k_phase5<T>,
+                       (const void*)k_phase6<T>, (const void*)k_phase7<T>, (const void*)k_gemv_t_part<T>,
+                       (const void*)k_init_xr<T>, (const void*)k_init_z<T>};
   for (const void* f : fns) {
-    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  return e;
+  return cudaSuccess;
 }
 
-cudaError_t apcg_max_coresident(int kmax, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_apcg_persistent, TPB,
+cudaError_t apcg_prepare_attributes(int kmax, bool fp32) {
+  const size_t sm = apcg_smem_bytes(kmax);
+  return fp32 ? prepare_attributes_t<float>(sm) : prepare_attributes_t<double>(sm);
+}
+
+cudaError_t apcg_max_coresident(int kmax, bool fp32, int* blocks_per_sm) {
+  if (fp32)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_apcg_persistent<float>, TPB,
+                                                         apcg_smem_bytes(kmax));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_apcg_persistent<double>, TPB,
                                                        apcg_smem_bytes(kmax));
 }
 
-// Set-up of x_0, r_0, z_0, w_0, rho_0, ||b||^2, ||r_0||^2 (scal[0..1]).  Counts launches.
-cudaError_t apcg_launch_init(const IterArgs& a, const double* b, double* scal, cudaStream_t st,
-                             int64_t* launches) {
+template <typename T>
+static cudaError_t launch_init_t(const IterArgs& a, const void* bv, double* scal, cudaStream_t st,
+                                 int64_t* launches) {
   const size_t sm = apcg_smem_bytes(a.kmax);
   const int k = a.nc;
+  const T* b = static_cast<const T*>(bv);
+  const T* C = static_cast<const T*>(a.C);
+  const T* AC = static_cast<const T*>(a.AC);
+  T* x = static_cast<T*>(a.x);
+  T* r = static_cast<T*>(a.r);
+  T* u = static_cast<T*>(a.u);
   if (k > 0) {
-    k_gemv_t_part<<<a.P, TPB, sm, st>>>(a.C, a.ld, k, b, a.nbr, a.npc, a.vpart, a.vld);
+    k_gemv_t_part<T><<<a.P, TPB, sm, st>>>(C, a.ld, k, b, a.nbr, a.npc, a.vpart, a.vld);
     k_reduce_cols<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.vpart, a.vld, a.P, k, a.tfull);
-    k_small_gemv<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.Ginv, a.ldg, k, a.tfull, a.sfull);
+    k_small_gemv<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.Ginv, a.ldg, k, a.nc_dense, a.dinv, a.tfull, a.sfull);
     *launches += 3;
   }
-  k_init_xr<<<a.P, TPB, sm, st>>>(a.C, a.AC, a.ld, k, a.sfull, b, a.x, a.r, a.nbr, a.npc, a.part);
-  k_precond_rows<<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a.precond, a.minv, a.r, a.u, a.n);
+  k_init_xr<T><<<a.P, TPB, sm, st>>>(C, AC, a.ld, k, a.sfull, b, x, r, a.nbr, a.npc, a.part);
+  k_precond_rows<T><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a.precond, static_cast<const T*>(a.minv), r, u,
+                                                                     a.n);
   *launches += 2;
   if (k > 0) {
-    k_gemv_t_part<<<a.P, TPB, sm, st>>>(a.AC, a.ld, k, a.u, a.nbr, a.npc, a.vpart, a.vld);
+    k_gemv_t_part<T><<<a.P, TPB, sm, st>>>(AC, a.ld, k, u, a.nbr, a.npc, a.vpart, a.vld);
     k_reduce_cols<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.vpart, a.vld, a.P, k, a.tfull);
-    k_small_gemv<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.Ginv, a.ldg, k, a.tfull, a.sfull);
+    k_small_gemv<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.Ginv, a.ldg, k, a.nc_dense, a.dinv, a.tfull, a.sfull);
     *launches += 3;
   }
-  k_init_z<<<a.P, TPB, sm, st>>>(a.C, a.ld, k, a.sfull, a.u, a.r, a.Z, a.W, a.nbr, a.npc, a.part);
+  k_init_z<T><<<a.P, TPB, sm, st>>>(C, a.ld, k, a.sfull, u, r, static_cast<T*>(a.Z), static_cast<T*>(a.W), a.nbr,
+                                    a.npc, a.part);
   k_init_finish<<<1, 96, 0, st>>>(a.part, a.P, scal, a.rho);
   *launches += 2;
   return cudaGetLastError();
 }
 
+// Set-up of x_0, r_0, z_0, w_0, rho_0, ||b||^2, ||r_0||^2 (scal[0..1]).  Counts launches.
+cudaError_t apcg_launch_init(const IterArgs& a, const void* b, double* scal, cudaStream_t st, int64_t* launches) {
+  return a.fp32 ? launch_init_t<float>(a, b, scal, st, launches) : launch_init_t<double>(a, b, scal, st, launches);
+}
+
 cudaError_t apcg_launch_persistent(const IterArgs& a, cudaStream_t st, int64_t* launches) {
-  ApcgCtx c = make_ctx(a);
-  void* args[] = {&c};
   *launches += 1;
-  return cudaLaunchCooperativeKernel((const void*)k_apcg_persistent, dim3(a.P), dim3(TPB), args,
+  if (a.fp32) {
+    ApcgCtx<float> c = make_ctx<float>(a);
+    void* args[] = {&c};
+    return cudaLaunchCooperativeKernel((const void*)k_apcg_persistent<float>, dim3(a.P), dim3(TPB), args,
+                                       apcg_smem_bytes(a.kmax), st);
+  }
+  ApcgCtx<double> c = make_ctx<double>(a);
+  void* args[] = {&c};
+  return cudaLaunchCooperativeKernel((const void*)k_apcg_persistent<double>, dim3(a.P), dim3(TPB), args,
                                      apcg_smem_bytes(a.kmax), st);
+}
+
+template <typename T>
+static cudaError_t launch_phases_t(const IterArgs& a, int j0, int j1, cudaStream_t st, int64_t* launches) {
+  ApcgCtx<T> c = make_ctx<T>(a);
+  const size_t sm = apcg_smem_bytes(a.kmax);
+  for (int j = j0; j < j1; j++) {
+    k_phase1<T><<<a.P, TPB, sm, st>>>(c, j);
+    k_phase2<T><<<a.P, TPB, sm, st>>>(c, j);
+    k_phase3<T><<<a.P, TPB, sm, st>>>(c, j);
+    if (a.nc > SMALL_NC) {
+      k_phase4<T><<<a.P, TPB, sm, st>>>(c, j);
+      *launches += 1;
+    }
+    k_phase5<T><<<a.P, TPB, sm, st>>>(c, j);
+    k_phase6<T><<<a.P, TPB, sm, st>>>(c, j);
+    k_phase7<T><<<a.P, TPB, sm, st>>>(c, j);
+    *launches += 6;
+  }
+  return cudaGetLastError();
 }
 
 // Launch the phases of iterations [j0, j1) (kernels mode).
 cudaError_t apcg_launch_phases(const IterArgs& a, int j0, int j1, cudaStream_t st, int64_t* launches) {
-  ApcgCtx c = make_ctx(a);
-  const size_t sm = apcg_smem_bytes(a.kmax);
-  for (int j = j0; j < j1; j++) {
-    k_phase1<<<a.P, TPB, sm, st>>>(c, j);
-    k_phase2<<<a.P, TPB, sm, st>>>(c, j);
-    k_phase3<<<a.P, TPB, sm, st>>>(c, j);
-    if (a.nc > SMALL_NC) {
-      k_phase4<<<a.P, TPB, sm, st>>>(c, j);
-      *launches += 1;
-    }
-    k_phase5<<<a.P, TPB, sm, st>>>(c, j);
-    k_phase6<<<a.P, TPB, sm, st>>>(c, j);
-    k_phase7<<<a.P, TPB, sm, st>>>(c, j);
-    *launches += 6;
-  }
-  return cudaGetLastError();
+  return a.fp32 ? launch_phases_t<float>(a, j0, j1, st, launches) : launch_phases_t<double>(a, j0, j1, st, launches);
 }
 
 }  // namespace krs

@@ -128,6 +128,16 @@ struct krs_seq {
   double* gram_scratch = nullptr;
   size_t gram_cap = 0;
 
+  // FP32 copies for the inner solves of the mixed-precision refinement
+  float *vals32 = nullptr, *minv32 = nullptr, *C32 = nullptr, *AC32 = nullptr;
+  float *W32 = nullptr, *AW32 = nullptr, *Z32 = nullptr;
+  float *x32 = nullptr, *r32 = nullptr, *u32 = nullptr, *b32 = nullptr;
+  double* dinv = nullptr;  // 1/(w, Aw) of the inner directions appended within one system
+  int64_t vals32_cap = 0;
+  int cap_c32 = 0, cap_w32 = 0;
+  bool vals32_valid = false;
+  int minv32_kind = -1;
+
   // pinned host mirrors
   double* h_scal = nullptr;
   int* h_ctrl = nullptr;
@@ -135,10 +145,11 @@ struct krs_seq {
   // last solve
   krs_solve_stats st{};
   int last_m = 0;
+  int last_ritz_m = 0;
   int last_srks = 0;
   int last_nsel = 0;
   long long spin_limit = kDefaultSpin;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 // ------------------------------------------------------------------------------------
@@ -334,6 +345,8 @@ krs_status krs_policy_default(krs_policy* p) {
   p->cap_mode = KRS_CAP_TRUNCATE;
   p->max_iter = 2000;
   p->exec = KRS_EXEC_PERSISTENT;
+  p->inner_tol = 0.1;
+  p->max_outer = 30;
   return KRS_OK;
 }
 
@@ -399,7 +412,7 @@ krs_status krs_create_sequence(int64_t n, const krs_device* dev, krs_seq_t* out)
     cudaGetLastError();
     return bail(fail(KRS_ERR_OOM, "pinned host allocation failed"));
   }
-  for (int i = 0; i < 4; i++) {
+  for (int i = 0; i < 6; i++) {
     if (cudaEventCreate(&s->ev[i]) != cudaSuccess) return bail(fail(KRS_ERR_CUDA, "cudaEventCreate failed"));
   }
   *out = s;
@@ -414,7 +427,7 @@ krs_status krs_destroy_sequence(krs_seq_t s) {
   for (void* p : all) dev_free(s, p);
   if (s->h_scal) cudaFreeHost(s->h_scal);
   if (s->h_ctrl) cudaFreeHost(s->h_ctrl);
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < 6; i++)
     if (s->ev[i]) cudaEventDestroy(s->ev[i]);
   delete s;
   return KRS_OK;
@@ -490,7 +503,7 @@ krs_status krs_last_coeffs(krs_seq_t s, double* alpha, double* rho, double* gamm
 
 krs_status krs_last_ritz(krs_seq_t s, double* theta_m, double* theta_m1, int32_t* sel) {
   if (!s) return fail(KRS_ERR_INVALID_ARG, "NULL sequence");
-  const int m = s->last_m;
+  const int m = s->last_ritz_m;
   if (!s->last_srks || m < 2) return KRS_OK;
   KRS_CUDA(cudaSetDevice(s->device));
   if (theta_m) KRS_CUDA(cudaMemcpyAsync(theta_m, s->theta_m, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream));
@@ -509,6 +522,7 @@ krs_status krs_last_vectors(krs_seq_t s, int32_t which, double* out) {
   if (!out) return fail(KRS_ERR_INVALID_ARG, "NULL output");
   KRS_CUDA(cudaSetDevice(s->device));
   const double* src = which == 0 ? s->W : (which == 1 ? s->AW : s->Z);
+  if (!src) return fail(KRS_ERR_INVALID_ARG, "the last solve stored no FP64 vectors (mixed precision)");
   const bool dv = is_device_ptr(out);
   KRS_CUDA(cudaMemcpy2DAsync(out, sizeof(double) * s->n, src, sizeof(double) * s->ld, sizeof(double) * s->n, m,
                              dv ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
@@ -526,7 +540,9 @@ static krs_status validate_policy(const krs_policy* p) {
   if (p->recycle < 0 || p->recycle > 2) return fail(KRS_ERR_INVALID_ARG, "bad recycle %d", p->recycle);
   if (p->precond < 0 || p->precond > 2) return fail(KRS_ERR_INVALID_ARG, "bad precond %d", p->precond);
   if (p->reorth < 0 || p->reorth > 1) return fail(KRS_ERR_INVALID_ARG, "bad reorth %d", p->reorth);
-  if (p->precision != KRS_FP64) return fail(KRS_ERR_INVALID_ARG, "precision %d not supported by this call", p->precision);
+  if (p->precision != KRS_FP64 && p->precision != KRS_MIXED_IR)
+    return fail(KRS_ERR_INVALID_ARG, "bad precision %d", p->precision);
+  if (!(p->inner_tol == p->inner_tol) || p->inner_tol >= 1.0) return fail(KRS_ERR_INVALID_ARG, "inner_tol must be < 1");
   if (p->cap_mode < 0 || p->cap_mode > 1) return fail(KRS_ERR_INVALID_ARG, "bad cap_mode %d", p->cap_mode);
   if (p->max_aug < 0) return fail(KRS_ERR_INVALID_ARG, "bad max_aug %d", p->max_aug);
   if (p->max_iter < 1 || p->max_iter > 16000) return fail(KRS_ERR_INVALID_ARG, "max_iter %d outside [1, 16000]", p->max_iter);
@@ -591,21 +607,178 @@ static krs_status read_status(krs_seq* s, int* st) {
   return KRS_OK;
 }
 
+// FP32 storage of the mixed-precision inner solves (sized like the FP64 state)
+static krs_status ensure_mixed(krs_seq* s, int max_iter, int64_t nnzb) {
+  if (!s->x32) {
+    KRS_TRY(alloc_n(s, &s->x32, s->ld));
+    KRS_TRY(alloc_n(s, &s->r32, s->ld));
+    KRS_TRY(alloc_n(s, &s->u32, s->ld));
+    KRS_TRY(alloc_n(s, &s->b32, s->ld));
+    KRS_TRY(alloc_n(s, &s->minv32, 3 * s->ld + 64));
+  }
+  if (nnzb > s->vals32_cap) {
+    dev_free(s, s->vals32);
+    s->vals32 = nullptr;
+    KRS_TRY(alloc_n(s, &s->vals32, (size_t)nnzb * 9 + 4));
+    s->vals32_cap = nnzb;
+    s->vals32_valid = false;
+  }
+  const int needw = max_iter + 1;
+  if (needw > s->cap_w32) {
+    const int cap = (int)round_up(needw, 32);
+    dev_free(s, s->W32);
+    dev_free(s, s->AW32);
+    dev_free(s, s->Z32);
+    s->W32 = s->AW32 = s->Z32 = nullptr;
+    KRS_TRY(alloc_n(s, &s->W32, (size_t)cap * s->ld));
+    KRS_TRY(alloc_n(s, &s->AW32, (size_t)cap * s->ld));
+    KRS_TRY(alloc_n(s, &s->Z32, (size_t)cap * s->ld));
+    s->cap_w32 = cap;
+    // the scalar arrays (alpha, gamma, rho, g) are shared with the FP64 path
+    KRS_TRY(ensure_cap_w(s, 0));
+    if (s->cap_w < needw) {
+      dev_free(s, s->alpha);
+      dev_free(s, s->gamma);
+      dev_free(s, s->rho);
+      dev_free(s, s->gfull);
+      KRS_TRY(alloc_n(s, &s->alpha, cap));
+      KRS_TRY(alloc_n(s, &s->gamma, cap));
+      KRS_TRY(alloc_n(s, &s->rho, cap + 1));
+      KRS_TRY(alloc_n(s, &s->gfull, cap));
+    }
+  }
+  // C32 / AC32 hold C, then the directions of the earlier inner solves of the same system
+  if (s->cap_c + s->cap_w32 > s->cap_c32) {
+    const int cap = s->cap_c + s->cap_w32;
+    dev_free(s, s->C32);
+    dev_free(s, s->AC32);
+    dev_free(s, s->dinv);
+    s->C32 = s->AC32 = nullptr;
+    s->dinv = nullptr;
+    KRS_TRY(alloc_n(s, &s->C32, (size_t)cap * s->ld));
+    KRS_TRY(alloc_n(s, &s->AC32, (size_t)cap * s->ld));
+    KRS_TRY(alloc_n(s, &s->dinv, (size_t)s->cap_w32));
+    s->cap_c32 = cap;
+  }
+  return KRS_OK;
+}
+
+// One APCG solve (init + iterations) for the IterArgs `a` with right-hand side b_in (device,
+// a's value type), to ||r|| <= tol ||b_in||.  Adds the iteration kernels' event time to
+// *t_iter_ms.  Returns the krs_status of the CUDA calls; the solve's own outcome is in
+// *status, its iteration count in *m and ||b_in||^2 in *bb.
+static krs_status run_apcg(krs_seq* s, IterArgs& a, const void* b_in, double tol, int exec, int* status, int* m,
+                           double* bb, float* t_iter_ms, int64_t* launches) {
+  KRS_CUDA(apcg_launch_init(a, b_in, s->scal, s->stream, launches));
+  KRS_CUDA(cudaMemcpyAsync(s->h_scal, s->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  *bb = s->h_scal[0];
+  const double rr0 = s->h_scal[1];
+  *status = KRS_OK;
+  *m = 0;
+  if (!isfinite(*bb)) return fail(KRS_ERR_INVALID_ARG, "right-hand side is not finite");
+  a.tol2 = tol * tol * (*bb);
+  if (rr0 <= a.tol2) return KRS_OK;
+  KRS_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, s->stream));
+  KRS_CUDA(cudaMemsetAsync(s->bar, 0, sizeof(unsigned long long), s->stream));
+  KRS_CUDA(cudaEventRecord(s->ev[4], s->stream));
+  if (exec == KRS_EXEC_PERSISTENT) {
+    KRS_CUDA(apcg_launch_persistent(a, s->stream, launches));
+    KRS_CUDA(cudaEventRecord(s->ev[5], s->stream));
+    KRS_CUDA(cudaMemcpyAsync(s->h_ctrl, s->ctrl, sizeof(int) * CTRL_WORDS, cudaMemcpyDeviceToHost, s->stream));
+    KRS_CUDA(cudaStreamSynchronize(s->stream));
+  } else {
+    int j = 0;
+    const int batch = 16;
+    for (;;) {
+      const int j1 = (j + batch < a.max_iter) ? j + batch : a.max_iter;
+      KRS_CUDA(apcg_launch_phases(a, j, j1, s->stream, launches));
+      KRS_CUDA(cudaMemcpyAsync(s->h_ctrl, s->ctrl, sizeof(int) * CTRL_WORDS, cudaMemcpyDeviceToHost, s->stream));
+      KRS_CUDA(cudaStreamSynchronize(s->stream));
+      j = j1;
+      if (s->h_ctrl[CTRL_DONE] || j >= a.max_iter) break;
+    }
+    KRS_CUDA(cudaEventRecord(s->ev[5], s->stream));
+    KRS_CUDA(cudaEventSynchronize(s->ev[5]));
+  }
+  float dt = 0.f;
+  cudaEventElapsedTime(&dt, s->ev[4], s->ev[5]);
+  *t_iter_ms += dt;
+  *status = s->h_ctrl[CTRL_STATUS];
+  *m = s->h_ctrl[CTRL_M];
+  if (!s->h_ctrl[CTRL_DONE] && *status == KRS_OK) *status = KRS_ERR_CUDA;
+  return KRS_OK;
+}
+
+// SRKS extraction (Algorithm 3) from the coefficients of an m-iteration solve and its z's
+// (FP64 or FP32): selected Ritz vectors written to C[:, nc .. nc + *cnt) (not yet counted in
+// s->nc).  room: how many may be appended.
+static krs_status srks_extract(krs_seq* s, int m, int nc, int room, const krs_policy* p, const double* Z,
+                               const float* Z32, int* cnt, int64_t* launches) {
+  *cnt = 0;
+  s->last_srks = 1;
+  s->last_ritz_m = m;
+  KRS_TRY(ensure_eig(s, m));
+  KRS_CUDA(launch_lanczos(m, s->alpha, s->rho, s->delta, s->eta, s->stream));
+  KRS_CUDA(launch_tridiag_eigvals2(m, m - 1, s->delta, s->eta, s->theta_m, s->theta_m1, s->stream));
+  KRS_CUDA(launch_srks_select(m, s->theta_m, s->theta_m1, p->ritz_eps, p->theta_frac, room, s->sel, s->selcount,
+                              s->tsel, s->stream));
+  *launches += 3;
+  KRS_CUDA(cudaMemcpyAsync(&s->h_ctrl[16], s->selcount, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  const int k = s->h_ctrl[16];
+  s->last_nsel = k;
+  if (k <= 0) return KRS_OK;
+  if (nc + k > s->cap_c) {
+    if (Z32) return fail(KRS_ERR_INVALID_ARG, "internal: augmentation capacity not reserved");
+    KRS_TRY(ensure_cap_c(s, nc + k));  // FP64 path: nothing else uses C, AC, G^-1 now
+  }
+  const size_t wneed = eigvecs_work_doubles(m, k) + (size_t)m * k * 2;
+  dev_free(s, s->eigwork);
+  s->eigwork = nullptr;
+  KRS_TRY(alloc_n(s, &s->eigwork, wneed));
+  double* Q = s->eigwork;
+  double* Fm = s->eigwork + (size_t)m * k;
+  double* wk = s->eigwork + 2 * (size_t)m * k;
+  KRS_CUDA(launch_tridiag_eigvecs(m, s->delta, s->eta, k, s->tsel, Q, wk, s->stream));
+  if (Z32)
+    KRS_CUDA(launch_ritz_vectors_f(s->n, s->ld, m, k, Z32, s->rho, Q, s->tsel, Fm, s->C + (size_t)nc * s->ld,
+                                   s->stream));
+  else
+    KRS_CUDA(launch_ritz_vectors(s->n, s->ld, m, k, Z, s->rho, Q, s->tsel, Fm, s->C + (size_t)nc * s->ld, s->stream));
+  *launches += 3;
+  *cnt = k;
+  return KRS_OK;
+}
+
+__global__ void k_recip(const double* __restrict__ src, double* __restrict__ dst, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = 1.0 / src[i];
+}
+
+__global__ void k_f2d_cols(const float* __restrict__ src, double* __restrict__ dst, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
 static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, double* x, double tol,
                              const krs_policy* p) {
   krs_solve_stats st{};
   st.n_c = s->nc;
   s->st = st;
   s->last_m = 0;
+  s->last_ritz_m = 0;
   s->last_srks = 0;
   s->last_nsel = 0;
   int64_t launches = 0;
+  const bool mixed = p->precision == KRS_MIXED_IR;
   KRS_CUDA(cudaSetDevice(s->device));
   KRS_CUDA(cudaEventRecord(s->ev[0], s->stream));
 
   // ---- matrix, preconditioner
   bool changed = false;
   KRS_TRY(upload_matrix(s, A, &changed));
+  if (changed) s->vals32_valid = false;
   if (s->precond_built != p->precond) {
     KRS_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, s->stream));
     KRS_CUDA(launch_precond_setup(p->precond, s->nbr, s->rp_use, s->ci_use, s->vals_use, s->minv, s->ctrl + CTRL_STATUS,
@@ -616,6 +789,7 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
     if (code) return fail((krs_status)code, code == KRS_ERR_NOT_SPD ? "preconditioner: a diagonal block is not positive definite"
                                                                     : "preconditioner: missing diagonal block");
     s->precond_built = p->precond;
+    s->minv32_kind = -1;
   }
 
   // ---- right-hand side into the padded device vector
@@ -623,19 +797,34 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
   KRS_CUDA(cudaMemcpyAsync(s->b, b, sizeof(double) * s->n, b_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                            s->stream));
 
-  // ---- storage
-  KRS_TRY(ensure_cap_w(s, p->max_iter));
-  const int kmax = (s->nc > p->max_iter + 1) ? s->nc : p->max_iter + 1;
-  KRS_CUDA(apcg_prepare_attributes(kmax));
+  // ---- storage, augmentation capacity for this solve's recycling step, partition
+  const int nc = s->nc;
+  const int cap = p->max_aug > 0 ? p->max_aug : 0x7fffffff;
+  int room = 0;
+  if (p->recycle != KRS_RECYCLE_NONE) {
+    room = (p->cap_mode == KRS_CAP_TRUNCATE) ? (cap - nc > 0 ? cap - nc : 0) : p->max_iter + 1;
+    if (room > p->max_iter + 1) room = p->max_iter + 1;
+  }
+  // The mixed path appends after its first inner solve while later inner solves still use
+  // C, AC and G^-1, so the room is reserved now; the FP64 path grows after its solve.
+  if (mixed) {
+    KRS_TRY(ensure_cap_c(s, nc + room));
+    KRS_TRY(ensure_mixed(s, p->max_iter, A->nnzb));
+  } else {
+    KRS_TRY(ensure_cap_c(s, nc));
+    KRS_TRY(ensure_cap_w(s, p->max_iter));
+  }
+  // largest column count a tall-skinny phase sees (mixed: C plus earlier inner directions)
+  const int kmax = mixed ? nc + p->max_iter + 1 : ((nc > p->max_iter + 1) ? nc : p->max_iter + 1);
+  KRS_CUDA(apcg_prepare_attributes(kmax, mixed));
   int bps = 0;
-  KRS_CUDA(apcg_max_coresident(kmax, &bps));
+  KRS_CUDA(apcg_max_coresident(kmax, mixed, &bps));
   if (bps < 1) return fail(KRS_ERR_CUDA, "persistent kernel cannot be resident (kmax %d)", kmax);
   int P = 0, npc = 0;
   partition(s, bps, &P, &npc);
   KRS_TRY(ensure_vpart(s, P, kmax));
 
-  // ---- coarse set-up: A C (new columns), C^T A C (new tiles), Cholesky and inverse
-  const int nc = s->nc;
+  // ---- coarse set-up (FP64): A C (new columns), C^T A C (new tiles), Cholesky and inverse
   if (nc > 0) {
     if (s->ac_valid < nc) {
       KRS_CUDA(launch_spmm(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->C, s->AC, s->ld, s->ac_valid, nc, s->stream));
@@ -671,59 +860,154 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
     }
   }
 
-  // ---- initialisation
+  // ---- FP32 copies for the inner solves
+  if (mixed) {
+    if (!s->vals32_valid) {
+      KRS_CUDA(launch_d2f(s->vals_use, s->vals32, 9 * A->nnzb, s->stream));
+      s->vals32_valid = true;
+      launches++;
+    }
+    if (s->minv32_kind != p->precond) {
+      KRS_CUDA(launch_d2f(s->minv, s->minv32, (p->precond == KRS_PRECOND_BLOCK_JACOBI3) ? 9 * (int64_t)s->nbr : s->n,
+                          s->stream));
+      s->minv32_kind = p->precond;
+      launches++;
+    }
+    if (nc > 0) {
+      KRS_CUDA(launch_d2f(s->C, s->C32, (int64_t)nc * s->ld, s->stream));
+      KRS_CUDA(launch_d2f(s->AC, s->AC32, (int64_t)nc * s->ld, s->stream));
+      launches += 2;
+    }
+  }
+
   IterArgs a{};
   a.n = s->n; a.ld = s->ld; a.nbr = s->nbr; a.npc = npc; a.P = P;
-  a.nc = nc; a.ldg = s->cap_c; a.max_iter = p->max_iter; a.reorth_full = (p->reorth == KRS_REORTH_FULL);
-  a.precond = p->precond; a.kmax = kmax; a.spin_limit = s->spin_limit;
-  a.rp = s->rp_use; a.ci = s->ci_use; a.vals = s->vals_use; a.minv = s->minv;
-  a.C = s->C; a.AC = s->AC; a.Ginv = s->Ginv;
-  a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.x = s->x; a.r = s->r; a.u = s->u;
+  a.nc = nc; a.nc_dense = nc; a.dinv = s->dinv;
+  a.ldg = s->cap_c; a.max_iter = p->max_iter; a.reorth_full = (p->reorth == KRS_REORTH_FULL);
+  a.precond = p->precond; a.kmax = kmax; a.spin_limit = s->spin_limit; a.fp32 = mixed;
+  a.rp = s->rp_use; a.ci = s->ci_use; a.Ginv = s->Ginv;
   a.alpha = s->alpha; a.gamma = s->gamma; a.rho = s->rho;
   a.tfull = s->tfull; a.sfull = s->sfull; a.gfull = s->gfull;
   a.part = s->part; a.vpart = s->vpart; a.gpart = s->gpart; a.vld = s->vld; a.ctrl = s->ctrl; a.bar = s->bar;
-  KRS_CUDA(apcg_launch_init(a, s->b, s->scal, s->stream, &launches));
-  KRS_CUDA(cudaMemcpyAsync(s->h_scal, s->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  KRS_CUDA(cudaStreamSynchronize(s->stream));
-  const double bb = s->h_scal[0], rr0 = s->h_scal[1];
-  if (!isfinite(bb)) return fail(KRS_ERR_INVALID_ARG, "right-hand side is not finite");
-  a.tol2 = tol * tol * bb;
-
-  // ---- iterations (events bracket exactly the iteration kernel launch(es))
-  int status = KRS_OK, m = 0;
-  bool iter_timed = false;
-  if (!(rr0 <= a.tol2)) {
-    KRS_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, s->stream));
-    KRS_CUDA(cudaMemsetAsync(s->bar, 0, sizeof(unsigned long long), s->stream));
-    KRS_CUDA(cudaEventRecord(s->ev[1], s->stream));
-    iter_timed = true;
-    if (p->exec == KRS_EXEC_PERSISTENT) {
-      KRS_CUDA(apcg_launch_persistent(a, s->stream, &launches));
-      KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
-      KRS_CUDA(cudaMemcpyAsync(s->h_ctrl, s->ctrl, sizeof(int) * CTRL_WORDS, cudaMemcpyDeviceToHost, s->stream));
-      KRS_CUDA(cudaStreamSynchronize(s->stream));
-    } else {
-      int j = 0;
-      const int batch = 16;
-      for (;;) {
-        const int j1 = (j + batch < p->max_iter) ? j + batch : p->max_iter;
-        KRS_CUDA(apcg_launch_phases(a, j, j1, s->stream, &launches));
-        KRS_CUDA(cudaMemcpyAsync(s->h_ctrl, s->ctrl, sizeof(int) * CTRL_WORDS, cudaMemcpyDeviceToHost, s->stream));
-        KRS_CUDA(cudaStreamSynchronize(s->stream));
-        j = j1;
-        if (s->h_ctrl[CTRL_DONE] || j >= p->max_iter) break;
-      }
-      KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
-    }
-    status = s->h_ctrl[CTRL_STATUS];
-    m = s->h_ctrl[CTRL_M];
-    if (!s->h_ctrl[CTRL_DONE] && status == KRS_OK) status = KRS_ERR_CUDA;
+  if (mixed) {
+    a.vals = s->vals32; a.minv = s->minv32; a.C = s->C32; a.AC = s->AC32;
+    a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.x = s->x32; a.r = s->r32; a.u = s->u32;
+  } else {
+    a.vals = s->vals_use; a.minv = s->minv; a.C = s->C; a.AC = s->AC;
+    a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.x = s->x; a.r = s->r; a.u = s->u;
   }
-  if (!iter_timed) {
-    KRS_CUDA(cudaEventRecord(s->ev[1], s->stream));
+  KRS_CUDA(cudaEventRecord(s->ev[1], s->stream));
+
+  int status = KRS_OK, m = 0, outer = 0, m_first = 0, add = 0;
+  float t_iter = 0.f;
+  double bb = 0.0;
+  if (!mixed) {
+    // ---- FP64: one APCG solve, then the recycling step on its W / Z
+    KRS_TRY(run_apcg(s, a, s->b, tol, p->exec, &status, &m, &bb, &t_iter, &launches));
+    s->last_m = m;
+    KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
+    if (status == KRS_OK) {
+      if (p->recycle == KRS_RECYCLE_TRKS && m > 0) {
+        add = m < room ? m : room;
+        if (add > 0) {
+          KRS_TRY(ensure_cap_c(s, nc + add));
+          KRS_CUDA(cudaMemcpyAsync(s->C + (size_t)nc * s->ld, s->W, sizeof(double) * (size_t)add * s->ld,
+                                   cudaMemcpyDeviceToDevice, s->stream));
+          if (s->ac_valid == nc) {
+            // A is unchanged since the directions' products were formed: A W is A C's new block
+            KRS_CUDA(cudaMemcpyAsync(s->AC + (size_t)nc * s->ld, s->AW, sizeof(double) * (size_t)add * s->ld,
+                                     cudaMemcpyDeviceToDevice, s->stream));
+            s->ac_valid = nc + add;
+          }
+        }
+      } else if (p->recycle == KRS_RECYCLE_SRKS && m >= 2) {
+        KRS_TRY(srks_extract(s, m, nc, room, p, s->Z, nullptr, &add, &launches));
+      }
+    }
+  } else {
+    // ---- mixed precision: FP64 refinement around FP32 inner APCG solves
+    const double inner_tol = p->inner_tol > 0.0 ? p->inner_tol : 0.1;
+    const int max_outer = p->max_outer > 0 ? p->max_outer : 30;
+    KRS_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * s->ld, s->stream));
+    // r = b - A*0 = b (FP64), r32 = (float) b, rr = ||b||^2
+    KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->r, s->b32,
+                                 s->part, s->scal + 4, s->stream));
+    launches += 3;
+    KRS_CUDA(cudaMemcpyAsync(s->h_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    KRS_CUDA(cudaStreamSynchronize(s->stream));
+    bb = s->h_scal[4];
+    if (!isfinite(bb)) return fail(KRS_ERR_INVALID_ARG, "right-hand side is not finite");
+    double rr = bb;
+    bool first = true;
+    for (;;) {
+      if (rr <= tol * tol * bb) break;
+      if (outer >= max_outer || m >= p->max_iter) {
+        status = KRS_ERR_NO_CONVERGENCE;
+        break;
+      }
+      // aim at inner_tol, or less when the outer tolerance is closer than that
+      double tin = 0.5 * tol * sqrt(bb / rr);
+      if (tin < inner_tol) tin = inner_tol;
+      if (tin > 0.5) tin = 0.5;
+      a.max_iter = p->max_iter - m;
+      int st_in = KRS_OK, m_in = 0;
+      double bb_in = 0.0;
+      KRS_TRY(run_apcg(s, a, s->b32, tin, p->exec, &st_in, &m_in, &bb_in, &t_iter, &launches));
+      // An FP32 breakdown ((w, Aw) <= 0 or (r, z) <= 0) after some progress only ends this
+      // inner solve: its iterate and directions up to there are valid, and the FP64 outer
+      // residual decides whether refinement still advances.
+      if (st_in != KRS_OK && st_in != KRS_ERR_NO_CONVERGENCE && !(st_in == KRS_ERR_NOT_SPD && m_in > 0)) {
+        status = st_in;
+        break;
+      }
+      m += m_in;
+      s->last_m = m_in;
+      if (first) {
+        m_first = m_in;
+        // recycling from the first inner solve (staged beyond nc until the system converges)
+        if (p->recycle == KRS_RECYCLE_TRKS && m_in > 0) {
+          add = m_in < room ? m_in : room;
+          if (add > 0) {
+            k_f2d_cols<<<1216, 256, 0, s->stream>>>(s->W32, s->C + (size_t)nc * s->ld, (int64_t)add * s->ld);
+            KRS_CUDA(cudaGetLastError());
+            launches++;
+          }
+        } else if (p->recycle == KRS_RECYCLE_SRKS && m_in >= 2) {
+          KRS_TRY(srks_extract(s, m_in, nc, room, p, nullptr, s->Z32, &add, &launches));
+        }
+        first = false;
+      }
+      // The next inner solve (same operator) is augmented by this one's directions: they
+      // are A-conjugate to C and to each other, so their coarse block is diag(1/(w, Aw)).
+      if (m_in > 0) {
+        const int nct = a.nc;
+        KRS_CUDA(cudaMemcpyAsync(s->C32 + (size_t)nct * s->ld, s->W32, sizeof(float) * (size_t)m_in * s->ld,
+                                 cudaMemcpyDeviceToDevice, s->stream));
+        KRS_CUDA(cudaMemcpyAsync(s->AC32 + (size_t)nct * s->ld, s->AW32, sizeof(float) * (size_t)m_in * s->ld,
+                                 cudaMemcpyDeviceToDevice, s->stream));
+        k_recip<<<(m_in + 255) / 256, 256, 0, s->stream>>>(s->gamma, s->dinv + (nct - nc), m_in);
+        KRS_CUDA(cudaGetLastError());
+        launches++;
+        a.nc = nct + m_in;
+      }
+      // x += d (FP64), r = b - A x (FP64), next inner right-hand side r32 = (float) r
+      KRS_CUDA(launch_add_f2d(s->x, s->x32, s->n, s->stream));
+      KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->r, s->b32,
+                                   s->part, s->scal + 4, s->stream));
+      launches += 4;
+      KRS_CUDA(cudaMemcpyAsync(s->h_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+      KRS_CUDA(cudaStreamSynchronize(s->stream));
+      const double rr_new = s->h_scal[4];
+      outer++;
+      if (!(rr_new < 0.81 * rr) && !(rr_new <= tol * tol * bb)) {  // stagnation: refinement no longer pays
+        rr = rr_new;
+        status = KRS_ERR_NO_CONVERGENCE;
+        break;
+      }
+      rr = rr_new;
+    }
     KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
   }
-  s->last_m = m;
 
   // ---- result and true residual
   const bool x_dev = is_device_ptr(x);
@@ -732,80 +1016,38 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
   KRS_CUDA(launch_true_residual(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->part, s->scal + 2,
                                 s->stream));
   launches += 3;
-  KRS_CUDA(launch_norm2(s->n, s->r, s->part, s->scal + 3, s->stream));
-  launches += 2;
+  if (!mixed) {
+    KRS_CUDA(launch_norm2(s->n, s->r, s->part, s->scal + 3, s->stream));
+    launches += 2;
+  }
   KRS_CUDA(cudaMemcpyAsync(s->h_scal, s->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   KRS_CUDA(cudaStreamSynchronize(s->stream));
 
   st.status = status;
   st.m = m;
   st.n_c = nc;
+  st.outer_iters = outer;
+  st.inner_m_first = m_first;
   st.true_rel_res = bb > 0.0 ? sqrt(s->h_scal[2] / bb) : 0.0;
-  st.rel_res = bb > 0.0 ? sqrt(s->h_scal[3] / bb) : 0.0;
+  st.rel_res = mixed ? st.true_rel_res : (bb > 0.0 ? sqrt(s->h_scal[3] / bb) : 0.0);
   if (status != KRS_OK) {
     st.n_c_after = nc;
-    float t1 = 0.f, t2 = 0.f;
+    float t1 = 0.f, t3 = 0.f;
     cudaEventElapsedTime(&t1, s->ev[0], s->ev[1]);
-    cudaEventElapsedTime(&t2, s->ev[1], s->ev[2]);
+    cudaEventElapsedTime(&t3, s->ev[0], s->ev[2]);
     st.t_setup_ms = t1;
-    st.t_iter_ms = t2;
-    st.t_total_ms = t1 + t2;
+    st.t_iter_ms = t_iter;
+    st.t_total_ms = t3;
     st.kernel_launches = launches;
     s->st = st;
     const char* what = status == KRS_ERR_NOT_SPD ? "operator not SPD ((w, Aw) <= 0 or (r, z) <= 0)"
-                       : status == KRS_ERR_NO_CONVERGENCE ? "max_iter reached"
+                       : status == KRS_ERR_NO_CONVERGENCE ? "max_iter / max_outer reached or refinement stagnated"
                        : status == KRS_ERR_TIMEOUT ? "device wait timed out"
                                                   : "solve did not complete";
     return fail((krs_status)status, "%s (m = %d)", what, m);
   }
 
-  // ---- recycling
-  int add = 0;
-  const int cap = p->max_aug > 0 ? p->max_aug : 0x7fffffff;
-  if (p->recycle == KRS_RECYCLE_TRKS && m > 0) {
-    add = m;
-    if (p->cap_mode == KRS_CAP_TRUNCATE && nc + add > cap) add = cap - nc > 0 ? cap - nc : 0;
-    if (add > 0) {
-      KRS_TRY(ensure_cap_c(s, nc + add));
-      KRS_CUDA(cudaMemcpyAsync(s->C + (size_t)nc * s->ld, s->W, sizeof(double) * (size_t)add * s->ld,
-                               cudaMemcpyDeviceToDevice, s->stream));
-      if (s->ac_valid == nc) {
-        // A is unchanged since the directions' products were formed: A W is A C's new block
-        KRS_CUDA(cudaMemcpyAsync(s->AC + (size_t)nc * s->ld, s->AW, sizeof(double) * (size_t)add * s->ld,
-                                 cudaMemcpyDeviceToDevice, s->stream));
-        s->ac_valid = nc + add;
-      }
-    }
-  } else if (p->recycle == KRS_RECYCLE_SRKS && m >= 2) {
-    s->last_srks = 1;
-    KRS_TRY(ensure_eig(s, m));
-    const int room = (p->cap_mode == KRS_CAP_TRUNCATE) ? (cap - nc > 0 ? cap - nc : 0) : m;
-    KRS_CUDA(launch_lanczos(m, s->alpha, s->rho, s->delta, s->eta, s->stream));
-    KRS_CUDA(launch_tridiag_eigvals2(m, m - 1, s->delta, s->eta, s->theta_m, s->theta_m1, s->stream));
-    KRS_CUDA(launch_srks_select(m, s->theta_m, s->theta_m1, p->ritz_eps, p->theta_frac, room, s->sel, s->selcount,
-                                s->tsel, s->stream));
-    launches += 3;
-    int cnt = 0;
-    KRS_CUDA(cudaMemcpyAsync(&s->h_ctrl[16], s->selcount, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-    KRS_CUDA(cudaStreamSynchronize(s->stream));
-    cnt = s->h_ctrl[16];
-    s->last_nsel = cnt;
-    if (cnt > 0) {
-      KRS_TRY(ensure_cap_c(s, nc + cnt));
-      const size_t wneed = eigvecs_work_doubles(m, cnt) + (size_t)m * cnt * 2;
-      dev_free(s, s->eigwork);
-      s->eigwork = nullptr;
-      KRS_TRY(alloc_n(s, &s->eigwork, wneed));
-      double* Q = s->eigwork;
-      double* Fm = s->eigwork + (size_t)m * cnt;
-      double* wk = s->eigwork + 2 * (size_t)m * cnt;
-      KRS_CUDA(launch_tridiag_eigvecs(m, s->delta, s->eta, cnt, s->tsel, Q, wk, s->stream));
-      KRS_CUDA(launch_ritz_vectors(s->n, s->ld, m, cnt, s->Z, s->rho, Q, s->tsel, Fm, s->C + (size_t)nc * s->ld,
-                                   s->stream));
-      launches += 3;
-      add = cnt;
-    }
-  }
+  // ---- commit the recycled columns
   s->nc = nc + add;
   if (p->cap_mode == KRS_CAP_RESTART && p->max_aug > 0 && s->nc >= p->max_aug) {
     // Algorithm 3, last step: back to C^(0)
@@ -818,16 +1060,16 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
   }
   KRS_CUDA(cudaEventRecord(s->ev[3], s->stream));
   KRS_CUDA(cudaStreamSynchronize(s->stream));
-  float t1 = 0.f, t2 = 0.f, t3 = 0.f;
+  float t1 = 0.f, t3 = 0.f, tt = 0.f;
   cudaEventElapsedTime(&t1, s->ev[0], s->ev[1]);
-  cudaEventElapsedTime(&t2, s->ev[1], s->ev[2]);
   cudaEventElapsedTime(&t3, s->ev[2], s->ev[3]);
+  cudaEventElapsedTime(&tt, s->ev[0], s->ev[3]);
   st.n_selected = add;
   st.n_c_after = s->nc;
   st.t_setup_ms = t1;
-  st.t_iter_ms = t2;
+  st.t_iter_ms = t_iter;
   st.t_recycle_ms = t3;
-  st.t_total_ms = t1 + t2 + t3;
+  st.t_total_ms = tt;
   st.kernel_launches = launches;
   s->st = st;
   return KRS_OK;

@@ -154,37 +154,66 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* counter, unsign
 }
 
 // ------------------------------------------------------------------------------------
+// Value types.  The FP64 path instantiates everything with T = double; the inner solve of
+// the mixed-precision refinement with T = float (storage and arithmetic), while every
+// partial sum that crosses CTAs is a double.
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct VT;
+template <>
+struct VT<double> {
+  using V4 = double4_32a;  // four rows, 32 bytes
+  using V2 = double2;      // 16 bytes
+  __device__ static __forceinline__ V4 make4(double a, double b, double c, double d) {
+    return make_double4_32a(a, b, c, d);
+  }
+};
+template <>
+struct VT<float> {
+  using V4 = float4;  // four rows, 16 bytes
+  using V2 = float2;  // 8 bytes
+  __device__ static __forceinline__ V4 make4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+
+// Load of four consecutive rows of data that is read-only for the whole kernel (NC = true:
+// non-coherent path) or that other CTAs of the same (persistent) kernel may have written
+// (NC = false).
+template <bool NC, typename T>
+__device__ __forceinline__ typename VT<T>::V4 ld4(const T* p);
+
+template <>
+__device__ __forceinline__ double4_32a ld4<true, double>(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+  return make_double4_32a(a.x, a.y, b.x, b.y);
+}
+template <>
+__device__ __forceinline__ double4_32a ld4<false, double>(const double* p) {
+  return *reinterpret_cast<const double4_32a*>(p);
+}
+template <>
+__device__ __forceinline__ float4 ld4<true, float>(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+template <>
+__device__ __forceinline__ float4 ld4<false, float>(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+
+// ------------------------------------------------------------------------------------
 // Tall-skinny kernels on one CTA's rows [r0, r1) (r0 a multiple of 4).
 // V: column-major, leading dimension ld (multiple of 4), rows >= n padded with zeros.
 // ------------------------------------------------------------------------------------
 
-// Load of data that is read-only for the whole kernel (NC = true: non-coherent path) or
-// that other CTAs of the same (persistent) kernel may have written (NC = false).
-template <bool NC>
-__device__ __forceinline__ double4_32a ld4(const double* p) {
-  if (NC) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
-    return make_double4_32a(a.x, a.y, b.x, b.y);
-  }
-  return *reinterpret_cast<const double4_32a*>(p);
-}
-
-// out[c] = sum_{i in [r0, r1)} V[c*ld + i] * u[i], c in [0, k).  Thread per column: each
-// thread streams its column with 32-byte loads into four independent accumulators (no
-// dependent FMA chain).  Columns are taken in blocks of kc with G = ceil(TPB / rem) row
-// groups each (kc = TPB / G), so that all threads stay busy whatever k is; the groups are
-// combined in shared memory in a fixed order.
-// u: global vector (zero padded past n).  su: shared (ROW_CHUNK doubles); red: shared
-// (TPB doubles).
 // Few columns (k <= TPB/32): warps instead of threads own the columns -- Gw = (TPB/32)/k
-// warps per column split the rows, lanes read consecutive 32-byte pieces of the column
-// (contiguous 1 KB per warp load), each warp folds its lanes with one shuffle tree, and
-// the Gw warp partials are summed in a fixed order.  Used by cta_gemv_t.
-template <bool NC>
-__device__ __forceinline__ void cta_gemv_t_few(const double* __restrict__ V, int64_t ld, int k,
-                                               const double* __restrict__ u, int64_t r0, int64_t r1,
+// warps per column split the rows, lanes read consecutive four-row pieces of the column
+// (contiguous per warp load), each warp folds its lanes with one shuffle tree, and the Gw
+// warp partials are summed in a fixed order.  Used by cta_gemv_t.
+template <bool NC, typename T>
+__device__ __forceinline__ void cta_gemv_t_few(const T* __restrict__ V, int64_t ld, int k,
+                                               const T* __restrict__ u, int64_t r0, int64_t r1,
                                                double* __restrict__ out, double* red) {
+  using V4 = typename VT<T>::V4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int W = TPB / 32;
   const int Gw = W / k;
@@ -192,15 +221,15 @@ __device__ __forceinline__ void cta_gemv_t_few(const double* __restrict__ V, int
   if (warp < Gw * k) {
     const int c = warp / Gw, g = warp % Gw;
     const int qa = (int)((int64_t)q4 * g / Gw), qb = (int)((int64_t)q4 * (g + 1) / Gw);
-    const double* col = V + (int64_t)c * ld + r0;
-    const double* uu = u + r0;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    const T* col = V + (int64_t)c * ld + r0;
+    const T* uu = u + r0;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     for (int q = qa + lane; q < qb; q += 32) {
-      const double4_32a x = ld4<NC>(col + 4 * q);
-      const double4_32a y = *reinterpret_cast<const double4_32a*>(uu + 4 * q);
+      const V4 x = ld4<NC, T>(col + 4 * q);
+      const V4 y = *reinterpret_cast<const V4*>(uu + 4 * q);
       a0 += x.x * y.x; a1 += x.y * y.y; a2 += x.z * y.z; a3 += x.w * y.w;
     }
-    double v = (a0 + a1) + (a2 + a3);
+    double v = (double)((a0 + a1) + (a2 + a3));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[warp] = v;
@@ -214,12 +243,20 @@ __device__ __forceinline__ void cta_gemv_t_few(const double* __restrict__ V, int
   __syncthreads();
 }
 
-template <bool NC>
-__device__ __forceinline__ void cta_gemv_t(const double* __restrict__ V, int64_t ld, int k,
-                                           const double* __restrict__ u, int64_t r0, int64_t r1,
-                                           double* __restrict__ out, double* su, double* red) {
+// out[c] = sum_{i in [r0, r1)} V[c*ld + i] * u[i], c in [0, k), as doubles.  Thread per
+// column: each thread streams its column with four-row vector loads into four independent
+// accumulators (no dependent FMA chain).  Columns are taken in blocks of kc with
+// G = ceil(TPB / rem) row groups each (kc = TPB / G), so that all threads stay busy
+// whatever k is; the groups are combined by a pairwise tree in a fixed order.
+// u: global vector (zero padded past n).  su: shared (ROW_CHUNK values of T); red: shared
+// (TPB doubles).
+template <bool NC, typename T>
+__device__ __forceinline__ void cta_gemv_t(const T* __restrict__ V, int64_t ld, int k,
+                                           const T* __restrict__ u, int64_t r0, int64_t r1,
+                                           double* __restrict__ out, T* su, double* red) {
+  using V4 = typename VT<T>::V4;
   if (k <= TPB / 32) {
-    cta_gemv_t_few<NC>(V, ld, k, u, r0, r1, out, red);
+    cta_gemv_t_few<NC, T>(V, ld, k, u, r0, r1, out, red);
     return;
   }
   const int t = threadIdx.x;
@@ -237,7 +274,7 @@ __device__ __forceinline__ void cta_gemv_t(const double* __restrict__ V, int64_t
     const int kc = min(rem, TPB / G);
     const int c = t % kc;
     const int g = t / kc;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     for (int64_t ch = 0; ch < rows4; ch += ROW_CHUNK) {
       const int len = (int)kmin64(ROW_CHUNK, rows4 - ch);
       if (!one_chunk) {
@@ -248,26 +285,26 @@ __device__ __forceinline__ void cta_gemv_t(const double* __restrict__ V, int64_t
       if (g < G) {
         const int q4 = len >> 2;
         const int qa = (int)((int64_t)q4 * g / G), qb = (int)((int64_t)q4 * (g + 1) / G);
-        const double* col = V + (int64_t)(cb + c) * ld + r0 + ch;
-        const double4_32a* s4 = reinterpret_cast<const double4_32a*>(su);
+        const T* col = V + (int64_t)(cb + c) * ld + r0 + ch;
+        const V4* s4 = reinterpret_cast<const V4*>(su);
         int q = qa;
         for (; q + 4 <= qb; q += 4) {
-          const double4_32a x0 = ld4<NC>(col + 4 * q), x1 = ld4<NC>(col + 4 * q + 4);
-          const double4_32a x2 = ld4<NC>(col + 4 * q + 8), x3 = ld4<NC>(col + 4 * q + 12);
-          const double4_32a y0 = s4[q], y1 = s4[q + 1], y2 = s4[q + 2], y3 = s4[q + 3];
+          const V4 x0 = ld4<NC, T>(col + 4 * q), x1 = ld4<NC, T>(col + 4 * q + 4);
+          const V4 x2 = ld4<NC, T>(col + 4 * q + 8), x3 = ld4<NC, T>(col + 4 * q + 12);
+          const V4 y0 = s4[q], y1 = s4[q + 1], y2 = s4[q + 2], y3 = s4[q + 3];
           a0 += x0.x * y0.x; a1 += x0.y * y0.y; a2 += x0.z * y0.z; a3 += x0.w * y0.w;
           a0 += x1.x * y1.x; a1 += x1.y * y1.y; a2 += x1.z * y1.z; a3 += x1.w * y1.w;
           a0 += x2.x * y2.x; a1 += x2.y * y2.y; a2 += x2.z * y2.z; a3 += x2.w * y2.w;
           a0 += x3.x * y3.x; a1 += x3.y * y3.y; a2 += x3.z * y3.z; a3 += x3.w * y3.w;
         }
         for (; q < qb; q++) {
-          const double4_32a x0 = ld4<NC>(col + 4 * q), y0 = s4[q];
+          const V4 x0 = ld4<NC, T>(col + 4 * q), y0 = s4[q];
           a0 += x0.x * y0.x; a1 += x0.y * y0.y; a2 += x0.z * y0.z; a3 += x0.w * y0.w;
         }
       }
     }
     __syncthreads();
-    if (g < G) red[g * kc + c] = (a0 + a1) + (a2 + a3);
+    if (g < G) red[g * kc + c] = (double)((a0 + a1) + (a2 + a3));
     __syncthreads();
     // combine the G row groups: pairwise tree (fixed order), log2(G) parallel rounds
     for (int st = 1; st < G; st <<= 1) {
@@ -281,13 +318,14 @@ __device__ __forceinline__ void cta_gemv_t(const double* __restrict__ V, int64_t
 }
 
 // z[i] = u[i] + sgn * sum_{c<k} V[c*ld + i] * s[c] for i in [r0, r1) (u == nullptr: 0).
-// Thread per 4 rows (four independent accumulators); quads are taken in blocks of qc with
-// G = ceil(TPB / remaining quads) column groups each (qc = TPB / G), combined in shared
-// memory in a fixed order.  s: shared (k doubles).  red: shared (4*TPB doubles).
-template <bool NC>
-__device__ __forceinline__ void cta_gemv_n(const double* __restrict__ V, int64_t ld, int k,
-                                           const double* s, double sgn, const double* u,
-                                           double* z, int64_t r0, int64_t r1, double* red) {
+// Thread per 4 rows (four independent accumulators), four-column unroll; quads are taken
+// in blocks of qc with G = ceil(TPB / remaining quads) column groups each (qc = TPB / G),
+// combined by a pairwise tree in a fixed order.  s: shared (k values of T).  red: shared
+// scratch of TPB four-row vectors of T.
+template <bool NC, typename T>
+__device__ __forceinline__ void cta_gemv_n(const T* __restrict__ V, int64_t ld, int k, const T* s, T sgn,
+                                           const T* u, T* z, int64_t r0, int64_t r1, void* red) {
+  using V4 = typename VT<T>::V4;
   const int t = threadIdx.x;
   const int64_t L = r1 - r0;
   const int64_t q4 = (L + 3) >> 2;
@@ -299,54 +337,54 @@ __device__ __forceinline__ void cta_gemv_n(const double* __restrict__ V, int64_t
     const int nq = (int)kmin64(remq, TPB / G);
     const int q = t % nq;
     const int g = t / nq;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     if (g < G && k > 0) {
       const int ca = (int)((int64_t)k * g / G), cbnd = (int)((int64_t)k * (g + 1) / G);
       const int64_t row = r0 + 4 * (qb0 + q);
       int c = ca;
       for (; c + 4 <= cbnd; c += 4) {
-        const double4_32a v0 = ld4<NC>(V + (int64_t)c * ld + row);
-        const double4_32a v1 = ld4<NC>(V + (int64_t)(c + 1) * ld + row);
-        const double4_32a v2 = ld4<NC>(V + (int64_t)(c + 2) * ld + row);
-        const double4_32a v3 = ld4<NC>(V + (int64_t)(c + 3) * ld + row);
-        const double s0 = s[c], s1 = s[c + 1], s2 = s[c + 2], s3 = s[c + 3];
+        const V4 v0 = ld4<NC, T>(V + (int64_t)c * ld + row);
+        const V4 v1 = ld4<NC, T>(V + (int64_t)(c + 1) * ld + row);
+        const V4 v2 = ld4<NC, T>(V + (int64_t)(c + 2) * ld + row);
+        const V4 v3 = ld4<NC, T>(V + (int64_t)(c + 3) * ld + row);
+        const T s0 = s[c], s1 = s[c + 1], s2 = s[c + 2], s3 = s[c + 3];
         a0 += v0.x * s0; a1 += v0.y * s0; a2 += v0.z * s0; a3 += v0.w * s0;
         a0 += v1.x * s1; a1 += v1.y * s1; a2 += v1.z * s1; a3 += v1.w * s1;
         a0 += v2.x * s2; a1 += v2.y * s2; a2 += v2.z * s2; a3 += v2.w * s2;
         a0 += v3.x * s3; a1 += v3.y * s3; a2 += v3.z * s3; a3 += v3.w * s3;
       }
       for (; c < cbnd; c++) {
-        const double4_32a v0 = ld4<NC>(V + (int64_t)c * ld + row);
-        const double s0 = s[c];
+        const V4 v0 = ld4<NC, T>(V + (int64_t)c * ld + row);
+        const T s0 = s[c];
         a0 += v0.x * s0; a1 += v0.y * s0; a2 += v0.z * s0; a3 += v0.w * s0;
       }
     }
     if (G > 1) {
       __syncthreads();
-      double4_32a* r4 = reinterpret_cast<double4_32a*>(red);
-      if (g < G) r4[g * nq + q] = make_double4_32a(a0, a1, a2, a3);
+      V4* r4 = reinterpret_cast<V4*>(red);
+      if (g < G) r4[g * nq + q] = VT<T>::make4(a0, a1, a2, a3);
       __syncthreads();
       // pairwise tree over the G column groups (fixed order), log2(G) parallel rounds
       for (int st = 1; st < G; st <<= 1) {
         if (g < G && (g % (2 * st)) == 0 && g + st < G) {
-          const double4_32a v = r4[(g + st) * nq + q];
-          double4_32a acc = r4[g * nq + q];
+          const V4 v = r4[(g + st) * nq + q];
+          V4 acc = r4[g * nq + q];
           acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
           r4[g * nq + q] = acc;
         }
         __syncthreads();
       }
       if (t < nq) {
-        const double4_32a acc = r4[t];
+        const V4 acc = r4[t];
         a0 = acc.x; a1 = acc.y; a2 = acc.z; a3 = acc.w;
       }
     }
     if (t < nq) {
       const int64_t row = r0 + 4 * (qb0 + t);
-      const double aa[4] = {a0, a1, a2, a3};
+      const T aa[4] = {a0, a1, a2, a3};
 #pragma unroll
       for (int e = 0; e < 4; e++) {
-        if (row + e < r1) z[row + e] = (u ? u[row + e] : 0.0) + sgn * aa[e];
+        if (row + e < r1) z[row + e] = (u ? u[row + e] : T(0)) + sgn * aa[e];
       }
     }
     qb0 += nq;
@@ -357,21 +395,23 @@ __device__ __forceinline__ void cta_gemv_n(const double* __restrict__ V, int64_t
 // q = A w on one CTA's nodes [r0/3, r1/3).  Two threads per node: each takes half of the
 // node's blocks and all three rows (three independent accumulators, 9 FMAs per block),
 // the odd thread's partial sums reach its even neighbour by register shuffle, and the
-// even thread writes q and adds its nodes' (w, q) and (r, w) terms to wq / rw.  Every
-// thread gets ~half a node, so the FP64 pipe is not idled by uneven rows per thread.
-// Blocks are read in pairs starting at an even block index, 144 bytes as nine 16-byte
-// loads (values must be 16-byte aligned; col_idx 8-byte aligned).  The matrix goes
-// through the non-coherent path; w (written by other CTAs of a persistent kernel) does not.
+// even thread writes q and adds its nodes' (w, q) and (r, w) terms to wq / rw (doubles).
+// Every thread gets ~half a node, so the FP64 pipe is not idled by uneven rows per thread.
+// Blocks are read in pairs starting at an even block index, 18 values as nine two-value
+// loads (16-byte loads for FP64 values: 16-byte aligned values and 8-byte aligned col_idx
+// required).  The matrix goes through the non-coherent path; w (written by other CTAs of a
+// persistent kernel) does not.
+template <typename T>
 __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* __restrict__ ci,
-                                         const double* __restrict__ vals,
-                                         const double* __restrict__ w, double* __restrict__ q,
-                                         const double* __restrict__ r, int64_t r0, int64_t r1,
+                                         const T* __restrict__ vals, const T* __restrict__ w,
+                                         T* __restrict__ q, const T* __restrict__ r, int64_t r0, int64_t r1,
                                          double& wq, double& rw) {
+  using V2 = typename VT<T>::V2;
   const int64_t n0 = r0 / 3;
   const int64_t items = 2 * ((r1 - r0) / 3);
   for (int64_t base = 0; base < items; base += TPB) {
     const int64_t it = base + threadIdx.x;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    T a0 = 0, a1 = 0, a2 = 0;
     const bool active = it < items;
     int64_t node = 0;
     if (active) {
@@ -380,32 +420,32 @@ __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* 
       const int mid = ka + ((kb - ka) >> 1);
       const int kbeg = (it & 1) ? mid : ka, kend = (it & 1) ? kb : mid;
       int k = kbeg;
-      if ((k & 1) && k < kend) {  // a leading odd block alone (its 72 bytes are not 16-aligned)
+      if ((k & 1) && k < kend) {  // a leading odd block alone (not aligned for pair loads)
         const int64_t cc = 3 * (int64_t)__ldg(ci + k);
-        const double* v = vals + 9 * (int64_t)k;
-        const double w0 = w[cc], w1 = w[cc + 1], w2 = w[cc + 2];
+        const T* v = vals + 9 * (int64_t)k;
+        const T w0 = w[cc], w1 = w[cc + 1], w2 = w[cc + 2];
         a0 += __ldg(v + 0) * w0; a1 += __ldg(v + 3) * w0; a2 += __ldg(v + 6) * w0;
         a0 += __ldg(v + 1) * w1; a1 += __ldg(v + 4) * w1; a2 += __ldg(v + 7) * w1;
         a0 += __ldg(v + 2) * w2; a1 += __ldg(v + 5) * w2; a2 += __ldg(v + 8) * w2;
         k++;
       }
-      // block pairs (k even): 144 bytes as nine 16-byte loads; the next pair's indices and
-      // values are loaded before the current pair is used (two-stage software pipeline)
+      // block pairs (k even): nine two-value loads; the next pair's indices and values are
+      // loaded before the current pair is used (two-stage software pipeline)
       if (k + 2 <= kend) {
         int2 cp = __ldg(reinterpret_cast<const int2*>(ci + k));
-        const double2* v2 = reinterpret_cast<const double2*>(vals + 9 * (int64_t)k);
-        double2 p0 = __ldg(v2 + 0), p1 = __ldg(v2 + 1), p2 = __ldg(v2 + 2), p3 = __ldg(v2 + 3);
-        double2 p4 = __ldg(v2 + 4), p5 = __ldg(v2 + 5), p6 = __ldg(v2 + 6), p7 = __ldg(v2 + 7);
-        double2 p8 = __ldg(v2 + 8);
+        const V2* v2 = reinterpret_cast<const V2*>(vals + 9 * (int64_t)k);
+        V2 p0 = __ldg(v2 + 0), p1 = __ldg(v2 + 1), p2 = __ldg(v2 + 2), p3 = __ldg(v2 + 3);
+        V2 p4 = __ldg(v2 + 4), p5 = __ldg(v2 + 5), p6 = __ldg(v2 + 6), p7 = __ldg(v2 + 7);
+        V2 p8 = __ldg(v2 + 8);
 #pragma unroll 1
         for (; k + 2 <= kend; k += 2) {
           const int64_t c0 = 3 * (int64_t)cp.x, c1 = 3 * (int64_t)cp.y;
-          const double x0 = w[c0], x1 = w[c0 + 1], x2 = w[c0 + 2];
-          const double y0 = w[c1], y1 = w[c1 + 1], y2 = w[c1 + 2];
-          const double2 q0 = p0, q1 = p1, q2 = p2, q3 = p3, q4 = p4, q5 = p5, q6 = p6, q7 = p7, q8 = p8;
+          const T x0 = w[c0], x1 = w[c0 + 1], x2 = w[c0 + 2];
+          const T y0 = w[c1], y1 = w[c1 + 1], y2 = w[c1 + 2];
+          const V2 q0 = p0, q1 = p1, q2 = p2, q3 = p3, q4 = p4, q5 = p5, q6 = p6, q7 = p7, q8 = p8;
           if (k + 4 <= kend) {
             cp = __ldg(reinterpret_cast<const int2*>(ci + k + 2));
-            const double2* n2 = reinterpret_cast<const double2*>(vals + 9 * (int64_t)(k + 2));
+            const V2* n2 = reinterpret_cast<const V2*>(vals + 9 * (int64_t)(k + 2));
             p0 = __ldg(n2 + 0); p1 = __ldg(n2 + 1); p2 = __ldg(n2 + 2); p3 = __ldg(n2 + 3);
             p4 = __ldg(n2 + 4); p5 = __ldg(n2 + 5); p6 = __ldg(n2 + 6); p7 = __ldg(n2 + 7);
             p8 = __ldg(n2 + 8);
@@ -421,45 +461,46 @@ __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* 
       }
       if (k < kend) {  // a trailing single block
         const int64_t cc = 3 * (int64_t)__ldg(ci + k);
-        const double* v = vals + 9 * (int64_t)k;
-        const double w0 = w[cc], w1 = w[cc + 1], w2 = w[cc + 2];
+        const T* v = vals + 9 * (int64_t)k;
+        const T w0 = w[cc], w1 = w[cc + 1], w2 = w[cc + 2];
         a0 += __ldg(v + 0) * w0; a1 += __ldg(v + 3) * w0; a2 += __ldg(v + 6) * w0;
         a0 += __ldg(v + 1) * w1; a1 += __ldg(v + 4) * w1; a2 += __ldg(v + 7) * w1;
         a0 += __ldg(v + 2) * w2; a1 += __ldg(v + 5) * w2; a2 += __ldg(v + 8) * w2;
       }
     }
     // pairs (2i, 2i+1) share a warp (TPB and base are even); every lane takes part
-    const double b0 = __shfl_xor_sync(0xffffffffu, a0, 1);
-    const double b1 = __shfl_xor_sync(0xffffffffu, a1, 1);
-    const double b2 = __shfl_xor_sync(0xffffffffu, a2, 1);
+    const T b0 = __shfl_xor_sync(0xffffffffu, a0, 1);
+    const T b1 = __shfl_xor_sync(0xffffffffu, a1, 1);
+    const T b2 = __shfl_xor_sync(0xffffffffu, a2, 1);
     if (active && !(it & 1)) {
-      const double q0 = a0 + b0, q1 = a1 + b1, q2 = a2 + b2;
+      const T q0 = a0 + b0, q1 = a1 + b1, q2 = a2 + b2;
       const int64_t row = 3 * node;
       q[row] = q0;
       q[row + 1] = q1;
       q[row + 2] = q2;
-      const double w0 = w[row], w1 = w[row + 1], w2 = w[row + 2];
-      wq += w0 * q0;
-      wq += w1 * q1;
-      wq += w2 * q2;
+      const T w0 = w[row], w1 = w[row + 1], w2 = w[row + 2];
+      wq += (double)w0 * (double)q0;
+      wq += (double)w1 * (double)q1;
+      wq += (double)w2 * (double)q2;
       if (r) {
-        rw += r[row] * w0;
-        rw += r[row + 1] * w1;
-        rw += r[row + 2] * w2;
+        rw += (double)r[row] * (double)w0;
+        rw += (double)r[row + 1] * (double)w1;
+        rw += (double)r[row + 2] * (double)w2;
       }
     }
   }
 }
 
-// u = M^-1 r on the CTA's rows (r read from global; Jacobi: minv[row]; block Jacobi:
-// minv[9*node + 3*d + e]; identity: copy).
-__device__ __forceinline__ double precond_row(int kind, const double* __restrict__ minv,
-                                              const double* __restrict__ r, int64_t row) {
+// u = M^-1 r for one row (Jacobi: minv[row]; block Jacobi: minv[9*node + 3*d + e];
+// identity: r).
+template <typename T>
+__device__ __forceinline__ T precond_row(int kind, const T* __restrict__ minv, const T* __restrict__ r,
+                                         int64_t row) {
   if (kind == 0) return minv[row] * r[row];
   if (kind == 1) {
     const int64_t node = row / 3;
     const int d = (int)(row - 3 * node);
-    const double* m = minv + 9 * node + 3 * d;
+    const T* m = minv + 9 * node + 3 * d;
     return m[0] * r[3 * node] + m[1] * r[3 * node + 1] + m[2] * r[3 * node + 2];
   }
   return r[row];

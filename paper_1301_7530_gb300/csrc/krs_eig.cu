@@ -346,7 +346,8 @@ __global__ void k_ritz_coeffs(int m, int k, const double* Q, const double* rho, 
 constexpr int RITZ_COLS = 8;
 constexpr int RITZ_JCHUNK = 256;
 
-__global__ void __launch_bounds__(256) k_ritz_gemm(int64_t n, int64_t ld, int m, int k, const double* __restrict__ Z,
+template <typename TZ>
+__global__ void __launch_bounds__(256) k_ritz_gemm(int64_t n, int64_t ld, int m, int k, const TZ* __restrict__ Z,
                                                    const double* __restrict__ F, double* __restrict__ Y) {
   __shared__ double sF[RITZ_JCHUNK][RITZ_COLS];
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(256) k_ritz_gemm(int64_t n, int64_t ld, int m,
     __syncthreads();
     if (row < n) {
       for (int jj = 0; jj < jl; jj++) {
-        const double z = Z[(int64_t)(j0 + jj) * ld + row];
+        const double z = (double)Z[(int64_t)(j0 + jj) * ld + row];
 #pragma unroll
         for (int q = 0; q < RITZ_COLS; q++) acc[q] += z * sF[jj][q];
       }
@@ -378,13 +379,26 @@ __global__ void __launch_bounds__(256) k_ritz_gemm(int64_t n, int64_t ld, int m,
   }
 }
 
-cudaError_t launch_ritz_vectors(int64_t n, int64_t ld, int m, int k, const double* Z, const double* rho,
-                                const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st) {
+template <typename TZ>
+static cudaError_t ritz_vectors_t(int64_t n, int64_t ld, int m, int k, const TZ* Z, const double* rho, const double* Q,
+                                  const double* tsel, double* F, double* Y, cudaStream_t st) {
   if (k <= 0 || m <= 0) return cudaSuccess;
   k_ritz_coeffs<<<(m * k + 255) / 256, 256, 0, st>>>(m, k, Q, rho, tsel, F);
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)((k + RITZ_COLS - 1) / RITZ_COLS));
-  k_ritz_gemm<<<grid, 256, 0, st>>>(n, ld, m, k, Z, F, Y);
+  k_ritz_gemm<TZ><<<grid, 256, 0, st>>>(n, ld, m, k, Z, F, Y);
   return cudaGetLastError();
+}
+
+cudaError_t launch_ritz_vectors(int64_t n, int64_t ld, int m, int k, const double* Z, const double* rho,
+                                const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st) {
+  return ritz_vectors_t<double>(n, ld, m, k, Z, rho, Q, tsel, F, Y, st);
+}
+
+// Ritz vectors from single-precision z_j (inner solve of the mixed-precision refinement);
+// accumulated and stored in FP64.
+cudaError_t launch_ritz_vectors_f(int64_t n, int64_t ld, int m, int k, const float* Z, const double* rho,
+                                  const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st) {
+  return ritz_vectors_t<float>(n, ld, m, k, Z, rho, Q, tsel, F, Y, st);
 }
 
 }  // namespace krs

@@ -10,23 +10,29 @@ namespace krs {
 // Records msg as the calling thread's krs_last_error() and returns st.
 krs_status set_error(krs_status st, const char* msg);
 
-// Everything the iteration kernels need (device pointers, sizes, partition).
+// Everything the iteration kernels need (device pointers, sizes, partition).  The value
+// arrays (matrix values, M^-1, C, AC, W, AW, Z, x, r, u) are doubles when fp32 is false and
+// floats when it is true (inner solve of the mixed-precision refinement); scalars, partial
+// sums and G^-1 are doubles in both.
 struct IterArgs {
   int64_t n, ld;
   int nbr, npc, P;
   int nc, ldg;
+  int nc_dense;          // columns of C with the dense coarse inverse Ginv (the rest: dinv)
+  const double* dinv;    // 1/(w_i, A w_i) for columns [nc_dense, nc)
   int max_iter, reorth_full, precond;
   int kmax;  // largest k a tall-skinny phase sees: max(nc, max_iter)
+  bool fp32;
   double tol2;
   long long spin_limit;
   const int* rp;
   const int* ci;
-  const double* vals;
-  const double* minv;
-  const double* C;
-  const double* AC;
+  const void* vals;
+  const void* minv;
+  const void* C;
+  const void* AC;
   const double* Ginv;
-  double *W, *AW, *Z, *x, *r, *u;
+  void *W, *AW, *Z, *x, *r, *u;
   double *alpha, *gamma, *rho;
   double *tfull, *sfull, *gfull;
   double* part;
@@ -39,10 +45,9 @@ struct IterArgs {
 
 // krs_apcg.cu
 size_t apcg_smem_bytes(int kmax);
-cudaError_t apcg_prepare_attributes(int kmax);
-cudaError_t apcg_max_coresident(int kmax, int* blocks_per_sm);
-cudaError_t apcg_launch_init(const IterArgs& a, const double* b, double* scal, cudaStream_t st,
-                             int64_t* launches);
+cudaError_t apcg_prepare_attributes(int kmax, bool fp32);
+cudaError_t apcg_max_coresident(int kmax, bool fp32, int* blocks_per_sm);
+cudaError_t apcg_launch_init(const IterArgs& a, const void* b, double* scal, cudaStream_t st, int64_t* launches);
 cudaError_t apcg_launch_persistent(const IterArgs& a, cudaStream_t st, int64_t* launches);
 cudaError_t apcg_launch_phases(const IterArgs& a, int j0, int j1, cudaStream_t st, int64_t* launches);
 
@@ -76,8 +81,14 @@ cudaError_t launch_gemv_n_rows(int64_t n, int k, const double* V, int64_t ldv, c
 cudaError_t launch_norm2(int64_t n, const double* v, double* part, double* out, cudaStream_t st);
 cudaError_t launch_axpy2_dot(int64_t n, const double* alpha, const double* w, const double* q, double* x,
                              double* r, double* rr, double* part, cudaStream_t st);
-// copy a host/device n-vector into a padded device column (ld >= n)
 cudaError_t launch_fill_zero(double* p, int64_t count, cudaStream_t st);
+// mixed-precision refinement: dst = (float) src; x += (double) d; r = b - A x (FP64),
+// r32 = (float) r, out = ||r||^2 (ax: n-vector scratch, part: >= 128 doubles)
+cudaError_t launch_d2f(const double* src, float* dst, int64_t count, cudaStream_t st);
+cudaError_t launch_add_f2d(double* x, const float* d, int64_t n, cudaStream_t st);
+cudaError_t launch_resid_update(int nbr, const int* rp, const int* ci, const double* vals, const double* x,
+                                const double* b, double* ax, double* r, float* r32, double* part, double* out,
+                                cudaStream_t st);
 
 // krs_eig.cu
 // delta/eta of H_m from alpha, rho (Section 4.1)
@@ -96,5 +107,7 @@ cudaError_t launch_srks_select(int m, const double* theta_m, const double* theta
 cudaError_t launch_ritz_vectors(int64_t n, int64_t ld, int m, int k, const double* Z, const double* rho,
                                 const double* Q, const double* tsel, double* F, double* Y,
                                 cudaStream_t st);
+cudaError_t launch_ritz_vectors_f(int64_t n, int64_t ld, int m, int k, const float* Z, const double* rho,
+                                  const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st);
 
 }  // namespace krs

@@ -460,6 +460,58 @@ cudaError_t launch_axpy2_dot(int64_t n, const double* alpha, const double* w, co
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------
+// mixed-precision refinement helpers
+// ------------------------------------------------------------------------------------
+__global__ void k_d2f(const double* __restrict__ src, float* __restrict__ dst, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+cudaError_t launch_d2f(const double* src, float* dst, int64_t count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_d2f<<<1216, 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+// x += (double) d
+__global__ void k_add_f2d(double* __restrict__ x, const float* __restrict__ d, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+
+cudaError_t launch_add_f2d(double* x, const float* d, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_add_f2d<<<1216, 256, 0, st>>>(x, d, n);
+  return cudaGetLastError();
+}
+
+// r = b - Ax, r32 = (float) r, partial ||r||^2 per CTA, then summed into out
+__global__ void k_resid_update(int64_t n, const double* b, const double* ax, double* r, float* r32, double* part) {
+  __shared__ double red[2 * TPB + 2];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB) {
+    const double d = b[i] - ax[i];
+    r[i] = d;
+    r32[i] = (float)d;
+    s += d * d;
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+cudaError_t launch_resid_update(int nbr, const int* rp, const int* ci, const double* vals, const double* x,
+                                const double* b, double* ax, double* r, float* r32, double* part, double* out,
+                                cudaStream_t st) {
+  const int64_t n = 3 * (int64_t)nbr;
+  cudaError_t e = launch_spmv(nbr, rp, ci, vals, x, ax, st);
+  if (e != cudaSuccess) return e;
+  const int blocks = 128;
+  k_resid_update<<<blocks, TPB, 0, st>>>(n, b, ax, r, r32, part);
+  k_sum_parts<<<1, 32, 0, st>>>(part, blocks, out);
+  return cudaGetLastError();
+}
+
 __global__ void k_fill_zero(double* p, int64_t count) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = 0.0;

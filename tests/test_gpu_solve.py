@@ -237,8 +237,10 @@ def test_invalid_arguments(gpu_lib):
         seq.solve(A, bs[0], -1.0, B.make_policy(), version=1)
     with pytest.raises(B.KrsError):
         seq.solve(A, bs[0], 1e-8, B.make_policy(max_iter=0), version=1)
+    bad = B.make_policy()
+    bad.precision = 7
     with pytest.raises(B.KrsError):
-        seq.solve(A, bs[0], 1e-8, B.make_policy(precision="mixed_ir"), version=1)
+        seq.solve(A, bs[0], 1e-8, bad, version=1)
     A3, _ = P.elasticity_sequence_fixed(3, 1, 1)
     with pytest.raises(B.KrsError):
         seq.solve(A3, np.zeros(A3.n), 1e-8, B.make_policy(), version=2)
