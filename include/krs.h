@@ -209,6 +209,89 @@ krs_status krs_last_vectors(krs_seq_t s, int32_t which, double* out);
  * kernel records KRS_ERR_TIMEOUT and returns.  0 restores the default (about 2^24). */
 krs_status krs_set_spin_limit(krs_seq_t s, int64_t spins);
 
+/* --- device memory of a sequence ------------------------------------------------------
+ * The paper keeps every sequence's space in memory; a process serving many sequences
+ * needs to know and bound what each holds.  These two calls have no counterpart in the
+ * paper.  krs_device_bytes: device bytes the sequence holds now (its own allocations,
+ * rounded to 256 bytes each).  krs_release frees parts of it between solves (never while
+ * a batched solve of the sequence is in flight: KRS_ERR_INVALID_ARG):
+ *   KRS_RELEASE_SCRATCH  direction storage W, AW, Z, partial sums, eigen / Gram scratch and
+ *                        FP32 copies (reallocated by the next solve; krs_last_* then
+ *                        return nothing);
+ *   KRS_RELEASE_SPACE    C, AC, C^T A C and its factor / inverse; n_c becomes 0 (export
+ *                        the space first with krs_export_space to restore it later with
+ *                        krs_import_space; C^(0) of the restart mode is kept);
+ *   KRS_RELEASE_MATRIX   the sequence's copy of A (re-uploaded by the next solve). */
+enum { KRS_RELEASE_SCRATCH = 1, KRS_RELEASE_SPACE = 2, KRS_RELEASE_MATRIX = 4 };
+krs_status krs_device_bytes(krs_seq_t s, int64_t* bytes);
+krs_status krs_release(krs_seq_t s, int32_t what);
+
+/* --- batched solves --------------------------------------------------------------------
+ * An engine that runs the iteration loops of many solves -- of different sequences,
+ * sizes and spaces -- in one cooperative persistent launch (the paper solves one system
+ * at a time; this is the same Algorithm 1 per solve).  The grid is cut into groups of
+ * group_ctas CTAs; each group takes the next solve from a queue ordered by estimated
+ * remaining work (largest first) and runs it with its own barrier and partial sums.
+ * Per solve, everything around the loop (set-up, init, recycling step, result, stats in
+ * krs_stats of its sequence) is the same as krs_solve's, on the engine's stream.
+ * Results: a solve's arithmetic depends only on group_ctas (its partition), so it is
+ * bitwise the same whichever other solves share the engine; against krs_solve (another
+ * partition) it differs by rounding only.
+ * Direction storage starts at 1.25x the sequence's previous iteration count (12 n^(1/3)
+ * for its first solve) and grows between launches when a solve fills it.
+ * Only KRS_FP64 policies are accepted; `exec` is ignored (the batched persistent kernel
+ * runs every solve).  The engine must not be used from two threads at once, and a
+ * sequence with a solve in flight must not be used elsewhere until it is returned. */
+typedef struct krs_batch* krs_batch_t;
+
+typedef struct {
+  int32_t group_ctas;   /* CTAs per solve; 0 = chosen by the autotuner on the first launch */
+  int32_t quantum;      /* iterations a solve runs per launch before the engine returns
+                           control (finished solves are returned, new ones admitted);
+                           0 = every launch runs until the queue is empty */
+  int32_t reserved[6];
+} krs_batch_config;
+
+typedef struct {
+  int32_t group_ctas, groups;  /* of the last launch */
+  int32_t in_flight;           /* submitted solves not yet returned */
+  int32_t last_launch_solves;  /* solves in the last launch's queue */
+  int64_t launches;            /* batched persistent launches so far */
+  int64_t kernel_launches;     /* all kernels the engine itself launched */
+  double last_kernel_ms;       /* event time of the last batched launch */
+  double total_kernel_ms;
+  int32_t tuned_group_ctas;    /* autotuner's choice (0 if it did not run) */
+  int32_t tune_candidates;     /* entries of tune_g / tune_ms */
+  int32_t tune_g[8];
+  double tune_ms[8];           /* probe time of each candidate */
+} krs_batch_stats;
+
+/* Create an engine on dev (allocator, stream, device as for krs_create_sequence); cfg may
+ * be NULL (autotuned group size, quantum 0).  group_ctas larger than the SM count:
+ * KRS_ERR_INVALID_ARG. */
+krs_status krs_batch_create(const krs_device* dev, const krs_batch_config* cfg, krs_batch_t* out);
+/* Destroy the engine; solves still in flight are dropped (their sequences stay usable). */
+krs_status krs_batch_destroy(krs_batch_t b);
+/* Submit one solve of sequence s (arguments as for krs_solve; x receives the result when
+ * the solve is returned by krs_batch_step and must stay valid until then).  Set-up and
+ * init run now; errors there (bad argument, NOT_SPD preconditioner or coarse factor) are
+ * returned here and nothing is queued.  tag is returned with the result. */
+krs_status krs_batch_submit(krs_batch_t b, krs_seq_t s, const krs_bsr* A, const double* rhs, double* x,
+                            double tol, const krs_policy* p, int64_t tag);
+/* One launch over every queued solve (at most `quantum` iterations each), then the
+ * recycling step and result of every solve that ended.  Up to max_done (tag, status)
+ * pairs of returned solves are written; further ones are kept for the next call.
+ * A device wait that timed out ends the launch: unfinished solves return KRS_ERR_TIMEOUT. */
+krs_status krs_batch_step(krs_batch_t b, int32_t max_done, int64_t* done_tags, int32_t* done_status,
+                          int32_t* n_done);
+/* One solve of each of `count` distinct sequences: seqs[i] with A[i], rhs[i], x[i], all
+ * with tol and p; status[i] receives each solve's outcome.  Returns KRS_OK when all
+ * succeeded, else the first failure.  The engine must have no solve in flight. */
+krs_status krs_solve_batch(krs_batch_t b, int32_t count, const krs_seq_t* seqs, const krs_bsr* A,
+                           const double* const* rhs, double* const* x, double tol, const krs_policy* p,
+                           int32_t* status);
+krs_status krs_batch_get_stats(krs_batch_t b, krs_batch_stats* out);
+
 /* --- single kernels (device pointers, ordered on `stream`; asynchronous) ----------------
  * These are the building blocks of the solve, exposed for verification and measurement.
  * Scratch memory they need is allocated with cudaMallocAsync on the stream.              */

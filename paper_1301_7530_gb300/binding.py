@@ -61,6 +61,26 @@ class krs_solve_stats(ct.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class krs_batch_config(ct.Structure):
+    _fields_ = [("group_ctas", ct.c_int32), ("quantum", ct.c_int32), ("reserved", ct.c_int32 * 6)]
+
+
+class krs_batch_stats(ct.Structure):
+    _fields_ = [("group_ctas", ct.c_int32), ("groups", ct.c_int32), ("in_flight", ct.c_int32),
+                ("last_launch_solves", ct.c_int32), ("launches", ct.c_int64), ("kernel_launches", ct.c_int64),
+                ("last_kernel_ms", ct.c_double), ("total_kernel_ms", ct.c_double),
+                ("tuned_group_ctas", ct.c_int32), ("tune_candidates", ct.c_int32),
+                ("tune_g", ct.c_int32 * 8), ("tune_ms", ct.c_double * 8)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("tune_g", "tune_ms")}
+        k = self.tune_candidates
+        d["tune"] = [(self.tune_g[i], self.tune_ms[i]) for i in range(min(k, 8))]
+        return d
+
+
+RELEASE_SCRATCH, RELEASE_SPACE, RELEASE_MATRIX = 1, 2, 4
+
 _lock = threading.Lock()
 _lib = None
 
@@ -90,6 +110,14 @@ SIGNATURES = {
     "krs_tridiag_eigvals": (ct.c_int, [_I32, _P, _P, _P, _P]),
     "krs_tridiag_eigvecs": (ct.c_int, [_I32, _P, _P, _I32, _P, _P, _P]),
     "krs_validate_bsr": (ct.c_int, [_I32, _I64, _P, _P]),
+    "krs_device_bytes": (ct.c_int, [_V, ct.POINTER(ct.c_int64)]),
+    "krs_release": (ct.c_int, [_V, _I32]),
+    "krs_batch_create": (ct.c_int, [ct.POINTER(krs_device), ct.POINTER(krs_batch_config), ct.POINTER(ct.c_void_p)]),
+    "krs_batch_destroy": (ct.c_int, [_V]),
+    "krs_batch_submit": (ct.c_int, [_V, _V, ct.POINTER(krs_bsr), _P, _P, _D, ct.POINTER(krs_policy), _I64]),
+    "krs_batch_step": (ct.c_int, [_V, _I32, _P, _P, ct.POINTER(ct.c_int32)]),
+    "krs_solve_batch": (ct.c_int, [_V, _I32, _P, ct.POINTER(krs_bsr), _P, _P, _D, ct.POINTER(krs_policy), _P]),
+    "krs_batch_get_stats": (ct.c_int, [_V, ct.POINTER(krs_batch_stats)]),
     "krs_version": (ct.c_char_p, []),
 }
 
@@ -276,6 +304,14 @@ class Sequence:
     def set_spin_limit(self, spins: int):
         check(lib().krs_set_spin_limit(self._h, int(spins)), "krs_set_spin_limit")
 
+    def device_bytes(self) -> int:
+        v = ct.c_int64()
+        check(lib().krs_device_bytes(self._h, ct.byref(v)), "krs_device_bytes")
+        return v.value
+
+    def release(self, what: int):
+        check(lib().krs_release(self._h, int(what)), "krs_release")
+
     def last_coeffs(self):
         m = self.stats()["m"]
         a, r, g = np.zeros(max(m, 1)), np.zeros(max(m, 1)), np.zeros(max(m, 1))
@@ -296,6 +332,94 @@ class Sequence:
         idx = {"W": 0, "AW": 1, "Z": 2}[which]
         check(lib().krs_last_vectors(self._h, idx, out.ctypes.data), "krs_last_vectors")
         return out[:m].T
+
+
+def _device_struct(device: int, stream, allocator):
+    dev = krs_device()
+    if allocator is not None:
+        dev.alloc, dev.free = allocator.alloc_fn, allocator.free_fn
+    dev.ctx = None
+    dev.cuda_stream = stream.cuda_stream
+    dev.device = device
+    return dev
+
+
+class Batch:
+    """Batched engine (krs_batch_t): solves of many sequences in one persistent launch."""
+
+    def __init__(self, device: int = 0, stream=None, group_ctas: int = 0, quantum: int = 0,
+                 torch_allocator: bool = True):
+        import torch
+        L = lib()
+        self.device = int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._alloc = TorchAllocator(self.device, self.stream) if torch_allocator else None
+        self._dev = _device_struct(self.device, self.stream, self._alloc)
+        cfg = krs_batch_config(int(group_ctas), int(quantum))
+        h = ct.c_void_p()
+        check(L.krs_batch_create(ct.byref(self._dev), ct.byref(cfg), ct.byref(h)), "krs_batch_create")
+        self._h = h
+        self._pending = {}  # tag -> (x, keep-alive objects)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().krs_batch_destroy(self._h)
+            self._h = None
+            self._pending.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def submit(self, seq: Sequence, A, b, tol: float, policy: krs_policy, tag: int, x=None,
+               version: int | None = None):
+        """Queue one solve of `seq`; x (returned by step() under `tag`) receives the result."""
+        keep = []
+        bs = bsr_struct(A, new_version() if version is None else version, keep=keep)
+        if x is None:
+            x = np.zeros(seq.n) if isinstance(b, np.ndarray) else b.new_zeros(seq.n)
+        check(lib().krs_batch_submit(self._h, seq._h, ct.byref(bs), ptr(b), ptr(x), float(tol),
+                                     ct.byref(policy), int(tag)), "krs_batch_submit")
+        self._pending[int(tag)] = x
+        return x
+
+    def step(self):
+        """One launch; returns [(tag, status, x)] of the solves that were returned."""
+        cap = max(len(self._pending), 1)
+        tags = np.zeros(cap, dtype=np.int64)
+        sts = np.zeros(cap, dtype=np.int32)
+        nd = ct.c_int32()
+        check(lib().krs_batch_step(self._h, cap, tags.ctypes.data, sts.ctypes.data, ct.byref(nd)), "krs_batch_step")
+        out = []
+        for i in range(nd.value):
+            t = int(tags[i])
+            out.append((t, int(sts[i]), self._pending.pop(t, None)))
+        return out
+
+    def solve(self, seqs, As, bs, tol: float, policy: krs_policy, xs=None, versions=None):
+        """One solve per sequence (krs_solve_batch); returns (xs, statuses)."""
+        n = len(seqs)
+        keep = []
+        mats = (krs_bsr * max(n, 1))()
+        for i, A in enumerate(As):
+            mats[i] = bsr_struct(A, new_version() if versions is None else versions[i], keep=keep)
+        if xs is None:
+            xs = [np.zeros(s.n) if isinstance(b, np.ndarray) else b.new_zeros(s.n) for s, b in zip(seqs, bs)]
+        hs = (ct.c_void_p * max(n, 1))(*[s._h.value for s in seqs])
+        rp = (ct.c_void_p * max(n, 1))(*[ptr(b) for b in bs])
+        xp = (ct.c_void_p * max(n, 1))(*[ptr(x) for x in xs])
+        sts = np.zeros(max(n, 1), dtype=np.int32)
+        st = lib().krs_solve_batch(self._h, n, hs, mats, rp, xp, float(tol), ct.byref(policy), sts.ctypes.data)
+        if st not in (OK, ERR_NO_CONVERGENCE) and not np.any(sts[:n] != OK):
+            raise KrsError(st, "krs_solve_batch")
+        return xs, [int(v) for v in sts[:n]]
+
+    def stats(self) -> dict:
+        out = krs_batch_stats()
+        check(lib().krs_batch_get_stats(self._h, ct.byref(out)), "krs_batch_get_stats")
+        return out.as_dict()
 
 
 # re-export the C function names as thin callables (same names as the C ABI)

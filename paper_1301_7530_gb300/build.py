@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libkrs.so")
-SOURCES = ["krs_api.cu", "krs_apcg.cu", "krs_kernels.cu", "krs_eig.cu", "krs_noalloc.cu"]
+SOURCES = ["krs_api.cu", "krs_apcg.cu", "krs_kernels.cu", "krs_eig.cu", "krs_noalloc.cu", "krs_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

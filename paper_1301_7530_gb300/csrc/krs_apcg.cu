@@ -24,6 +24,9 @@
 // block products and the coarse solve are the items of Section 2.3.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
+
+#include <mutex>
 
 #include "krs_device.cuh"
 #include "krs_internal.h"
@@ -33,11 +36,14 @@ namespace krs {
 template <typename T>
 struct ApcgCtx {
   int64_t n, ld;       // order, leading dimension of multi-vectors and vector padding
-  int nbr, npc, P;     // block rows, nodes per CTA, CTAs
+  int nbr, npc, P;     // block rows, nodes per CTA, CTAs of this problem's group
+  int cta0;            // first CTA of the group in a batched launch (0 otherwise)
+  int lb;              // this CTA's index within its group (set on kernel entry)
   int nc, ldg;         // columns of C, leading dimension of Ginv
   int nc_dense;        // columns [0, nc_dense) use Ginv; columns [nc_dense, nc) are mutually
                        // A-conjugate directions whose coarse block is diag(dinv)
   int max_iter, reorth_full, precond;
+  int jcap;            // iterations j >= jcap do not start in this launch (direction storage)
   double tol2;         // tol^2 * ||b||^2
   long long spin_limit;
   const double* dinv;  // 1/(w_i, A w_i) of the tail columns
@@ -64,7 +70,8 @@ struct ApcgCtx {
   double* vpart;       // [P * vld]  partials of t = (AC)^T u
   double* gpart;       // [P * vld]  partials of g = (AW)^T z (separate: no phase overlap hazard)
   int64_t vld;
-  int* ctrl;
+  int* ctrl;           // this solve's status / done / iteration words
+  int* bctrl;          // status / abort words the barrier watches (== ctrl for one solve)
   unsigned long long* bar;
 };
 
@@ -90,7 +97,7 @@ enum PhaseResult { PH_CONTINUE = 0, PH_STOP = 1 };
 
 template <typename T>
 __device__ __forceinline__ void finish(const ApcgCtx<T>& c, int status, int m) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (c.lb == 0 && threadIdx.x == 0) {
     if (status) atomicCAS(c.ctrl + CTRL_STATUS, 0, status);
     c.ctrl[CTRL_M] = m;
     c.ctrl[CTRL_DONE] = 1;
@@ -144,15 +151,15 @@ __device__ __forceinline__ double coarse_coef(const double* Ginv, int ldg, int n
 template <typename T>
 __device__ __forceinline__ void phase1(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
   int64_t r0, r1;
-  cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
+  cta_rows(c.nbr, c.npc, c.lb, r0, r1);
   const T* w = c.W + (int64_t)j * c.ld;
   T* q = c.AW + (int64_t)j * c.ld;
   double wq = 0.0, rw = 0.0;
   cta_spmv<T>(c.rp, c.ci, c.vals, w, q, c.r, r0, r1, wq, rw);
   block_sum2(wq, rw, sm.red);
   if (threadIdx.x == 0) {
-    c.part[blockIdx.x * PS_STRIDE + PS_WQ] = wq;
-    c.part[blockIdx.x * PS_STRIDE + PS_RW] = rw;
+    c.part[c.lb * PS_STRIDE + PS_WQ] = wq;
+    c.part[c.lb * PS_STRIDE + PS_RW] = rw;
   }
 }
 
@@ -165,13 +172,13 @@ __device__ __forceinline__ int phase2(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
     return PH_STOP;
   }
   const double al = rws / gam;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (c.lb == 0 && threadIdx.x == 0) {
     c.alpha[j] = al;
     c.gamma[j] = gam;
   }
   const T alT = (T)al;
   int64_t r0, r1;
-  cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
+  cta_rows(c.nbr, c.npc, c.lb, r0, r1);
   const T* w = c.W + (int64_t)j * c.ld;
   const T* q = c.AW + (int64_t)j * c.ld;
   double rr = 0.0;
@@ -185,9 +192,9 @@ __device__ __forceinline__ int phase2(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
   for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB)
     c.u[row] = precond_row<T>(c.precond, c.minv, c.r, row);
   rr = block_sum(rr, sm.red);
-  if (threadIdx.x == 0) c.part[blockIdx.x * PS_STRIDE + PS_RR] = rr;
+  if (threadIdx.x == 0) c.part[c.lb * PS_STRIDE + PS_RR] = rr;
   if (c.nc > 0)
-    cta_gemv_t<true, T>(c.AC, c.ld, c.nc, c.u, r0, r1, c.vpart + blockIdx.x * c.vld, sm.su, sm.red);
+    cta_gemv_t<true, T>(c.AC, c.ld, c.nc, c.u, r0, r1, c.vpart + c.lb * c.vld, sm.su, sm.red);
   return PH_CONTINUE;
 }
 
@@ -213,7 +220,7 @@ __device__ __forceinline__ int phase3(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
   if (c.nc > SMALL_NC) {
     // slice of t reduced here; s follows in phase 4 after a barrier
     int a, e;
-    col_slice(c.nc, c.P, blockIdx.x, a, e);
+    col_slice(c.nc, c.P, c.lb, a, e);
     for (int col = a + warp; col < e; col += TPB / 32) {
       const double v = warp_sum_strided(c.vpart + col, c.P, c.vld);
       if (lane == 0) c.tfull[col] = v;
@@ -229,7 +236,7 @@ __device__ __forceinline__ int phase3(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
       const double sacc = coarse_coef(c.Ginv, c.ldg, c.nc_dense, c.dinv, col, sm.red);
       if (lane == 0) {
         sm.sv[col] = (T)sacc;
-        if (blockIdx.x == 0) c.sfull[col] = sacc;  // for the per-phase kernel mode
+        if (c.lb == 0) c.sfull[col] = sacc;  // for the per-phase kernel mode
       }
     }
     __syncthreads();
@@ -240,7 +247,7 @@ __device__ __forceinline__ int phase3(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
 template <typename T>
 __device__ __forceinline__ void phase4(const ApcgCtx<T>& c) {
   int a, e;
-  col_slice(c.nc, c.P, blockIdx.x, a, e);
+  col_slice(c.nc, c.P, c.lb, a, e);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int col = a + warp; col < e; col += TPB / 32) {
     const double s = coarse_coef(c.Ginv, c.ldg, c.nc_dense, c.dinv, col, c.tfull);
@@ -253,7 +260,7 @@ __device__ __forceinline__ void phase4(const ApcgCtx<T>& c) {
 template <typename T>
 __device__ __forceinline__ void phase5(const ApcgCtx<T>& c, int j, Smem<T>& sm, bool s_in_smem) {
   int64_t r0, r1;
-  cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
+  cta_rows(c.nbr, c.npc, c.lb, r0, r1);
   T* z = c.Z + (int64_t)(j + 1) * c.ld;
   if (c.nc > 0) {
     if (!s_in_smem) {
@@ -268,10 +275,10 @@ __device__ __forceinline__ void phase5(const ApcgCtx<T>& c, int j, Smem<T>& sm, 
   double rz = 0.0;
   for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) rz += (double)c.r[row] * (double)z[row];
   rz = block_sum(rz, sm.red);
-  if (threadIdx.x == 0) c.part[blockIdx.x * PS_STRIDE + PS_RZ] = rz;
+  if (threadIdx.x == 0) c.part[c.lb * PS_STRIDE + PS_RZ] = rz;
   const int base = c.reorth_full ? 0 : j;
   const int kk = j + 1 - base;
-  cta_gemv_t<false, T>(c.AW + (int64_t)base * c.ld, c.ld, kk, z, r0, r1, c.gpart + blockIdx.x * c.vld,
+  cta_gemv_t<false, T>(c.AW + (int64_t)base * c.ld, c.ld, kk, z, r0, r1, c.gpart + c.lb * c.vld,
                        sm.su, sm.red);
 }
 
@@ -282,11 +289,11 @@ __device__ __forceinline__ int phase6(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
     finish(c, 2 /* KRS_ERR_NOT_SPD */, j + 1);
     return PH_STOP;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) c.rho[j + 1] = rz;
+  if (c.lb == 0 && threadIdx.x == 0) c.rho[j + 1] = rz;
   const int base = c.reorth_full ? 0 : j;
   const int kk = j + 1 - base;
   int a, e;
-  col_slice(kk, c.P, blockIdx.x, a, e);
+  col_slice(kk, c.P, c.lb, a, e);
   const int warp = threadIdx.x >> 5;
   for (int col = a + warp; col < e; col += TPB / 32) {
     const double v = warp_sum_strided(c.gpart + col, c.P, c.vld);
@@ -298,7 +305,7 @@ __device__ __forceinline__ int phase6(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
 template <typename T>
 __device__ __forceinline__ void phase7(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
   int64_t r0, r1;
-  cta_rows(c.nbr, c.npc, blockIdx.x, r0, r1);
+  cta_rows(c.nbr, c.npc, c.lb, r0, r1);
   const int base = c.reorth_full ? 0 : j;
   const int kk = j + 1 - base;
   for (int k = threadIdx.x; k < kk; k += TPB) sm.sv[k] = (T)c.gfull[k];
@@ -311,22 +318,30 @@ __device__ __forceinline__ void phase7(const ApcgCtx<T>& c, int j, Smem<T>& sm) 
 // ------------------------------------------------------------------------------------
 // persistent kernel: the whole iteration loop of one solve
 // ------------------------------------------------------------------------------------
+enum LoopResult { LOOP_ENDED = 0, LOOP_SUSPENDED = 1, LOOP_ABORTED = 2 };
+
+// The iteration loop of one solve from iteration j0, run by the CTAs of one group: at most
+// `quantum` iterations, after which the solve is suspended with CTRL_J = the next iteration
+// (every value the loop carries from one iteration to the next is in global memory).
+// `target` is the CTA's running count for the group's barrier counter.
 template <typename T>
-__global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx<T> c) {
-  extern __shared__ double4_32a smem_raw4[];
-  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
-  unsigned long long target = 0;
+__device__ __forceinline__ int apcg_loop(const ApcgCtx<T>& c, Smem<T>& sm, int j0, int quantum,
+                                         unsigned long long& target) {
   const int TO = 6;  // KRS_ERR_TIMEOUT
-#define KRS_SYNC()                                                                   \
-  do {                                                                               \
-    if (!grid_barrier(c.bar, target, (unsigned)c.P, c.ctrl, c.spin_limit, TO)) return; \
+#define KRS_SYNC()                                                                         \
+  do {                                                                                     \
+    if (!grid_barrier(c.bar, target, (unsigned)c.P, c.bctrl, c.spin_limit, TO)) return LOOP_ABORTED; \
   } while (0)
-  for (int j = 0;; j++) {
+  for (int j = j0;; j++) {
+    if (j - j0 >= quantum || j >= c.jcap) {
+      if (c.lb == 0 && threadIdx.x == 0) c.ctrl[CTRL_J] = j;
+      return LOOP_SUSPENDED;
+    }
     phase1(c, j, sm);
     KRS_SYNC();
-    if (phase2(c, j, sm) == PH_STOP) return;
+    if (phase2(c, j, sm) == PH_STOP) return LOOP_ENDED;
     KRS_SYNC();
-    if (phase3(c, j, sm) == PH_STOP) return;
+    if (phase3(c, j, sm) == PH_STOP) return LOOP_ENDED;
     if (c.nc > SMALL_NC) {
       KRS_SYNC();
       phase4(c);
@@ -336,12 +351,91 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx<T> c) {
       phase5(c, j, sm, true);  // nothing written in phase 3 is read by another CTA here
     }
     KRS_SYNC();
-    if (phase6(c, j, sm) == PH_STOP) return;
+    if (phase6(c, j, sm) == PH_STOP) return LOOP_ENDED;
     KRS_SYNC();
     phase7(c, j, sm);
     KRS_SYNC();
   }
 #undef KRS_SYNC
+}
+
+// persistent kernel: one solve, all CTAs in one group
+template <typename T>
+__global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx<T> c) {
+  extern __shared__ double4_32a smem_raw4[];
+  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
+  c.lb = blockIdx.x;
+  unsigned long long target = 0;
+  apcg_loop(c, sm, 0, 0x7fffffff, target);
+}
+
+// Batched persistent kernel: many independent solves in one cooperative launch.  The grid
+// is cut into groups of `g` CTAs.  A group takes the next solve from a work queue, runs its
+// iterations (at most `quantum` of them) with the group's own barrier counter and partial-sum
+// buffers, and takes the next, until the queue is empty.  Solves of uneven sizes and
+// iteration counts therefore never wait for each other, and a group that finishes early
+// picks up queued work at once.  Every solve's context is prepared for a partition over g
+// CTAs, so its arithmetic (the partition and the order of every reduction) does not depend
+// on which group runs it or on which other solves share the launch.
+template <typename T>
+struct BatchArgs {
+  const ApcgCtx<T>* ctxs;   // one per solve in the table
+  const int* queue;         // indices into ctxs, in the order groups should take them
+  int qlen;
+  int g;                    // CTAs per group
+  int quantum;              // iteration limit per solve in this launch
+  int* head;                // queue position (one counter, zero at launch)
+  int* mail;                // [groups * 2] solve index handed from the group's first CTA
+  unsigned long long* gbar; // [groups * 16] barrier counters (one 128-byte line each)
+  double* gpart;            // [groups * g * PS_STRIDE]
+  double* gvpart;           // [groups * g * vld]
+  double* ggpart;           // [groups * g * vld]
+  int64_t vld;
+  int* bctrl;               // launch-wide status / abort words
+};
+
+template <typename T>
+__global__ void __launch_bounds__(TPB, 1) k_apcg_batched(BatchArgs<T> B) {
+  extern __shared__ double4_32a smem_raw4[];
+  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
+  const int group = blockIdx.x / B.g;
+  const int lb = blockIdx.x % B.g;
+  unsigned long long* bar = B.gbar + (int64_t)group * 16;
+  unsigned long long target = 0;
+  __shared__ ApcgCtx<T> s_ctx;
+  __shared__ int s_j0;
+  long long spin_limit = B.queue && B.qlen > 0 ? B.ctxs[B.queue[0]].spin_limit : 1;
+  for (int round = 0;; round++) {
+    int* box = B.mail + 2 * group + (round & 1);
+    if (lb == 0 && threadIdx.x == 0) {
+      const int k = atomicAdd(B.head, 1);
+      *box = k < B.qlen ? B.queue[k] : -1;
+    }
+    if (!grid_barrier(bar, target, (unsigned)B.g, B.bctrl, spin_limit, 6)) return;
+    const int idx = *((volatile int*)box);
+    if (idx < 0) return;
+    // the solve's context lives in shared memory (the kernel-parameter copy of the
+    // single-solve kernel has no per-solve equivalent; registers would spill)
+    __syncthreads();  // every thread is done with the previous solve's context
+    if (threadIdx.x == 0) {
+      ApcgCtx<T> c = B.ctxs[idx];
+      c.lb = lb;
+      c.P = B.g;
+      c.bar = bar;
+      c.bctrl = B.bctrl;
+      c.part = B.gpart + (int64_t)group * B.g * PS_STRIDE;
+      c.vpart = B.gvpart + (int64_t)group * B.g * B.vld;
+      c.gpart = B.ggpart + (int64_t)group * B.g * B.vld;
+      c.vld = B.vld;
+      s_ctx = c;
+      s_j0 = *((volatile int*)(c.ctrl + CTRL_J));
+    }
+    __syncthreads();
+    const ApcgCtx<T>& c = s_ctx;
+    spin_limit = c.spin_limit;
+    const int j0 = s_j0;
+    if (apcg_loop(c, sm, j0, B.quantum, target) == LOOP_ABORTED) return;
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -357,6 +451,7 @@ __device__ __forceinline__ bool ended(const ApcgCtx<T>& c) {
   __global__ void __launch_bounds__(TPB, 1) NAME(ApcgCtx<T> c, int j) {      \
     extern __shared__ double4_32a smem_raw4[];                                \
     Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));       \
+    c.lb = blockIdx.x;                                                        \
     if (ended(c)) return;                                                     \
     (void)sm;                                                                 \
     BODY;                                                                     \
@@ -490,6 +585,7 @@ static ApcgCtx<T> make_ctx(const IterArgs& a) {
   c.n = a.n; c.ld = a.ld; c.nbr = a.nbr; c.npc = a.npc; c.P = a.P;
   c.nc = a.nc; c.ldg = a.ldg; c.max_iter = a.max_iter; c.reorth_full = a.reorth_full;
   c.nc_dense = a.nc_dense; c.dinv = a.dinv;
+  c.cta0 = 0; c.lb = 0; c.jcap = a.jcap > 0 ? a.jcap : 0x7fffffff;
   c.precond = a.precond; c.tol2 = a.tol2; c.spin_limit = a.spin_limit;
   c.rp = a.rp; c.ci = a.ci;
   c.vals = static_cast<const T*>(a.vals); c.minv = static_cast<const T*>(a.minv);
@@ -499,6 +595,7 @@ static ApcgCtx<T> make_ctx(const IterArgs& a) {
   c.alpha = a.alpha; c.gamma = a.gamma; c.rho = a.rho;
   c.tfull = a.tfull; c.sfull = a.sfull; c.gfull = a.gfull;
   c.part = a.part; c.vpart = a.vpart; c.gpart = a.gpart; c.vld = a.vld; c.ctrl = a.ctrl; c.bar = a.bar;
+  c.bctrl = a.ctrl;
   return c;
 }
 
@@ -515,9 +612,23 @@ static cudaError_t prepare_attributes_t(size_t sm) {
   return cudaSuccess;
 }
 
+// The dynamic shared-memory limit is a per-function attribute of the device: it only ever
+// grows here, so a launch prepared for one solve stays valid after another solve (of a
+// smaller kmax) prepared the same kernels.
 cudaError_t apcg_prepare_attributes(int kmax, bool fp32) {
+  static std::mutex mu;
+  static size_t set_bytes[64][2] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   const size_t sm = apcg_smem_bytes(kmax);
-  return fp32 ? prepare_attributes_t<float>(sm) : prepare_attributes_t<double>(sm);
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = set_bytes[dev][fp32 ? 1 : 0];
+  if (sm <= cur) return cudaSuccess;
+  e = fp32 ? prepare_attributes_t<float>(sm) : prepare_attributes_t<double>(sm);
+  if (e == cudaSuccess) cur = sm;
+  return e;
 }
 
 cudaError_t apcg_max_coresident(int kmax, bool fp32, int* blocks_per_sm) {
@@ -579,6 +690,53 @@ cudaError_t apcg_launch_persistent(const IterArgs& a, cudaStream_t st, int64_t* 
   void* args[] = {&c};
   return cudaLaunchCooperativeKernel((const void*)k_apcg_persistent<double>, dim3(a.P), dim3(TPB), args,
                                      apcg_smem_bytes(a.kmax), st);
+}
+
+size_t apcg_ctx_bytes() { return sizeof(ApcgCtx<double>); }
+
+void apcg_fill_ctx(const IterArgs& a, void* dst) {
+  ApcgCtx<double> c = make_ctx<double>(a);
+  memcpy(dst, &c, sizeof(c));
+}
+
+cudaError_t apcg_batched_coresident(int kmax, int* blocks_per_sm) {
+  const size_t sm = apcg_smem_bytes(kmax);
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_apcg_batched<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_apcg_batched<double>, TPB, sm);
+}
+
+// out[4 p + w] = word w (status, done, m, j) of solve p's control block
+__global__ void k_gather_ctrl(const ApcgCtx<double>* __restrict__ ctxs, int count, int* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 4 * count) out[i] = *((volatile const int*)(ctxs[i >> 2].ctrl + (i & 3)));
+}
+
+cudaError_t apcg_gather_ctrl(const void* ctxs, int count, int* out, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_gather_ctrl<<<(4 * count + 255) / 256, 256, 0, st>>>(static_cast<const ApcgCtx<double>*>(ctxs), count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t apcg_launch_batched(const BatchLaunch& L, cudaStream_t st) {
+  BatchArgs<double> B;
+  B.ctxs = static_cast<const ApcgCtx<double>*>(L.ctxs);
+  B.queue = L.queue;
+  B.qlen = L.qlen;
+  B.g = L.g;
+  B.quantum = L.quantum > 0 ? L.quantum : 0x7fffffff;
+  B.head = L.head;
+  B.mail = L.mail;
+  B.gbar = L.gbar;
+  B.gpart = L.gpart;
+  B.gvpart = L.gvpart;
+  B.ggpart = L.ggpart;
+  B.vld = L.vld;
+  B.bctrl = L.bctrl;
+  void* args[] = {&B};
+  return cudaLaunchCooperativeKernel((const void*)k_apcg_batched<double>, dim3(L.g * L.groups), dim3(TPB), args,
+                                     apcg_smem_bytes(L.kmax), st);
 }
 
 template <typename T>

@@ -19,6 +19,7 @@
 #include "krs.h"
 #include "krs_device.cuh"
 #include "krs_internal.h"
+#include "krs_seq.h"
 
 using namespace krs;
 
@@ -29,8 +30,7 @@ cudaError_t launch_tridiag_eigvals2(int m, int m1, const double* delta, const do
 
 static thread_local std::string g_last_error;
 
-static krs_status fail(krs_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
-static krs_status fail(krs_status st, const char* fmt, ...) {
+krs_status krs::failf(krs_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -39,123 +39,17 @@ static krs_status fail(krs_status st, const char* fmt, ...) {
   g_last_error = buf;
   return st;
 }
+#define fail krs::failf
 
 krs_status krs::set_error(krs_status st, const char* msg) {
   g_last_error = msg;
   return st;
 }
 
-#define KRS_CUDA(call)                                                                     \
-  do {                                                                                     \
-    cudaError_t e_ = (call);                                                               \
-    if (e_ != cudaSuccess) {                                                               \
-      return fail(KRS_ERR_CUDA, "%s failed: %s (line %d)", #call, cudaGetErrorString(e_), \
-                  __LINE__);                                                               \
-    }                                                                                      \
-  } while (0)
-
-#define KRS_TRY(expr)                  \
-  do {                                 \
-    krs_status s_ = (expr);            \
-    if (s_ != KRS_OK) return s_;       \
-  } while (0)
-
-static const long long kDefaultSpin = 1ll << 24;
-static const int kMinNodesPerCta = 16;
-
-struct krs_seq {
-  int64_t n = 0, ld = 0;
-  int nbr = 0;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  void* (*ualloc)(size_t, void*) = nullptr;
-  void (*ufree)(void*, void*) = nullptr;
-  void* uctx = nullptr;
-  int sms = 0;
-  std::vector<void*> allocs;
-
-  // matrix
-  int32_t* rp = nullptr;
-  int32_t* ci = nullptr;
-  double* vals = nullptr;
-  int64_t nnzb_cap = 0;
-  const int32_t* rp_use = nullptr;
-  const int32_t* ci_use = nullptr;
-  const double* vals_use = nullptr;
-  bool A_valid = false;
-  uint64_t A_version = 0;
-  int precond_built = -1;
-  double* minv = nullptr;
-
-  // augmentation space
-  int nc = 0, cap_c = 0;
-  double* C = nullptr;
-  double* AC = nullptr;
-  int ac_valid = 0;   // columns of AC valid for the current A
-  int g_valid = 0;    // leading columns of G valid
-  bool ginv_valid = false;
-  double* G = nullptr;
-  double* Lw = nullptr;
-  double* Ginv = nullptr;
-  int nc0 = 0;
-  double* C0 = nullptr;
-
-  // Krylov storage and vectors
-  int cap_w = 0;
-  double *W = nullptr, *AW = nullptr, *Z = nullptr;
-  double *x = nullptr, *r = nullptr, *u = nullptr, *b = nullptr, *tmp = nullptr;
-
-  // scalars, partials, control
-  double *alpha = nullptr, *gamma = nullptr, *rho = nullptr;
-  double *tfull = nullptr, *sfull = nullptr, *gfull = nullptr;
-  double* part = nullptr;
-  double* vpart = nullptr;
-  double* gpart = nullptr;
-  int64_t vld = 0;
-  int vpart_P = 0;
-  int* ctrl = nullptr;
-  unsigned long long* bar = nullptr;
-  double* scal = nullptr;  // [0] bb, [1] rr0, [2] true residual^2
-
-  // eigen / Ritz scratch (sized by cap_w)
-  double *delta = nullptr, *eta = nullptr, *theta_m = nullptr, *theta_m1 = nullptr, *tsel = nullptr;
-  int* sel = nullptr;
-  int* selcount = nullptr;
-  double *Qsel = nullptr, *F = nullptr, *eigwork = nullptr;
-  int eig_cap = 0;
-
-  // Gram scratch
-  double* gram_scratch = nullptr;
-  size_t gram_cap = 0;
-
-  // FP32 copies for the inner solves of the mixed-precision refinement
-  float *vals32 = nullptr, *minv32 = nullptr, *C32 = nullptr, *AC32 = nullptr;
-  float *W32 = nullptr, *AW32 = nullptr, *Z32 = nullptr;
-  float *x32 = nullptr, *r32 = nullptr, *u32 = nullptr, *b32 = nullptr;
-  double* dinv = nullptr;  // 1/(w, Aw) of the inner directions appended within one system
-  int64_t vals32_cap = 0;
-  int cap_c32 = 0, cap_w32 = 0;
-  bool vals32_valid = false;
-  int minv32_kind = -1;
-
-  // pinned host mirrors
-  double* h_scal = nullptr;
-  int* h_ctrl = nullptr;
-
-  // last solve
-  krs_solve_stats st{};
-  int last_m = 0;
-  int last_ritz_m = 0;
-  int last_srks = 0;
-  int last_nsel = 0;
-  long long spin_limit = kDefaultSpin;
-  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-};
-
 // ------------------------------------------------------------------------------------
 // memory helpers
 // ------------------------------------------------------------------------------------
-static krs_status dev_alloc(krs_seq* s, size_t bytes, void** out) {
+krs_status krs::dev_alloc(krs_seq* s, size_t bytes, void** out) {
   void* p = nullptr;
   if (bytes == 0) bytes = 256;
   bytes = (bytes + 255) & ~size_t(255);
@@ -173,16 +67,21 @@ static krs_status dev_alloc(krs_seq* s, size_t bytes, void** out) {
   cudaError_t e = cudaMemsetAsync(p, 0, bytes, s->stream);
   if (e != cudaSuccess) return fail(KRS_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   s->allocs.push_back(p);
+  s->alloc_bytes.push_back(bytes);
+  s->bytes_held += (int64_t)bytes;
   *out = p;
   return KRS_OK;
 }
 
-static void dev_free(krs_seq* s, void* p) {
+void krs::dev_free(krs_seq* s, void* p) {
   if (!p) return;
   for (size_t i = 0; i < s->allocs.size(); i++) {
     if (s->allocs[i] == p) {
+      s->bytes_held -= (int64_t)s->alloc_bytes[i];
       s->allocs[i] = s->allocs.back();
+      s->alloc_bytes[i] = s->alloc_bytes.back();
       s->allocs.pop_back();
+      s->alloc_bytes.pop_back();
       break;
     }
   }
@@ -194,15 +93,7 @@ static void dev_free(krs_seq* s, void* p) {
   }
 }
 
-template <typename T>
-static krs_status alloc_n(krs_seq* s, T** p, size_t count) {
-  void* v = nullptr;
-  KRS_TRY(dev_alloc(s, count * sizeof(T), &v));
-  *p = static_cast<T*>(v);
-  return KRS_OK;
-}
-
-static bool is_device_ptr(const void* p) {
+bool krs::is_device_ptr(const void* p) {
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, p);
   if (e != cudaSuccess) {
@@ -211,8 +102,6 @@ static bool is_device_ptr(const void* p) {
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
-
-static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 // grow C / AC (and C^T A C work) to hold `need` columns, keeping the first nc columns
 static krs_status ensure_cap_c(krs_seq* s, int need) {
@@ -488,6 +377,74 @@ krs_status krs_import_space(krs_seq_t s, int32_t n_c, const double* C_in, int32_
   return KRS_OK;
 }
 
+krs_status krs_device_bytes(krs_seq_t s, int64_t* bytes) {
+  if (!s || !bytes) return fail(KRS_ERR_INVALID_ARG, "NULL argument");
+  *bytes = s->bytes_held;
+  return KRS_OK;
+}
+
+krs_status krs_release(krs_seq_t s, int32_t what) {
+  if (!s || (what & ~(KRS_RELEASE_SCRATCH | KRS_RELEASE_SPACE | KRS_RELEASE_MATRIX)))
+    return fail(KRS_ERR_INVALID_ARG, "bad argument");
+  if (s->busy) return fail(KRS_ERR_INVALID_ARG, "the sequence has a solve in flight");
+  KRS_CUDA(cudaSetDevice(s->device));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  auto drop = [&](auto*& p) {
+    dev_free(s, p);
+    p = nullptr;
+  };
+  if (what & KRS_RELEASE_SCRATCH) {
+    drop(s->W); drop(s->AW); drop(s->Z);
+    drop(s->alpha); drop(s->gamma); drop(s->rho); drop(s->gfull);
+    s->cap_w = 0;
+    drop(s->vpart); drop(s->gpart); drop(s->part); drop(s->tfull); drop(s->sfull);
+    s->vpart_P = 0;
+    s->vld = 0;
+    drop(s->delta); drop(s->eta); drop(s->theta_m); drop(s->theta_m1); drop(s->tsel); drop(s->sel);
+    s->eig_cap = 0;
+    drop(s->eigwork);
+    drop(s->gram_scratch);
+    s->gram_cap = 0;
+    drop(s->W32); drop(s->AW32); drop(s->Z32);
+    s->cap_w32 = 0;
+    drop(s->C32); drop(s->AC32); drop(s->dinv);
+    s->cap_c32 = 0;
+    drop(s->x32); drop(s->r32); drop(s->u32); drop(s->b32); drop(s->minv32);
+    s->minv32_kind = -1;
+    drop(s->vals32);
+    s->vals32_cap = 0;
+    s->vals32_valid = false;
+    s->last_m = 0;
+    s->last_ritz_m = 0;
+    s->last_srks = 0;
+    s->last_nsel = 0;
+  }
+  if (what & KRS_RELEASE_SPACE) {
+    drop(s->C); drop(s->AC); drop(s->G); drop(s->Lw); drop(s->Ginv);
+    s->cap_c = 0;
+    s->nc = 0;
+    s->ac_valid = 0;
+    s->g_valid = 0;
+    s->ginv_valid = false;
+  }
+  if (what & KRS_RELEASE_MATRIX) {
+    drop(s->rp); drop(s->ci); drop(s->vals);
+    s->nnzb_cap = 0;
+    s->rp_use = nullptr;
+    s->ci_use = nullptr;
+    s->vals_use = nullptr;
+    s->A_valid = false;
+    s->precond_built = -1;
+    s->ac_valid = 0;
+    s->g_valid = 0;
+    s->ginv_valid = false;
+    drop(s->vals32);
+    s->vals32_cap = 0;
+    s->vals32_valid = false;
+  }
+  return KRS_OK;
+}
+
 krs_status krs_last_coeffs(krs_seq_t s, double* alpha, double* rho, double* gamma) {
   if (!s) return fail(KRS_ERR_INVALID_ARG, "NULL sequence");
   const int m = s->last_m;
@@ -663,22 +620,25 @@ static krs_status ensure_mixed(krs_seq* s, int max_iter, int64_t nnzb) {
   return KRS_OK;
 }
 
-// One APCG solve (init + iterations) for the IterArgs `a` with right-hand side b_in (device,
-// a's value type), to ||r|| <= tol ||b_in||.  Adds the iteration kernels' event time to
-// *t_iter_ms.  Returns the krs_status of the CUDA calls; the solve's own outcome is in
-// *status, its iteration count in *m and ||b_in||^2 in *bb.
-static krs_status run_apcg(krs_seq* s, IterArgs& a, const void* b_in, double tol, int exec, int* status, int* m,
-                           double* bb, float* t_iter_ms, int64_t* launches) {
+// Init kernels of an APCG solve for the IterArgs `a` with right-hand side b_in (device, a's
+// value type), then one read of ||b_in||^2 (*bb) and ||r_0||^2 (*rr0); sets a.tol2.
+static krs_status run_init(krs_seq* s, IterArgs& a, const void* b_in, double tol, double* bb, double* rr0,
+                           int64_t* launches) {
   KRS_CUDA(apcg_launch_init(a, b_in, s->scal, s->stream, launches));
   KRS_CUDA(cudaMemcpyAsync(s->h_scal, s->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   KRS_CUDA(cudaStreamSynchronize(s->stream));
   *bb = s->h_scal[0];
-  const double rr0 = s->h_scal[1];
-  *status = KRS_OK;
-  *m = 0;
+  *rr0 = s->h_scal[1];
   if (!isfinite(*bb)) return fail(KRS_ERR_INVALID_ARG, "right-hand side is not finite");
   a.tol2 = tol * tol * (*bb);
-  if (rr0 <= a.tol2) return KRS_OK;
+  return KRS_OK;
+}
+
+// The iteration loop of an initialised solve (persistent kernel, or per-phase kernels).
+// Adds the iteration kernels' event time to *t_iter_ms; the solve's outcome is in *status
+// and its iteration count in *m.
+static krs_status run_loop(krs_seq* s, IterArgs& a, int exec, int* status, int* m, float* t_iter_ms,
+                           int64_t* launches) {
   KRS_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, s->stream));
   KRS_CUDA(cudaMemsetAsync(s->bar, 0, sizeof(unsigned long long), s->stream));
   KRS_CUDA(cudaEventRecord(s->ev[4], s->stream));
@@ -708,6 +668,17 @@ static krs_status run_apcg(krs_seq* s, IterArgs& a, const void* b_in, double tol
   *m = s->h_ctrl[CTRL_M];
   if (!s->h_ctrl[CTRL_DONE] && *status == KRS_OK) *status = KRS_ERR_CUDA;
   return KRS_OK;
+}
+
+// One APCG solve (init + iterations) to ||r|| <= tol ||b_in||; *bb = ||b_in||^2.
+static krs_status run_apcg(krs_seq* s, IterArgs& a, const void* b_in, double tol, int exec, int* status, int* m,
+                           double* bb, float* t_iter_ms, int64_t* launches) {
+  double rr0 = 0.0;
+  *status = KRS_OK;
+  *m = 0;
+  KRS_TRY(run_init(s, a, b_in, tol, bb, &rr0, launches));
+  if (rr0 <= a.tol2) return KRS_OK;
+  return run_loop(s, a, exec, status, m, t_iter_ms, launches);
 }
 
 // SRKS extraction (Algorithm 3) from the coefficients of an m-iteration solve and its z's
@@ -761,8 +732,11 @@ __global__ void k_f2d_cols(const float* __restrict__ src, double* __restrict__ d
     dst[i] = (double)src[i];
 }
 
-static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, double* x, double tol,
-                             const krs_policy* p) {
+// Set-up shared by both precisions: matrix, preconditioner, right-hand side, storage,
+// partition, coarse set-up (FP64), the FP32 copies (mixed), and the iteration arguments.
+// cap_iter: direction columns reserved (FP64 path).
+static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const krs_policy* p, int cap_iter,
+                            SolveState* ss) {
   krs_solve_stats st{};
   st.n_c = s->nc;
   s->st = st;
@@ -770,7 +744,7 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
   s->last_ritz_m = 0;
   s->last_srks = 0;
   s->last_nsel = 0;
-  int64_t launches = 0;
+  int64_t& launches = ss->launches;
   const bool mixed = p->precision == KRS_MIXED_IR;
   KRS_CUDA(cudaSetDevice(s->device));
   KRS_CUDA(cudaEventRecord(s->ev[0], s->stream));
@@ -799,12 +773,14 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
 
   // ---- storage, augmentation capacity for this solve's recycling step, partition
   const int nc = s->nc;
+  ss->nc = nc;
   const int cap = p->max_aug > 0 ? p->max_aug : 0x7fffffff;
   int room = 0;
   if (p->recycle != KRS_RECYCLE_NONE) {
     room = (p->cap_mode == KRS_CAP_TRUNCATE) ? (cap - nc > 0 ? cap - nc : 0) : p->max_iter + 1;
     if (room > p->max_iter + 1) room = p->max_iter + 1;
   }
+  ss->room = room;
   // The mixed path appends after its first inner solve while later inner solves still use
   // C, AC and G^-1, so the room is reserved now; the FP64 path grows after its solve.
   if (mixed) {
@@ -812,14 +788,16 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
     KRS_TRY(ensure_mixed(s, p->max_iter, A->nnzb));
   } else {
     KRS_TRY(ensure_cap_c(s, nc));
-    KRS_TRY(ensure_cap_w(s, p->max_iter));
+    KRS_TRY(ensure_cap_w(s, cap_iter));
   }
   // largest column count a tall-skinny phase sees (mixed: C plus earlier inner directions)
-  const int kmax = mixed ? nc + p->max_iter + 1 : ((nc > p->max_iter + 1) ? nc : p->max_iter + 1);
+  const int kmax = mixed ? nc + p->max_iter + 1 : ((nc > cap_iter + 1) ? nc : cap_iter + 1);
+  ss->kmax = kmax;
   KRS_CUDA(apcg_prepare_attributes(kmax, mixed));
   int bps = 0;
   KRS_CUDA(apcg_max_coresident(kmax, mixed, &bps));
   if (bps < 1) return fail(KRS_ERR_CUDA, "persistent kernel cannot be resident (kmax %d)", kmax);
+  ss->bps = bps;
   int P = 0, npc = 0;
   partition(s, bps, &P, &npc);
   KRS_TRY(ensure_vpart(s, P, kmax));
@@ -880,7 +858,8 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
     }
   }
 
-  IterArgs a{};
+  IterArgs& a = ss->a;
+  a = IterArgs{};
   a.n = s->n; a.ld = s->ld; a.nbr = s->nbr; a.npc = npc; a.P = P;
   a.nc = nc; a.nc_dense = nc; a.dinv = s->dinv;
   a.ldg = s->cap_c; a.max_iter = p->max_iter; a.reorth_full = (p->reorth == KRS_REORTH_FULL);
@@ -897,18 +876,67 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
     a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.x = s->x; a.r = s->r; a.u = s->u;
   }
   KRS_CUDA(cudaEventRecord(s->ev[1], s->stream));
+  return KRS_OK;
+}
 
-  int status = KRS_OK, m = 0, outer = 0, m_first = 0, add = 0;
-  float t_iter = 0.f;
-  double bb = 0.0;
+krs_status krs::seq_begin(krs_seq* s, const krs_bsr* A, const double* b, double tol, const krs_policy* p,
+                          int cap_iter, SolveState* ss) {
+  if (p->precision != KRS_FP64) return fail(KRS_ERR_INVALID_ARG, "internal: seq_begin is the FP64 path");
+  ss->tol = tol;
+  KRS_TRY(seq_setup(s, A, b, p, cap_iter, ss));
+  KRS_TRY(run_init(s, ss->a, s->b, tol, &ss->bb, &ss->rr0, &ss->launches));
+  ss->need_iter = ss->rr0 > ss->a.tol2;
+  return KRS_OK;
+}
+
+krs_status krs::seq_grow_directions(krs_seq* s, int cap_iter, int keep) {
+  const int need = cap_iter + 1;
+  if (need <= s->cap_w) return KRS_OK;
+  const int cap = (int)round_up(need, 32);
+  double *W = nullptr, *AW = nullptr, *Z = nullptr, *al = nullptr, *ga = nullptr, *rh = nullptr, *gf = nullptr;
+  KRS_TRY(alloc_n(s, &W, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &AW, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &Z, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &al, cap));
+  KRS_TRY(alloc_n(s, &ga, cap));
+  KRS_TRY(alloc_n(s, &rh, cap + 1));
+  KRS_TRY(alloc_n(s, &gf, cap));
+  if (keep > s->cap_w) keep = s->cap_w;
+  if (keep > 0) {
+    const size_t vb = sizeof(double) * (size_t)keep * s->ld;
+    KRS_CUDA(cudaMemcpyAsync(W, s->W, vb, cudaMemcpyDeviceToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(AW, s->AW, vb, cudaMemcpyDeviceToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(Z, s->Z, vb, cudaMemcpyDeviceToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(al, s->alpha, sizeof(double) * keep, cudaMemcpyDeviceToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(ga, s->gamma, sizeof(double) * keep, cudaMemcpyDeviceToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(rh, s->rho, sizeof(double) * (keep + 1), cudaMemcpyDeviceToDevice, s->stream));
+  }
+  dev_free(s, s->W);
+  dev_free(s, s->AW);
+  dev_free(s, s->Z);
+  dev_free(s, s->alpha);
+  dev_free(s, s->gamma);
+  dev_free(s, s->rho);
+  dev_free(s, s->gfull);
+  s->W = W; s->AW = AW; s->Z = Z;
+  s->alpha = al; s->gamma = ga; s->rho = rh; s->gfull = gf;
+  s->cap_w = cap;
+  return KRS_OK;
+}
+
+krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x, const krs_policy* p) {
+  const bool mixed = p->precision == KRS_MIXED_IR;
+  const int nc = ss->nc;
+  int64_t& launches = ss->launches;
+  krs_solve_stats st{};
   if (!mixed) {
-    // ---- FP64: one APCG solve, then the recycling step on its W / Z
-    KRS_TRY(run_apcg(s, a, s->b, tol, p->exec, &status, &m, &bb, &t_iter, &launches));
+    // ---- FP64: the recycling step on this solve's W / Z
     s->last_m = m;
     KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
+    ss->add = 0;
     if (status == KRS_OK) {
       if (p->recycle == KRS_RECYCLE_TRKS && m > 0) {
-        add = m < room ? m : room;
+        const int add = m < ss->room ? m : ss->room;
         if (add > 0) {
           KRS_TRY(ensure_cap_c(s, nc + add));
           KRS_CUDA(cudaMemcpyAsync(s->C + (size_t)nc * s->ld, s->W, sizeof(double) * (size_t)add * s->ld,
@@ -920,94 +948,14 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
             s->ac_valid = nc + add;
           }
         }
+        ss->add = add;
       } else if (p->recycle == KRS_RECYCLE_SRKS && m >= 2) {
-        KRS_TRY(srks_extract(s, m, nc, room, p, s->Z, nullptr, &add, &launches));
+        KRS_TRY(srks_extract(s, m, nc, ss->room, p, s->Z, nullptr, &ss->add, &launches));
       }
     }
-  } else {
-    // ---- mixed precision: FP64 refinement around FP32 inner APCG solves
-    const double inner_tol = p->inner_tol > 0.0 ? p->inner_tol : 0.1;
-    const int max_outer = p->max_outer > 0 ? p->max_outer : 30;
-    KRS_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * s->ld, s->stream));
-    // r = b - A*0 = b (FP64), r32 = (float) b, rr = ||b||^2
-    KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->r, s->b32,
-                                 s->part, s->scal + 4, s->stream));
-    launches += 3;
-    KRS_CUDA(cudaMemcpyAsync(s->h_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-    KRS_CUDA(cudaStreamSynchronize(s->stream));
-    bb = s->h_scal[4];
-    if (!isfinite(bb)) return fail(KRS_ERR_INVALID_ARG, "right-hand side is not finite");
-    double rr = bb;
-    bool first = true;
-    for (;;) {
-      if (rr <= tol * tol * bb) break;
-      if (outer >= max_outer || m >= p->max_iter) {
-        status = KRS_ERR_NO_CONVERGENCE;
-        break;
-      }
-      // aim at inner_tol, or less when the outer tolerance is closer than that
-      double tin = 0.5 * tol * sqrt(bb / rr);
-      if (tin < inner_tol) tin = inner_tol;
-      if (tin > 0.5) tin = 0.5;
-      a.max_iter = p->max_iter - m;
-      int st_in = KRS_OK, m_in = 0;
-      double bb_in = 0.0;
-      KRS_TRY(run_apcg(s, a, s->b32, tin, p->exec, &st_in, &m_in, &bb_in, &t_iter, &launches));
-      // An FP32 breakdown ((w, Aw) <= 0 or (r, z) <= 0) after some progress only ends this
-      // inner solve: its iterate and directions up to there are valid, and the FP64 outer
-      // residual decides whether refinement still advances.
-      if (st_in != KRS_OK && st_in != KRS_ERR_NO_CONVERGENCE && !(st_in == KRS_ERR_NOT_SPD && m_in > 0)) {
-        status = st_in;
-        break;
-      }
-      m += m_in;
-      s->last_m = m_in;
-      if (first) {
-        m_first = m_in;
-        // recycling from the first inner solve (staged beyond nc until the system converges)
-        if (p->recycle == KRS_RECYCLE_TRKS && m_in > 0) {
-          add = m_in < room ? m_in : room;
-          if (add > 0) {
-            k_f2d_cols<<<1216, 256, 0, s->stream>>>(s->W32, s->C + (size_t)nc * s->ld, (int64_t)add * s->ld);
-            KRS_CUDA(cudaGetLastError());
-            launches++;
-          }
-        } else if (p->recycle == KRS_RECYCLE_SRKS && m_in >= 2) {
-          KRS_TRY(srks_extract(s, m_in, nc, room, p, nullptr, s->Z32, &add, &launches));
-        }
-        first = false;
-      }
-      // The next inner solve (same operator) is augmented by this one's directions: they
-      // are A-conjugate to C and to each other, so their coarse block is diag(1/(w, Aw)).
-      if (m_in > 0) {
-        const int nct = a.nc;
-        KRS_CUDA(cudaMemcpyAsync(s->C32 + (size_t)nct * s->ld, s->W32, sizeof(float) * (size_t)m_in * s->ld,
-                                 cudaMemcpyDeviceToDevice, s->stream));
-        KRS_CUDA(cudaMemcpyAsync(s->AC32 + (size_t)nct * s->ld, s->AW32, sizeof(float) * (size_t)m_in * s->ld,
-                                 cudaMemcpyDeviceToDevice, s->stream));
-        k_recip<<<(m_in + 255) / 256, 256, 0, s->stream>>>(s->gamma, s->dinv + (nct - nc), m_in);
-        KRS_CUDA(cudaGetLastError());
-        launches++;
-        a.nc = nct + m_in;
-      }
-      // x += d (FP64), r = b - A x (FP64), next inner right-hand side r32 = (float) r
-      KRS_CUDA(launch_add_f2d(s->x, s->x32, s->n, s->stream));
-      KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->r, s->b32,
-                                   s->part, s->scal + 4, s->stream));
-      launches += 4;
-      KRS_CUDA(cudaMemcpyAsync(s->h_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-      KRS_CUDA(cudaStreamSynchronize(s->stream));
-      const double rr_new = s->h_scal[4];
-      outer++;
-      if (!(rr_new < 0.81 * rr) && !(rr_new <= tol * tol * bb)) {  // stagnation: refinement no longer pays
-        rr = rr_new;
-        status = KRS_ERR_NO_CONVERGENCE;
-        break;
-      }
-      rr = rr_new;
-    }
-    KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
   }
+  const int add = ss->add;
+  const double bb = ss->bb;
 
   // ---- result and true residual
   const bool x_dev = is_device_ptr(x);
@@ -1026,8 +974,8 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
   st.status = status;
   st.m = m;
   st.n_c = nc;
-  st.outer_iters = outer;
-  st.inner_m_first = m_first;
+  st.outer_iters = ss->outer;
+  st.inner_m_first = ss->m_first;
   st.true_rel_res = bb > 0.0 ? sqrt(s->h_scal[2] / bb) : 0.0;
   st.rel_res = mixed ? st.true_rel_res : (bb > 0.0 ? sqrt(s->h_scal[3] / bb) : 0.0);
   if (status != KRS_OK) {
@@ -1036,7 +984,7 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
     cudaEventElapsedTime(&t1, s->ev[0], s->ev[1]);
     cudaEventElapsedTime(&t3, s->ev[0], s->ev[2]);
     st.t_setup_ms = t1;
-    st.t_iter_ms = t_iter;
+    st.t_iter_ms = ss->t_iter;
     st.t_total_ms = t3;
     st.kernel_launches = launches;
     s->st = st;
@@ -1067,7 +1015,7 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
   st.n_selected = add;
   st.n_c_after = s->nc;
   st.t_setup_ms = t1;
-  st.t_iter_ms = t_iter;
+  st.t_iter_ms = ss->t_iter;
   st.t_recycle_ms = t3;
   st.t_total_ms = tt;
   st.kernel_launches = launches;
@@ -1075,9 +1023,123 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
   return KRS_OK;
 }
 
+// mixed precision: FP64 refinement around FP32 inner APCG solves
+static krs_status mixed_refine(krs_seq* s, const krs_policy* p, double tol, SolveState* ss, int* status_out,
+                               int* m_out) {
+  IterArgs& a = ss->a;
+  const int nc = ss->nc;
+  const int room = ss->room;
+  int64_t& launches = ss->launches;
+  int status = KRS_OK, m = 0, outer = 0, m_first = 0, add = 0;
+  const double inner_tol = p->inner_tol > 0.0 ? p->inner_tol : 0.1;
+  const int max_outer = p->max_outer > 0 ? p->max_outer : 30;
+  KRS_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * s->ld, s->stream));
+  // r = b - A*0 = b (FP64), r32 = (float) b, rr = ||b||^2
+  KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->r, s->b32,
+                               s->part, s->scal + 4, s->stream));
+  launches += 3;
+  KRS_CUDA(cudaMemcpyAsync(s->h_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  const double bb = s->h_scal[4];
+  ss->bb = bb;
+  if (!isfinite(bb)) return fail(KRS_ERR_INVALID_ARG, "right-hand side is not finite");
+  double rr = bb;
+  bool first = true;
+  for (;;) {
+    if (rr <= tol * tol * bb) break;
+    if (outer >= max_outer || m >= p->max_iter) {
+      status = KRS_ERR_NO_CONVERGENCE;
+      break;
+    }
+    // aim at inner_tol, or less when the outer tolerance is closer than that
+    double tin = 0.5 * tol * sqrt(bb / rr);
+    if (tin < inner_tol) tin = inner_tol;
+    if (tin > 0.5) tin = 0.5;
+    a.max_iter = p->max_iter - m;
+    int st_in = KRS_OK, m_in = 0;
+    double bb_in = 0.0;
+    KRS_TRY(run_apcg(s, a, s->b32, tin, p->exec, &st_in, &m_in, &bb_in, &ss->t_iter, &launches));
+    // An FP32 breakdown ((w, Aw) <= 0 or (r, z) <= 0) after some progress only ends this
+    // inner solve: its iterate and directions up to there are valid, and the FP64 outer
+    // residual decides whether refinement still advances.
+    if (st_in != KRS_OK && st_in != KRS_ERR_NO_CONVERGENCE && !(st_in == KRS_ERR_NOT_SPD && m_in > 0)) {
+      status = st_in;
+      break;
+    }
+    m += m_in;
+    s->last_m = m_in;
+    if (first) {
+      m_first = m_in;
+      // recycling from the first inner solve (staged beyond nc until the system converges)
+      if (p->recycle == KRS_RECYCLE_TRKS && m_in > 0) {
+        add = m_in < room ? m_in : room;
+        if (add > 0) {
+          k_f2d_cols<<<1216, 256, 0, s->stream>>>(s->W32, s->C + (size_t)nc * s->ld, (int64_t)add * s->ld);
+          KRS_CUDA(cudaGetLastError());
+          launches++;
+        }
+      } else if (p->recycle == KRS_RECYCLE_SRKS && m_in >= 2) {
+        KRS_TRY(srks_extract(s, m_in, nc, room, p, nullptr, s->Z32, &add, &launches));
+      }
+      first = false;
+    }
+    // The next inner solve (same operator) is augmented by this one's directions: they
+    // are A-conjugate to C and to each other, so their coarse block is diag(1/(w, Aw)).
+    if (m_in > 0) {
+      const int nct = a.nc;
+      KRS_CUDA(cudaMemcpyAsync(s->C32 + (size_t)nct * s->ld, s->W32, sizeof(float) * (size_t)m_in * s->ld,
+                               cudaMemcpyDeviceToDevice, s->stream));
+      KRS_CUDA(cudaMemcpyAsync(s->AC32 + (size_t)nct * s->ld, s->AW32, sizeof(float) * (size_t)m_in * s->ld,
+                               cudaMemcpyDeviceToDevice, s->stream));
+      k_recip<<<(m_in + 255) / 256, 256, 0, s->stream>>>(s->gamma, s->dinv + (nct - nc), m_in);
+      KRS_CUDA(cudaGetLastError());
+      launches++;
+      a.nc = nct + m_in;
+    }
+    // x += d (FP64), r = b - A x (FP64), next inner right-hand side r32 = (float) r
+    KRS_CUDA(launch_add_f2d(s->x, s->x32, s->n, s->stream));
+    KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->r, s->b32,
+                                 s->part, s->scal + 4, s->stream));
+    launches += 4;
+    KRS_CUDA(cudaMemcpyAsync(s->h_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    KRS_CUDA(cudaStreamSynchronize(s->stream));
+    const double rr_new = s->h_scal[4];
+    outer++;
+    if (!(rr_new < 0.81 * rr) && !(rr_new <= tol * tol * bb)) {  // stagnation: refinement no longer pays
+      rr = rr_new;
+      status = KRS_ERR_NO_CONVERGENCE;
+      break;
+    }
+    rr = rr_new;
+  }
+  KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
+  ss->add = add;
+  ss->outer = outer;
+  ss->m_first = m_first;
+  *status_out = status;
+  *m_out = m;
+  return KRS_OK;
+}
+
+static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, double* x, double tol,
+                             const krs_policy* p) {
+  SolveState ss;
+  ss.tol = tol;
+  int status = KRS_OK, m = 0;
+  if (p->precision == KRS_MIXED_IR) {
+    KRS_TRY(seq_setup(s, A, b, p, p->max_iter, &ss));
+    KRS_TRY(mixed_refine(s, p, tol, &ss, &status, &m));
+  } else {
+    KRS_TRY(seq_begin(s, A, b, tol, p, p->max_iter, &ss));
+    if (ss.need_iter) KRS_TRY(run_loop(s, ss.a, p->exec, &status, &m, &ss.t_iter, &ss.launches));
+  }
+  return seq_end(s, &ss, status, m, x, p);
+}
+
 extern "C" krs_status krs_solve(krs_seq_t s, const krs_bsr* A, const double* b, double* x, double tol,
                                 const krs_policy* p) {
   if (!s || !A || !b || !x) return fail(KRS_ERR_INVALID_ARG, "NULL argument");
+  if (s->busy) return fail(KRS_ERR_INVALID_ARG, "the sequence has a batched solve in flight");
   if (!(tol >= 0.0) || !isfinite(tol)) return fail(KRS_ERR_INVALID_ARG, "tol must be finite and >= 0");
   KRS_TRY(validate_policy(p));
   krs_status st = solve_impl(s, A, b, x, tol, p);

@@ -21,6 +21,7 @@ struct IterArgs {
   int nc_dense;          // columns of C with the dense coarse inverse Ginv (the rest: dinv)
   const double* dinv;    // 1/(w_i, A w_i) for columns [nc_dense, nc)
   int max_iter, reorth_full, precond;
+  int jcap;  // iterations j >= jcap do not start in one launch (0: no limit)
   int kmax;  // largest k a tall-skinny phase sees: max(nc, max_iter)
   bool fp32;
   double tol2;
@@ -43,8 +44,30 @@ struct IterArgs {
   unsigned long long* bar;
 };
 
+// One launch of the batched persistent kernel (FP64): groups of g CTAs take solves from
+// queue[0..qlen) (indices into the device array of contexts written by apcg_fill_ctx) and
+// run each for at most `quantum` iterations (<= 0: no limit).
+struct BatchLaunch {
+  const void* ctxs;
+  const int* queue;
+  int qlen;
+  int g, groups, quantum, kmax;
+  int* head;                  // zeroed before the launch
+  int* mail;                  // [2 * groups]
+  unsigned long long* gbar;   // [16 * groups], zeroed before the launch
+  double *gpart, *gvpart, *ggpart;
+  int64_t vld;
+  int* bctrl;                 // [CTRL_WORDS], zeroed before the launch
+};
+
 // krs_apcg.cu
 size_t apcg_smem_bytes(int kmax);
+size_t apcg_ctx_bytes();
+void apcg_fill_ctx(const IterArgs& a, void* dst);
+cudaError_t apcg_batched_coresident(int kmax, int* blocks_per_sm);
+cudaError_t apcg_launch_batched(const BatchLaunch& L, cudaStream_t st);
+// out[4 p + w], w = CTRL_STATUS, CTRL_DONE, CTRL_M, CTRL_J of the control block of ctxs[p]
+cudaError_t apcg_gather_ctrl(const void* ctxs, int count, int* out, cudaStream_t st);
 cudaError_t apcg_prepare_attributes(int kmax, bool fp32);
 cudaError_t apcg_max_coresident(int kmax, bool fp32, int* blocks_per_sm);
 cudaError_t apcg_launch_init(const IterArgs& a, const void* b, double* scal, cudaStream_t st, int64_t* launches);

@@ -1,0 +1,172 @@
+// krs_seq.h -- the state of one sequence of solves (krs_seq_t) and the host-side stages
+// of a solve, shared by the single-solve entry point and the batched engine.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "krs.h"
+#include "krs_internal.h"
+
+namespace krs {
+// printf-style krs_last_error() message; returns st
+krs_status failf(krs_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+}  // namespace krs
+
+#define KRS_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      return krs::failf(KRS_ERR_CUDA, "%s failed: %s (line %d)", #call, cudaGetErrorString(e_), \
+                        __LINE__);                                                           \
+    }                                                                                        \
+  } while (0)
+
+#define KRS_TRY(expr)            \
+  do {                           \
+    krs_status s_ = (expr);      \
+    if (s_ != KRS_OK) return s_; \
+  } while (0)
+
+constexpr long long kDefaultSpin = 1ll << 24;
+constexpr int kMinNodesPerCta = 16;
+
+struct krs_seq {
+  int64_t n = 0, ld = 0;
+  int nbr = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* (*ualloc)(size_t, void*) = nullptr;
+  void (*ufree)(void*, void*) = nullptr;
+  void* uctx = nullptr;
+  int sms = 0;
+  std::vector<void*> allocs;
+  std::vector<size_t> alloc_bytes;  // size of each entry of allocs
+  int64_t bytes_held = 0;           // device bytes this sequence holds
+  bool busy = false;                // a batched solve of this sequence is in flight
+
+  // matrix
+  int32_t* rp = nullptr;
+  int32_t* ci = nullptr;
+  double* vals = nullptr;
+  int64_t nnzb_cap = 0;
+  const int32_t* rp_use = nullptr;
+  const int32_t* ci_use = nullptr;
+  const double* vals_use = nullptr;
+  bool A_valid = false;
+  uint64_t A_version = 0;
+  int precond_built = -1;
+  double* minv = nullptr;
+
+  // augmentation space
+  int nc = 0, cap_c = 0;
+  double* C = nullptr;
+  double* AC = nullptr;
+  int ac_valid = 0;   // columns of AC valid for the current A
+  int g_valid = 0;    // leading columns of G valid
+  bool ginv_valid = false;
+  double* G = nullptr;
+  double* Lw = nullptr;
+  double* Ginv = nullptr;
+  int nc0 = 0;
+  double* C0 = nullptr;
+
+  // Krylov storage and vectors
+  int cap_w = 0;
+  double *W = nullptr, *AW = nullptr, *Z = nullptr;
+  double *x = nullptr, *r = nullptr, *u = nullptr, *b = nullptr, *tmp = nullptr;
+
+  // scalars, partials, control
+  double *alpha = nullptr, *gamma = nullptr, *rho = nullptr;
+  double *tfull = nullptr, *sfull = nullptr, *gfull = nullptr;
+  double* part = nullptr;
+  double* vpart = nullptr;
+  double* gpart = nullptr;
+  int64_t vld = 0;
+  int vpart_P = 0;
+  int* ctrl = nullptr;
+  unsigned long long* bar = nullptr;
+  double* scal = nullptr;  // [0] bb, [1] rr0, [2] true residual^2
+
+  // eigen / Ritz scratch (sized by cap_w)
+  double *delta = nullptr, *eta = nullptr, *theta_m = nullptr, *theta_m1 = nullptr, *tsel = nullptr;
+  int* sel = nullptr;
+  int* selcount = nullptr;
+  double *Qsel = nullptr, *F = nullptr, *eigwork = nullptr;
+  int eig_cap = 0;
+
+  // Gram scratch
+  double* gram_scratch = nullptr;
+  size_t gram_cap = 0;
+
+  // FP32 copies for the inner solves of the mixed-precision refinement
+  float *vals32 = nullptr, *minv32 = nullptr, *C32 = nullptr, *AC32 = nullptr;
+  float *W32 = nullptr, *AW32 = nullptr, *Z32 = nullptr;
+  float *x32 = nullptr, *r32 = nullptr, *u32 = nullptr, *b32 = nullptr;
+  double* dinv = nullptr;  // 1/(w, Aw) of the inner directions appended within one system
+  int64_t vals32_cap = 0;
+  int cap_c32 = 0, cap_w32 = 0;
+  bool vals32_valid = false;
+  int minv32_kind = -1;
+
+  // pinned host mirrors
+  double* h_scal = nullptr;
+  int* h_ctrl = nullptr;
+
+  // last solve
+  krs_solve_stats st{};
+  int last_m = 0;
+  int last_ritz_m = 0;
+  int last_srks = 0;
+  int last_nsel = 0;
+  long long spin_limit = kDefaultSpin;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace krs {
+
+krs_status dev_alloc(krs_seq* s, size_t bytes, void** out);
+void dev_free(krs_seq* s, void* p);
+template <typename T>
+krs_status alloc_n(krs_seq* s, T** p, size_t count) {
+  void* v = nullptr;
+  KRS_TRY(dev_alloc(s, count * sizeof(T), &v));
+  *p = static_cast<T*>(v);
+  return KRS_OK;
+}
+bool is_device_ptr(const void* p);
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// One FP64 solve split into the stages around its iteration loop.
+struct SolveState {
+  int nc = 0;        // columns of C used by this solve
+  int room = 0;      // columns the recycling step may append
+  int kmax = 0;      // largest column count a tall-skinny phase sees
+  int bps = 0;       // co-resident CTAs per SM of the persistent kernel
+  IterArgs a{};      // iteration arguments (own partition)
+  double tol = 0.0;
+  double bb = 0.0;   // ||b||^2
+  double rr0 = 0.0;  // ||r_0||^2
+  bool need_iter = false;
+  int add = 0;        // columns the recycling step appended (committed by seq_end)
+  int outer = 0;      // mixed precision: refinement steps
+  int m_first = 0;    // mixed precision: iterations of the first inner solve
+  int64_t launches = 0;
+  float t_iter = 0.f;
+};
+
+// Stage 1: matrix, preconditioner, right-hand side, storage (direction capacity `cap_iter`
+// columns), coarse set-up, and the init kernels (x_0, r_0, z_0, w_0, rho_0), followed by
+// one read of ||b||^2 and ||r_0||^2.  On return ss->need_iter says whether iterations run.
+krs_status seq_begin(krs_seq* s, const krs_bsr* A, const double* b, double tol, const krs_policy* p, int cap_iter,
+                     SolveState* ss);
+// Grow the direction storage to at least cap_iter + 1 columns keeping the first `keep`
+// columns of W, AW, Z and the scalars of the first `keep` iterations (between launches).
+krs_status seq_grow_directions(krs_seq* s, int cap_iter, int keep);
+// Stage 3: recycling step (TRKS / SRKS), result copy to x (host or device), true residual,
+// statistics and the commit of the new augmentation space.  `status` and `m` are the
+// iteration loop's outcome.
+krs_status seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x, const krs_policy* p);
+
+}  // namespace krs
