@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["krs", "reference"], default="krs")
     ap.add_argument("--N", type=int, default=32)
     ap.add_argument("--systems", type=int, default=20)
+    ap.add_argument("--systems-many", type=int, default=None, help="batched/served: systems per sequence (10 / 30)")
     ap.add_argument("--exec", choices=["persistent", "kernels"], default="persistent")
     ap.add_argument("--ritz-eps", type=float, default=1e-6)
     ap.add_argument("--theta-frac", type=float, default=0.1)
@@ -64,6 +65,18 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--workload", choices=["sequence", "batched", "served"], default="sequence",
+                    help="sequence: one 32^3 damage sequence (default); batched: many sequences of "
+                         "uneven size through the batched engine; served: Poisson requests of many clients")
+    ap.add_argument("--nseq", type=int, default=None, help="batched/served: sequences (256 / 64)")
+    ap.add_argument("--nmin", type=int, default=None, help="batched/served: smallest cube (16 / 12)")
+    ap.add_argument("--nmax", type=int, default=None, help="batched/served: largest cube (40 / 48)")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: offered requests per second")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="served: device memory budget")
+    ap.add_argument("--group-ctas", type=int, default=0, help="batched/served: CTAs per solve (0: autotune)")
+    ap.add_argument("--quantum", type=int, default=None, help="batched/served: iterations per launch")
+    ap.add_argument("--baseline-seqs", type=int, default=None,
+                    help="batched/served: sequences in the per-solve reference sample (default all)")
     return ap.parse_args()
 
 
@@ -430,8 +443,132 @@ def run_reference(args, rank, world):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------------------------------------------
+# many sequences: batched engine and served requests
+# ----------------------------------------------------------------------------------------
+
+def _many(args, kind):
+    """Clients of the batched / served workload (generated by a spawn pool before any GPU
+    call) and the policy."""
+    import multiprocessing as mp
+    if kind == "batched":
+        nseq, nmin, nmax, systems = args.nseq or 256, args.nmin or 16, args.nmax or 40, args.systems_many or 10
+    else:
+        nseq, nmin, nmax, systems = args.nseq or 64, args.nmin or 12, args.nmax or 48, args.systems_many or 30
+    Ns = P.batch_sizes(nseq, nmin, nmax, 4000 if kind == "batched" else 5000)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 1)) as pool:
+        from paper_1301_7530_gb300 import serve as S
+        clients = S.make_clients(Ns, systems, 7000 if kind == "batched" else 9000, pool=pool)
+    return Ns, systems, clients
+
+
+def _flops_of(reqs, Ns):
+    f = 0.0
+    for r in reqs:
+        if r.m > 0:
+            f += alg_counts(int(Ns[r.cid]), 24, r.m, r.n_c)[0]
+    return f
+
+
+def _reset(clients):
+    for c in clients:
+        c.seq.import_space(np.zeros((c.n, 0)))
+        c.m_prev = 0
+
+
+def run_many(args, kind):
+    import torch
+    from paper_1301_7530_gb300 import binding as B
+    from paper_1301_7530_gb300 import serve as S
+    Ns, systems, clients = _many(args, kind)
+    B.lib()
+    pol = B.make_policy("srks", "block_jacobi3", ritz_eps=args.ritz_eps, theta_frac=args.theta_frac,
+                        max_aug=100, max_iter=1000)
+    quantum = args.quantum if args.quantum is not None else (0 if kind == "batched" else 32)
+    budget = int(args.budget_gb * (1 << 30)) if kind == "served" else int(200 * (1 << 30))
+    srv = S.Server(clients, pol, TOL, budget_bytes=budget, group_ctas=args.group_ctas, quantum=quantum)
+    # warm-up: system 0 of every sequence (autotuner, allocations), then empty spaces again
+    srv.run([(0.0, c.cid, 0) for c in clients], closed_loop=True, n_systems=1)
+    _reset(clients)
+    bst0 = srv.engine.stats()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device(), enabled=not args.no_clocks)
+    t0 = time.perf_counter()
+    if kind == "batched":
+        reqs = srv.run([(0.0, c.cid, 0) for c in clients], closed_loop=True, n_systems=systems)
+    else:
+        reqs = srv.run(S.poisson_arrivals(len(clients), systems, args.rate, 11))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    bst = srv.engine.stats()
+    summ = S.latency_summary(reqs)
+    kern_ms = bst["total_kernel_ms"] - bst0["total_kernel_ms"]
+    flops = _flops_of(reqs, Ns)
+    ach = flops / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
+    value = len(reqs) / wall
+    srv.close()
+    # per-solve launches (krs_solve, one full-device persistent launch per solve) on the
+    # same sequences: the reference point the batched / served form must beat
+    nb = args.baseline_seqs or len(clients)
+    _reset(clients)
+    base_clients = clients[:nb]
+    el, breqs = S.solve_alone(base_clients, pol, TOL)
+    base_value = len(breqs) / el
+    cpu = None
+    if not args.no_cpu_baseline:
+        c0 = min(clients, key=lambda c: c.n)
+        from paper_1301_7530_gb300 import problems as PP
+        A_out, vin, b = PP.damage_parts(int(Ns[c0.cid]), (7000 if kind == "batched" else 9000) + c0.cid,
+                                        (7000 if kind == "batched" else 9000) + 10000 + c0.cid)
+        sec, st = oracle_one_solve([PP.damage_matrix(A_out, vin, 1.0)], b)
+        cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one oracle solve of the smallest sequence's first system (n = {c0.n}, m = {st['m']}), "
+                         f"single-threaded: {sec:.2f} s"}
+    hbm_peak, hbm_kind = measured_peaks()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": systems, "warmup": 1,
+        "ms_per_step": wall * 1e3 / systems, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "krs", "workload_kind": kind,
+        "config": {
+            "workload": (f"{len(clients)} damage sequences x {systems} systems, cubes N ~ U{{{min(Ns)}..{max(Ns)}}}"
+                         if kind == "batched" else
+                         f"{len(clients)} clients x {systems} damage systems, Poisson {args.rate}/s total, "
+                         f"cubes N ~ U{{{min(Ns)}..{max(Ns)}}}, budget {args.budget_gb} GB"),
+            "total_dofs": int(sum(c.n for c in clients)), "recycle": "srks", "ritz_eps": args.ritz_eps,
+            "theta_frac": args.theta_frac, "max_aug": 100, "tol": TOL, "precond": "block_jacobi3",
+            "group_ctas": bst["group_ctas"], "quantum": quantum,
+            "autotune": bst["tune"], "l2": "inputs larger than L2 (every sequence's matrices resident)"},
+        "latency_ms": {"p50": summ["p50_ms"], "p99": summ["p99_ms"], "mean": summ["mean_ms"],
+                       "what": "result returned - request arrival (host clock)"},
+        "per_solve_launches": {"value": base_value, "unit": UNIT, "sequences": nb,
+                               "what": "the same solves with krs_solve, one full-device launch each"},
+        "speedup_vs_per_solve": value / base_value,
+        "solves": {"count": len(reqs), "failed": summ["failed"], "true_rel_res_max": summ["max_true_rel_res"],
+                   "iterations": int(sum(r.m for r in reqs)),
+                   "iterations_per_solve_path": int(sum(r.m for r in breqs))},
+        "roofline": {"kernel": "k_apcg_batched", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel_ms": kern_ms, "share_of_wall": kern_ms / (wall * 1e3)},
+        "hbm_peak": {"value": hbm_peak, "kind": hbm_kind},
+        "server": {"steps": srv.steps, "evictions": srv.evictions, "reimports": srv.reimports,
+                   "peak_held_gb": srv.peak_held / 2 ** 30},
+        "e2e": None,
+        "gpu_launches": int(bst["kernel_launches"] - bst0["kernel_launches"] + sum(r.launches for r in reqs)),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out))
+    for c in clients:
+        c.close()
+
+
 def main():
     args = parse_args()
+    if args.impl == "krs" and args.workload != "sequence":
+        run_many(args, args.workload)
+        return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         world = int(os.environ.get("WORLD_SIZE", "1"))

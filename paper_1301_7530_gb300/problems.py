@@ -43,6 +43,9 @@ __all__ = [
     "elasticity_sequence_fixed",
     "elasticity_sequence_damage",
     "elasticity_inclusions",
+    "damage_parts",
+    "damage_matrix",
+    "batch_sizes",
     "sizes",
 ]
 
@@ -328,3 +331,31 @@ def elasticity_inclusions(N: int, seed_geom: int, E: float = 1.0, E_incl: float 
     """Heterogeneous cube: matrix modulus E, seeded spherical inclusions of modulus E_incl."""
     mask, _ = sphere_inclusions_mask(N, seed_geom, fraction)
     return assemble(N, np.where(mask, E_incl, E), nu)
+
+
+# ----------------------------------------------------------------------------------------
+# Many sequences (batched and served workloads)
+# ----------------------------------------------------------------------------------------
+
+def damage_parts(N: int, seed_geom: int, seed_rhs: int, E: float = 1.0, nu: float = 0.3):
+    """Damage sequence in split form.  The stiffness is linear in the element moduli, so
+    A^(k) = A_out + d_k * A_in, with A_out assembled from the elements outside the seeded
+    ellipsoid (modulus E) and A_in from those inside (modulus E); both have the full
+    27-neighbour pattern.  Returns (A_out: BSR3, vals_in: float64[nb, 3, 3], b)."""
+    mask, _, _ = ellipsoid_mask(N, seed_geom)
+    A_out = assemble(N, np.where(mask, 0.0, E), nu)
+    A_in = assemble(N, np.where(mask, E, 0.0), nu)
+    assert np.array_equal(A_out.col_idx, A_in.col_idx)
+    b = traction_rhs(N, random_traction(N, seed_rhs))
+    return A_out, A_in.vals, b
+
+
+def damage_matrix(A_out: BSR3, vals_in: np.ndarray, d: float) -> BSR3:
+    """A_out + d * A_in (host)."""
+    return BSR3(A_out.row_ptr, A_out.col_idx, A_out.vals + d * vals_in)
+
+
+def batch_sizes(n_seq: int, n_min: int, n_max: int, seed: int) -> np.ndarray:
+    """Cube sizes N ~ U{n_min, ..., n_max}, one per sequence (seeded)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.integers(n_min, n_max + 1, size=n_seq)

@@ -1,0 +1,69 @@
+"""Served solves (continuous batching over the batched engine).
+
+Each result must be the same alone and in the mix: with the group size fixed, a solve's
+arithmetic does not depend on the other solves sharing the launches, on how its
+iterations are split across launches, or on its space having been evicted to the host and
+re-imported (the damage sequence changes A at every system, so A C and C^T A C are formed
+anew either way) -- so the comparisons below are bitwise.  Accuracy against the FP64
+oracle is covered by the batched lock-step test.
+"""
+import numpy as np
+import pytest
+
+from paper_1301_7530_gb300 import binding as B
+from paper_1301_7530_gb300 import problems as P
+from paper_1301_7530_gb300 import serve as S
+
+pytestmark = pytest.mark.gpu
+
+NS = [5, 7, 4, 6, 8, 5]
+SYSTEMS = 4
+
+
+def _policy():
+    return B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, theta_frac=0.1, max_aug=40, max_iter=1000)
+
+
+def _serve(cids, arrivals, budget=8 << 30, quantum=6):
+    clients = S.make_clients(NS, SYSTEMS, 600)
+    sel = [clients[c] for c in cids]
+    for new_id, c in enumerate(sel):
+        c.cid = new_id
+    remap = {c: i for i, c in enumerate(cids)}
+    arr = [(t, remap[c], k) for t, c, k in arrivals if c in remap]
+    srv = S.Server(sel, _policy(), 1e-8, budget_bytes=budget, group_ctas=4, quantum=quantum)
+    reqs = srv.run(arr)
+    out = {(cids[r.cid], r.k): (r.x.cpu().numpy(), r.m, r.n_c, r.status, r.true_rel_res) for r in reqs}
+    info = {"evictions": srv.evictions, "reimports": srv.reimports, "steps": srv.steps, "peak": srv.peak_held}
+    srv.close()
+    for c in sel:
+        c.close()
+    return out, info
+
+
+def test_same_alone_and_in_mix_served():
+    arrivals = S.poisson_arrivals(len(NS), SYSTEMS, rate=2000.0, seed=17)
+    mix, info = _serve(list(range(len(NS))), arrivals)
+    assert len(mix) == len(NS) * SYSTEMS
+    assert info["steps"] > SYSTEMS  # solves overlapped and were split across launches
+    for (cid, k), (x, m, nc, st, res) in mix.items():
+        assert st == 0 and res <= 1e-8 * 1.0001
+    for cid in (0, 4):
+        alone, _ = _serve([cid], arrivals)
+        for k in range(SYSTEMS):
+            xa, ma, nca, sta, _ = alone[(cid, k)]
+            xm, mm, ncm, stm, _ = mix[(cid, k)]
+            assert (ma, nca, sta) == (mm, ncm, stm)
+            assert np.array_equal(xa, xm)
+
+
+def test_eviction_under_small_budget_same_results():
+    arrivals = S.poisson_arrivals(len(NS), SYSTEMS, rate=2000.0, seed=23)
+    big, info_big = _serve(list(range(len(NS))), arrivals)
+    assert info_big["evictions"] == 0
+    small, info_small = _serve(list(range(len(NS))), arrivals, budget=24 << 20)
+    assert info_small["evictions"] > 0 and info_small["reimports"] > 0
+    for key, (x, m, nc, st, _) in big.items():
+        xs, ms, ncs, sts, _ = small[key]
+        assert (m, nc, st) == (ms, ncs, sts)
+        assert np.array_equal(x, xs)
