@@ -245,25 +245,30 @@ krs_status krs_release(krs_seq_t s, int32_t what);
 typedef struct krs_batch* krs_batch_t;
 
 typedef struct {
-  int32_t group_ctas;   /* CTAs per solve; 0 = chosen by the autotuner on the first launch */
+  int32_t group_ctas;   /* CTAs per solve for every solve; 0 = per solve: its share of the
+                           SMs by estimated work, at most rows / rows_per_cta, a power of 2 */
+  int32_t rows_per_cta; /* with group_ctas = 0: fewest rows a CTA is given; 0 = chosen by
+                           the autotuner on the first launch */
   int32_t quantum;      /* iterations a solve runs per launch before the engine returns
                            control (finished solves are returned, new ones admitted);
-                           0 = every launch runs until the queue is empty */
-  int32_t reserved[6];
+                           0 = every launch runs until its queues are empty */
+  int32_t reserved[5];
 } krs_batch_config;
 
 typedef struct {
-  int32_t group_ctas, groups;  /* of the last launch */
+  int32_t group_ctas;          /* mean CTAs per group of the last launch */
+  int32_t groups, classes;     /* groups and group sizes of the last launch */
   int32_t in_flight;           /* submitted solves not yet returned */
-  int32_t last_launch_solves;  /* solves in the last launch's queue */
+  int32_t last_launch_solves;  /* solves queued in the last launch */
+  int32_t tuned_rows_per_cta;  /* autotuner's choice (0 if it did not run) */
   int64_t launches;            /* batched persistent launches so far */
   int64_t kernel_launches;     /* all kernels the engine itself launched */
   double last_kernel_ms;       /* event time of the last batched launch */
   double total_kernel_ms;
-  int32_t tuned_group_ctas;    /* autotuner's choice (0 if it did not run) */
-  int32_t tune_candidates;     /* entries of tune_g / tune_ms */
-  int32_t tune_g[8];
-  double tune_ms[8];           /* probe time of each candidate */
+  int32_t tune_candidates;     /* entries of tune_rows / tune_ms / tune_rate */
+  int32_t tune_rows[8];        /* candidate rows_per_cta */
+  double tune_ms[8];           /* probe launch time of each candidate */
+  double tune_rate[8];         /* rows x iterations per second of each candidate */
 } krs_batch_stats;
 
 /* Create an engine on dev (allocator, stream, device as for krs_create_sequence); cfg may

@@ -370,27 +370,32 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx<T> c) {
 }
 
 // Batched persistent kernel: many independent solves in one cooperative launch.  The grid
-// is cut into groups of `g` CTAs.  A group takes the next solve from a work queue, runs its
-// iterations (at most `quantum` of them) with the group's own barrier counter and partial-sum
-// buffers, and takes the next, until the queue is empty.  Solves of uneven sizes and
-// iteration counts therefore never wait for each other, and a group that finishes early
-// picks up queued work at once.  Every solve's context is prepared for a partition over g
-// CTAs, so its arithmetic (the partition and the order of every reduction) does not depend
-// on which group runs it or on which other solves share the launch.
+// is cut into groups of CTAs; groups of the same size form a class with its own work
+// queue.  A group takes the next solve from its class's queue, runs its iterations (at
+// most `quantum` of them) with the group's own barrier counter and partial-sum buffers,
+// and takes the next, until the queue is empty.  Solves of uneven sizes and iteration
+// counts therefore never wait for each other, a group that finishes early picks up queued
+// work at once, and a large solve can run on a larger group than a small one.  A solve is
+// queued only in the class whose group size its context was prepared for, so its
+// arithmetic (the partition and the order of every reduction) depends on its group size
+// only -- not on which group runs it or on which other solves share the launch.
 template <typename T>
 struct BatchArgs {
   const ApcgCtx<T>* ctxs;   // one per solve in the table
-  const int* queue;         // indices into ctxs, in the order groups should take them
-  int qlen;
-  int g;                    // CTAs per group
+  const int* queue;         // per class, indices into ctxs in the order groups take them
+  const int* qoff;          // [classes + 1] offsets of the classes' queues
+  int* heads;               // [classes] queue positions (zero at launch)
+  const int* cta_group;     // [CTAs] group of each CTA
+  const int* grp_cta0;      // [groups + 1] first CTA of each group (groups are contiguous)
+  const int* grp_class;     // [groups] class (queue) of each group
   int quantum;              // iteration limit per solve in this launch
-  int* head;                // queue position (one counter, zero at launch)
   int* mail;                // [groups * 2] solve index handed from the group's first CTA
   unsigned long long* gbar; // [groups * 16] barrier counters (one 128-byte line each)
-  double* gpart;            // [groups * g * PS_STRIDE]
-  double* gvpart;           // [groups * g * vld]
-  double* ggpart;           // [groups * g * vld]
+  double* gpart;            // [CTAs * PS_STRIDE], a group uses the rows of its CTAs
+  double* gvpart;           // [CTAs * vld]
+  double* ggpart;           // [CTAs * vld]
   int64_t vld;
+  long long spin_limit;
   int* bctrl;               // launch-wide status / abort words
 };
 
@@ -398,20 +403,23 @@ template <typename T>
 __global__ void __launch_bounds__(TPB, 1) k_apcg_batched(BatchArgs<T> B) {
   extern __shared__ double4_32a smem_raw4[];
   Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
-  const int group = blockIdx.x / B.g;
-  const int lb = blockIdx.x % B.g;
+  const int group = B.cta_group[blockIdx.x];
+  const int c0 = B.grp_cta0[group];
+  const int g = B.grp_cta0[group + 1] - c0;
+  const int lb = (int)blockIdx.x - c0;
+  const int cls = B.grp_class[group];
+  const int q0 = B.qoff[cls], qlen = B.qoff[cls + 1] - q0;
   unsigned long long* bar = B.gbar + (int64_t)group * 16;
   unsigned long long target = 0;
   __shared__ ApcgCtx<T> s_ctx;
   __shared__ int s_j0;
-  long long spin_limit = B.queue && B.qlen > 0 ? B.ctxs[B.queue[0]].spin_limit : 1;
   for (int round = 0;; round++) {
     int* box = B.mail + 2 * group + (round & 1);
     if (lb == 0 && threadIdx.x == 0) {
-      const int k = atomicAdd(B.head, 1);
-      *box = k < B.qlen ? B.queue[k] : -1;
+      const int k = atomicAdd(B.heads + cls, 1);
+      *box = k < qlen ? B.queue[q0 + k] : -1;
     }
-    if (!grid_barrier(bar, target, (unsigned)B.g, B.bctrl, spin_limit, 6)) return;
+    if (!grid_barrier(bar, target, (unsigned)g, B.bctrl, B.spin_limit, 6)) return;
     const int idx = *((volatile int*)box);
     if (idx < 0) return;
     // the solve's context lives in shared memory (the kernel-parameter copy of the
@@ -420,19 +428,18 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_batched(BatchArgs<T> B) {
     if (threadIdx.x == 0) {
       ApcgCtx<T> c = B.ctxs[idx];
       c.lb = lb;
-      c.P = B.g;
+      c.P = g;
       c.bar = bar;
       c.bctrl = B.bctrl;
-      c.part = B.gpart + (int64_t)group * B.g * PS_STRIDE;
-      c.vpart = B.gvpart + (int64_t)group * B.g * B.vld;
-      c.gpart = B.ggpart + (int64_t)group * B.g * B.vld;
+      c.part = B.gpart + (int64_t)c0 * PS_STRIDE;
+      c.vpart = B.gvpart + (int64_t)c0 * B.vld;
+      c.gpart = B.ggpart + (int64_t)c0 * B.vld;
       c.vld = B.vld;
       s_ctx = c;
       s_j0 = *((volatile int*)(c.ctrl + CTRL_J));
     }
     __syncthreads();
     const ApcgCtx<T>& c = s_ctx;
-    spin_limit = c.spin_limit;
     const int j0 = s_j0;
     if (apcg_loop(c, sm, j0, B.quantum, target) == LOOP_ABORTED) return;
   }
@@ -723,19 +730,22 @@ cudaError_t apcg_launch_batched(const BatchLaunch& L, cudaStream_t st) {
   BatchArgs<double> B;
   B.ctxs = static_cast<const ApcgCtx<double>*>(L.ctxs);
   B.queue = L.queue;
-  B.qlen = L.qlen;
-  B.g = L.g;
+  B.qoff = L.qoff;
+  B.heads = L.heads;
+  B.cta_group = L.cta_group;
+  B.grp_cta0 = L.grp_cta0;
+  B.grp_class = L.grp_class;
   B.quantum = L.quantum > 0 ? L.quantum : 0x7fffffff;
-  B.head = L.head;
   B.mail = L.mail;
   B.gbar = L.gbar;
   B.gpart = L.gpart;
   B.gvpart = L.gvpart;
   B.ggpart = L.ggpart;
   B.vld = L.vld;
+  B.spin_limit = L.spin_limit;
   B.bctrl = L.bctrl;
   void* args[] = {&B};
-  return cudaLaunchCooperativeKernel((const void*)k_apcg_batched<double>, dim3(L.g * L.groups), dim3(TPB), args,
+  return cudaLaunchCooperativeKernel((const void*)k_apcg_batched<double>, dim3(L.ctas), dim3(TPB), args,
                                      apcg_smem_bytes(L.kmax), st);
 }
 

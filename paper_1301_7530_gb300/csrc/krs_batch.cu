@@ -23,16 +23,23 @@
 // size instead of max_iter.
 //
 // Group size.  g (CTAs per solve) is the engine's tile shape: small g gives many solves
-// in flight with little barrier cost per row, large g finishes each solve sooner.  With
-// group_ctas = 0 the autotuner picks g the first time a launch is made: it runs every
-// candidate on the queued solves for a few iterations, times it with events, keeps the
-// fastest, and re-initialises the solves (the init stage recomputes every value the probe
-// iterations changed, so results do not depend on the probe).
+// in flight with little barrier cost per row, large g finishes each solve sooner.  A
+// solve's g is fixed at its first launch: with group_ctas > 0 every solve uses that size;
+// otherwise g is its fair share of the SMs by estimated work (its work / all queued work
+// x SMs, so a lone solve gets the whole device and a large solve more CTAs than a small
+// one), capped by its rows / rows_per_cta and rounded down to a power of two.  Groups of
+// one size form a class with its own queue; each launch splits the SMs among the classes
+// in proportion to their queued work (at least one group per class, at most one group
+// per queued solve).  With rows_per_cta = 0 the autotuner picks it at the first launch:
+// it runs each candidate on the queued solves for a few iterations, times the launch with
+// events, keeps the candidate with the highest rows x iterations per second, and
+// re-initialises the solves (the init stage recomputes every value the probe iterations
+// changed, so results do not depend on the probe).
 //
-// Reproducibility.  Every solve's context is built for a partition over g CTAs, so the
-// rounding of its iteration depends on g alone: a solve gives the same bits whichever
-// group runs it, whatever other solves share the launches and however its iterations are
-// split across launches.
+// Reproducibility.  Every solve's context is built for a partition over its g CTAs, so
+// the rounding of its iteration depends on g alone: it gives the same bits whichever
+// group runs it and however its iterations are split across launches; with group_ctas
+// fixed it also gives the same bits whatever other solves share the engine.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -63,10 +70,12 @@ struct Entry {
   int m = 0;
   int j = 0;           // next iteration
   double m_est = 0.0;  // expected iteration count
+  int g = 0;           // CTAs per group for this solve (0 until its first launch)
 };
 
 constexpr int kTuneIters = 8;
-const int kTuneCandidates[] = {1, 2, 4, 8, 19, 38};
+const int kTuneRows[] = {2048, 8192, 32768};
+constexpr int kMaxGroup = 128;
 
 }  // namespace
 
@@ -78,7 +87,7 @@ struct krs_batch {
   void* uctx = nullptr;
   int sms = 0;
   krs_batch_config cfg{};
-  int g = 0;  // group size in use (0 until chosen)
+  int rows_per_cta = 0;  // in use (0 until chosen)
 
   std::vector<Entry*> entries;  // submitted, not yet returned
   std::vector<int64_t> done_tags;
@@ -87,7 +96,7 @@ struct krs_batch {
   // device buffers
   void* d_ctxs = nullptr;
   int ctx_cap = 0;
-  int* d_queue = nullptr;
+  int* d_tab = nullptr;               // queue | qoff | heads | cta_group | grp_cta0 | grp_class
   int* d_gather = nullptr;
   int* d_misc = nullptr;              // head [0], bctrl [8 .. 8 + CTRL_WORDS)
   int* d_mail = nullptr;
@@ -98,7 +107,7 @@ struct krs_batch {
 
   // pinned host staging
   char* h_ctxs = nullptr;
-  int* h_queue = nullptr;
+  int* h_tab = nullptr;
   int* h_gather = nullptr;
   int h_cap = 0;
 
@@ -146,26 +155,30 @@ static krs_status b_alloc_n(krs_batch* b, T** p, size_t count) {
   return KRS_OK;
 }
 
-// table of `count` solves (contexts, queue, gathered control words)
+// ints of the launch table for `count` solves: queue, class offsets and heads, CTA ->
+// group map, group offsets and classes (classes and groups <= SMs)
+static size_t tab_ints(const krs_batch* b, int count) { return (size_t)count + 6 * (size_t)b->sms + 16; }
+
+// table of `count` solves (contexts, launch table, gathered control words)
 static krs_status ensure_table(krs_batch* b, int count) {
   if (count <= b->ctx_cap) return KRS_OK;
   int cap = b->ctx_cap ? b->ctx_cap : 64;
   while (cap < count) cap *= 2;
   b_free(b, b->d_ctxs);
-  b_free(b, b->d_queue);
+  b_free(b, b->d_tab);
   b_free(b, b->d_gather);
   b->d_ctxs = nullptr;
-  b->d_queue = b->d_gather = nullptr;
+  b->d_tab = b->d_gather = nullptr;
   KRS_TRY(b_alloc(b, apcg_ctx_bytes() * cap, &b->d_ctxs));
-  KRS_TRY(b_alloc_n(b, &b->d_queue, cap));
+  KRS_TRY(b_alloc_n(b, &b->d_tab, tab_ints(b, cap)));
   KRS_TRY(b_alloc_n(b, &b->d_gather, 4 * (size_t)cap + CTRL_WORDS));
   if (b->h_ctxs) cudaFreeHost(b->h_ctxs);
-  if (b->h_queue) cudaFreeHost(b->h_queue);
+  if (b->h_tab) cudaFreeHost(b->h_tab);
   if (b->h_gather) cudaFreeHost(b->h_gather);
   b->h_ctxs = nullptr;
-  b->h_queue = b->h_gather = nullptr;
+  b->h_tab = b->h_gather = nullptr;
   if (cudaMallocHost(&b->h_ctxs, apcg_ctx_bytes() * cap) != cudaSuccess ||
-      cudaMallocHost(&b->h_queue, sizeof(int) * cap) != cudaSuccess ||
+      cudaMallocHost(&b->h_tab, sizeof(int) * tab_ints(b, cap)) != cudaSuccess ||
       cudaMallocHost(&b->h_gather, sizeof(int) * (4 * (size_t)cap + CTRL_WORDS)) != cudaSuccess) {
     cudaGetLastError();
     return failf(KRS_ERR_OOM, "batch: pinned host allocation failed");
@@ -217,8 +230,9 @@ static int first_cap(const Entry* e) {
   return cap;
 }
 
-// iteration arguments of entry e for a partition over g CTAs (g-group launch)
-static IterArgs group_args(const Entry* e, int g, int64_t vld) {
+// iteration arguments of entry e for a partition over its g CTAs
+static IterArgs group_args(const Entry* e, int64_t vld) {
+  const int g = e->g;
   krs_seq* s = e->s;
   IterArgs a = e->ss.a;
   a.W = s->W; a.AW = s->AW; a.Z = s->Z;
@@ -239,55 +253,161 @@ static krs_status restore_stream(Entry* e) {
   return KRS_OK;
 }
 
-// Run the queued (not ended) entries for at most `quantum` iterations in one launch with
-// group size g.  Updates each entry's j / ended / status / m.  *ms: the launch's event time.
-static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int g, int quantum, float* ms) {
-  const int count = (int)run.size();
+static int pow2_floor(double v) {
+  int p = 1;
+  while (2.0 * p <= v) p *= 2;
+  return p;
+}
+
+// Group size of entries that have none yet (their first launch).
+static void assign_groups(krs_batch* b, std::vector<Entry*>& run) {
+  const int T = b->sms;
+  double W = 0.0;
+  for (Entry* e : run) W += remaining_work(e);
+  const int cap = std::min(kMaxGroup, T);
+  for (Entry* e : run) {
+    if (e->g > 0) continue;
+    if (b->cfg.group_ctas > 0) {
+      e->g = b->cfg.group_ctas;
+      continue;
+    }
+    double share = W > 0.0 ? remaining_work(e) / W * T : 1.0;
+    const double by_rows = (double)e->s->n / (double)(b->rows_per_cta > 0 ? b->rows_per_cta : 8192);
+    if (share > by_rows) share = by_rows;
+    if (share < 1.0) share = 1.0;
+    if (share > cap) share = cap;
+    e->g = pow2_floor(share);
+  }
+}
+
+// Run the not-ended entries of `run` for at most `quantum` iterations in one launch.
+// Entries of a class that gets no CTAs this time stay queued for the next launch.
+// *ms: the launch's event time; *rows_iters: sum over the solves that ran of n x the
+// iterations they did (the autotuner's work measure).
+static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int quantum, float* ms,
+                              double* rows_iters = nullptr) {
   *ms = 0.f;
-  if (count == 0) return KRS_OK;
-  const int ctas_total = b->sms;  // one CTA per SM (the kernel's register budget)
-  const int groups = ctas_total / g;
-  if (groups < 1) return failf(KRS_ERR_INVALID_ARG, "batch: group of %d CTAs exceeds the %d SMs", g, ctas_total);
+  if (rows_iters) *rows_iters = 0.0;
+  if (run.empty()) return KRS_OK;
+  const int T = b->sms;  // one CTA per SM (the kernel's register budget)
+  assign_groups(b, run);
+
+  // classes: one per group size, with their queued work
+  std::vector<int> gs;
+  for (Entry* e : run) {
+    if (e->g > T) return failf(KRS_ERR_INVALID_ARG, "batch: group of %d CTAs exceeds the %d SMs", e->g, T);
+    if (std::find(gs.begin(), gs.end(), e->g) == gs.end()) gs.push_back(e->g);
+  }
+  const int ncls = (int)gs.size();
+  std::vector<std::vector<Entry*>> members(ncls);
+  std::vector<double> work(ncls, 0.0);
+  for (Entry* e : run) {
+    const int c = (int)(std::find(gs.begin(), gs.end(), e->g) - gs.begin());
+    members[c].push_back(e);
+    work[c] += remaining_work(e);
+  }
+  // CTAs per class: one group each by decreasing work while they fit, then one more group
+  // at a time to the class with the most work per CTA (never more groups than solves)
+  std::vector<int> cls_order(ncls), groups(ncls, 0);
+  for (int c = 0; c < ncls; c++) cls_order[c] = c;
+  std::sort(cls_order.begin(), cls_order.end(), [&](int x, int y) { return work[x] > work[y]; });
+  int left = T;
+  for (int c : cls_order)
+    if (gs[c] <= left) {
+      groups[c] = 1;
+      left -= gs[c];
+    }
+  for (;;) {
+    int best = -1;
+    double best_r = 0.0;
+    for (int c = 0; c < ncls; c++) {
+      if (groups[c] == 0 || gs[c] > left || groups[c] >= (int)members[c].size()) continue;
+      const double r = work[c] / ((double)groups[c] * gs[c]);
+      if (best < 0 || r > best_r) {
+        best = c;
+        best_r = r;
+      }
+    }
+    if (best < 0) break;
+    groups[best]++;
+    left -= gs[best];
+  }
+
+  // the solves that run, class by class, each queue largest remaining work first
+  std::vector<Entry*> queued;
+  std::vector<int> qoff(1, 0), act;  // act: classes with CTAs, in table order
+  for (int c = 0; c < ncls; c++) {
+    if (groups[c] == 0) continue;
+    std::vector<Entry*> m = members[c];
+    std::stable_sort(m.begin(), m.end(), [](Entry* x, Entry* y) { return remaining_work(x) > remaining_work(y); });
+    for (Entry* e : m) queued.push_back(e);
+    qoff.push_back((int)queued.size());
+    act.push_back(c);
+  }
+  const int count = (int)queued.size();
+  const int nact = (int)act.size();
   int kmax = 1;
-  for (Entry* e : run) kmax = std::max(kmax, std::max(e->ss.nc, e->s->cap_w));
+  for (Entry* e : queued) kmax = std::max(kmax, std::max(e->ss.nc, e->s->cap_w));
   const int64_t vld = round_up(kmax + 1, 32);
   int bps = 0;
   KRS_CUDA(apcg_batched_coresident(kmax, &bps));
   if (bps < 1) return failf(KRS_ERR_CUDA, "batch: persistent kernel cannot be resident (kmax %d)", kmax);
   KRS_TRY(ensure_table(b, count));
-  KRS_TRY(ensure_groups(b, groups * g, vld));
+  KRS_TRY(ensure_groups(b, T, vld));
 
-  // contexts and queue, largest remaining work first
-  std::vector<int> order(count);
-  for (int i = 0; i < count; i++) order[i] = i;
-  std::vector<double> w(count);
-  for (int i = 0; i < count; i++) w[i] = remaining_work(run[i]);
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
+  // launch table: queue | qoff | heads | cta_group | grp_cta0 | grp_class
+  int* tq = b->h_tab;
+  int* tqoff = tq + count;
+  int* theads = tqoff + (nact + 1);
+  int* tcg = theads + nact;
+  std::vector<int> cta0(1, 0), gcls;
+  for (int a = 0; a < nact; a++) {
+    const int c = act[a];
+    for (int k = 0; k < groups[c]; k++) {
+      cta0.push_back(cta0.back() + gs[c]);
+      gcls.push_back(a);
+    }
+  }
+  const int ngroups = (int)gcls.size();
+  const int ctas = cta0.back();
+  int* tg0 = tcg + ctas;
+  int* tgc = tg0 + (ngroups + 1);
   const size_t cb = apcg_ctx_bytes();
   for (int i = 0; i < count; i++) {
-    IterArgs a = group_args(run[i], g, vld);
+    IterArgs a = group_args(queued[i], vld);
     apcg_fill_ctx(a, b->h_ctxs + cb * i);
-    b->h_queue[i] = order[i];
+    tq[i] = i;
   }
+  for (int a = 0; a <= nact; a++) tqoff[a] = qoff[a];
+  for (int a = 0; a < nact; a++) theads[a] = 0;
+  for (int gi = 0; gi < ngroups; gi++)
+    for (int t = cta0[gi]; t < cta0[gi + 1]; t++) tcg[t] = gi;
+  for (int gi = 0; gi <= ngroups; gi++) tg0[gi] = cta0[gi];
+  for (int gi = 0; gi < ngroups; gi++) tgc[gi] = gcls[gi];
+  const size_t tab_n = (size_t)(tgc + ngroups - tq);
   KRS_CUDA(cudaMemcpyAsync(b->d_ctxs, b->h_ctxs, cb * count, cudaMemcpyHostToDevice, b->stream));
-  KRS_CUDA(cudaMemcpyAsync(b->d_queue, b->h_queue, sizeof(int) * count, cudaMemcpyHostToDevice, b->stream));
+  KRS_CUDA(cudaMemcpyAsync(b->d_tab, b->h_tab, sizeof(int) * tab_n, cudaMemcpyHostToDevice, b->stream));
   KRS_CUDA(cudaMemsetAsync(b->d_misc, 0, sizeof(int) * 64, b->stream));
-  KRS_CUDA(cudaMemsetAsync(b->d_gbar, 0, sizeof(unsigned long long) * 16 * groups, b->stream));
+  KRS_CUDA(cudaMemsetAsync(b->d_gbar, 0, sizeof(unsigned long long) * 16 * ngroups, b->stream));
+  int* d = b->d_tab;
   BatchLaunch L{};
   L.ctxs = b->d_ctxs;
-  L.queue = b->d_queue;
-  L.qlen = count;
-  L.g = g;
-  L.groups = groups;
+  L.queue = d;
+  L.qoff = d + (tqoff - tq);
+  L.heads = d + (theads - tq);
+  L.cta_group = d + (tcg - tq);
+  L.grp_cta0 = d + (tg0 - tq);
+  L.grp_class = d + (tgc - tq);
+  L.ctas = ctas;
   L.quantum = quantum;
   L.kmax = kmax;
-  L.head = b->d_misc;
   L.mail = b->d_mail;
   L.gbar = b->d_gbar;
   L.gpart = b->d_gpart;
   L.gvpart = b->d_gvpart;
   L.ggpart = b->d_ggpart;
   L.vld = vld;
+  L.spin_limit = queued[0]->s->spin_limit;
   L.bctrl = b->d_misc + 8;
   KRS_CUDA(cudaEventRecord(b->e0, b->stream));
   KRS_CUDA(apcg_launch_batched(L, b->stream));
@@ -304,23 +424,27 @@ static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int g, int
   b->st.kernel_launches += 3;
   b->st.last_kernel_ms = *ms;
   b->st.total_kernel_ms += *ms;
-  b->st.group_ctas = g;
-  b->st.groups = groups;
+  b->st.group_ctas = ngroups > 0 ? ctas / ngroups : 0;
+  b->st.groups = ngroups;
+  b->st.classes = nact;
   b->st.last_launch_solves = count;
   for (int i = 0; i < count; i++) {
-    Entry* e = run[i];
+    Entry* e = queued[i];
     const int* cw = b->h_gather + 4 * i;
+    const int j_before = e->j;
     e->ss.t_iter += *ms;
     if (cw[CTRL_DONE]) {
       e->ended = true;
       e->status = cw[CTRL_STATUS];
       e->m = cw[CTRL_M];
+      if (rows_iters) *rows_iters += (double)e->s->n * (e->m - j_before);
     } else if (bctrl[CTRL_STATUS] || bctrl[CTRL_ABORT]) {
       e->ended = true;  // a group gave up waiting: the launch was abandoned
       e->status = bctrl[CTRL_STATUS] ? bctrl[CTRL_STATUS] : KRS_ERR_TIMEOUT;
       e->m = cw[CTRL_J];
     } else {
       e->j = cw[CTRL_J];
+      if (rows_iters) *rows_iters += (double)e->s->n * (e->j - j_before);
     }
   }
   return KRS_OK;
@@ -333,6 +457,7 @@ static krs_status reinit(krs_batch* b, std::vector<Entry*>& run) {
     KRS_CUDA(apcg_launch_init(e->ss.a, s->b, s->scal, b->stream, &e->ss.launches));
     KRS_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, b->stream));
     e->j = 0;
+    e->g = 0;
     e->ended = false;
     e->status = KRS_OK;
     e->m = 0;
@@ -342,31 +467,34 @@ static krs_status reinit(krs_batch* b, std::vector<Entry*>& run) {
 }
 
 static krs_status autotune(krs_batch* b, std::vector<Entry*>& run) {
-  // the probe runs every candidate on the same (solve, first iterations) items
+  // every candidate runs the same solves for their first iterations; compare rows x
+  // iterations per second (classes that get no CTAs under a candidate do no work)
   int nc = 0;
-  b->st.tune_candidates = 0;
-  float best = 0.f;
-  int best_g = 0;
-  for (int g : kTuneCandidates) {
-    if (g > b->sms) continue;
+  double best = -1.0;
+  int best_r = 0;
+  for (int r : kTuneRows) {
     if (nc > 0) KRS_TRY(reinit(b, run));
+    b->rows_per_cta = r;
     float ms = 0.f;
-    KRS_TRY(launch_once(b, run, g, kTuneIters, &ms));
+    double ri = 0.0;
+    KRS_TRY(launch_once(b, run, kTuneIters, &ms, &ri));
     for (Entry* e : run) e->ss.t_iter = 0.f;
+    const double rate = ms > 0.f ? ri / ms : 0.0;
     if (nc < 8) {
-      b->st.tune_g[nc] = g;
+      b->st.tune_rows[nc] = r;
       b->st.tune_ms[nc] = ms;
+      b->st.tune_rate[nc] = rate * 1e3;
     }
     nc++;
-    if (best_g == 0 || ms < best) {
-      best = ms;
-      best_g = g;
+    if (rate > best) {
+      best = rate;
+      best_r = r;
     }
   }
   b->st.tune_candidates = nc;
   KRS_TRY(reinit(b, run));
-  b->st.tuned_group_ctas = best_g;
-  b->g = best_g;
+  b->st.tuned_rows_per_cta = best_r;
+  b->rows_per_cta = best_r;
   return KRS_OK;
 }
 
@@ -414,7 +542,8 @@ krs_status krs_batch_create(const krs_device* dev, const krs_batch_config* cfg, 
     return failf(KRS_ERR_INVALID_ARG, "alloc and free must both be set or both be NULL");
   krs_batch_config c{};
   if (cfg) c = *cfg;
-  if (c.group_ctas < 0 || c.quantum < 0) return failf(KRS_ERR_INVALID_ARG, "group_ctas and quantum must be >= 0");
+  if (c.group_ctas < 0 || c.quantum < 0 || c.rows_per_cta < 0)
+    return failf(KRS_ERR_INVALID_ARG, "group_ctas, rows_per_cta and quantum must be >= 0");
   krs_batch* b = new (std::nothrow) krs_batch();
   if (!b) return failf(KRS_ERR_OOM, "host allocation failed");
   b->cfg = c;
@@ -439,7 +568,7 @@ krs_status krs_batch_create(const krs_device* dev, const krs_batch_config* cfg, 
     delete b;
     return failf(KRS_ERR_INVALID_ARG, "group_ctas %d exceeds the %d SMs", c.group_ctas, b->sms);
   }
-  b->g = c.group_ctas;
+  b->rows_per_cta = c.rows_per_cta;
   krs_status st = b_alloc_n(b, &b->d_misc, 64);
   if (st) return bail(st);
   if (cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess)
@@ -457,10 +586,10 @@ krs_status krs_batch_destroy(krs_batch_t b) {
     delete e;
   }
   b->entries.clear();
-  void* bufs[] = {b->d_ctxs, b->d_queue, b->d_gather, b->d_misc, b->d_mail, b->d_gbar, b->d_gpart, b->d_gvpart, b->d_ggpart};
+  void* bufs[] = {b->d_ctxs, b->d_tab, b->d_gather, b->d_misc, b->d_mail, b->d_gbar, b->d_gpart, b->d_gvpart, b->d_ggpart};
   for (void* p : bufs) b_free(b, p);
   if (b->h_ctxs) cudaFreeHost(b->h_ctxs);
-  if (b->h_queue) cudaFreeHost(b->h_queue);
+  if (b->h_tab) cudaFreeHost(b->h_tab);
   if (b->h_gather) cudaFreeHost(b->h_gather);
   if (b->e0) cudaEventDestroy(b->e0);
   if (b->e1) cudaEventDestroy(b->e1);
@@ -513,14 +642,14 @@ krs_status krs_batch_step(krs_batch_t b, int32_t max_done, int64_t* done_tags, i
   for (Entry* e : b->entries)
     if (!e->ended) run.push_back(e);
   if (!run.empty()) {
-    if (b->g == 0) {
+    if (b->cfg.group_ctas == 0 && b->rows_per_cta == 0) {
       bool fresh = true;
-      for (Entry* e : run) fresh = fresh && e->j == 0;
+      for (Entry* e : run) fresh = fresh && e->j == 0 && e->g == 0;
       if (fresh) KRS_TRY(autotune(b, run));
-      if (b->g == 0) b->g = 4;
+      if (b->rows_per_cta == 0) b->rows_per_cta = 8192;
     }
     float ms = 0.f;
-    KRS_TRY(launch_once(b, run, b->g, b->cfg.quantum, &ms));
+    KRS_TRY(launch_once(b, run, b->cfg.quantum, &ms));
     KRS_TRY(grow_full(b));
   }
   KRS_TRY(finish_ended(b));

@@ -44,19 +44,25 @@ struct IterArgs {
   unsigned long long* bar;
 };
 
-// One launch of the batched persistent kernel (FP64): groups of g CTAs take solves from
-// queue[0..qlen) (indices into the device array of contexts written by apcg_fill_ctx) and
-// run each for at most `quantum` iterations (<= 0: no limit).
+// One launch of the batched persistent kernel (FP64).  The `ctas` CTAs are cut into groups
+// (contiguous CTA ranges); the groups of one size form a class.  A group takes solves from
+// its class's queue (indices into the device array of contexts written by apcg_fill_ctx,
+// each prepared for that class's group size) and runs each for at most `quantum`
+// iterations (<= 0: no limit).  All arrays are device arrays.
 struct BatchLaunch {
   const void* ctxs;
-  const int* queue;
-  int qlen;
-  int g, groups, quantum, kmax;
-  int* head;                  // zeroed before the launch
+  const int* queue;           // concatenated class queues
+  const int* qoff;            // [classes + 1]
+  int* heads;                 // [classes], zeroed before the launch
+  const int* cta_group;       // [ctas]
+  const int* grp_cta0;        // [groups + 1]
+  const int* grp_class;       // [groups]
+  int ctas, quantum, kmax;
   int* mail;                  // [2 * groups]
   unsigned long long* gbar;   // [16 * groups], zeroed before the launch
-  double *gpart, *gvpart, *ggpart;
+  double *gpart, *gvpart, *ggpart;  // [ctas * PS_STRIDE], [ctas * vld], [ctas * vld]
   int64_t vld;
+  long long spin_limit;
   int* bctrl;                 // [CTRL_WORDS], zeroed before the launch
 };
 
