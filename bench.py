@@ -75,7 +75,7 @@ def parse_args():
     ap.add_argument("--budget-gb", type=float, default=150.0, help="served: device memory budget")
     ap.add_argument("--group-ctas", type=int, default=0, help="batched/served: CTAs per solve (0: autotune)")
     ap.add_argument("--quantum", type=int, default=None, help="batched/served: iterations per launch")
-    ap.add_argument("--rows-per-cta", type=int, default=0, help="batched/served: fewest rows per CTA (0: autotune)")
+    ap.add_argument("--group-scale", type=int, default=0, help="batched/served: group size scale in percent (0: autotune)")
     ap.add_argument("--baseline-seqs", type=int, default=None,
                     help="batched/served: sequences in the per-solve reference sample (default all)")
     return ap.parse_args()
@@ -489,7 +489,7 @@ def run_many(args, kind):
     quantum = args.quantum if args.quantum is not None else (0 if kind == "batched" else 32)
     budget = int(args.budget_gb * (1 << 30)) if kind == "served" else int(200 * (1 << 30))
     srv = S.Server(clients, pol, TOL, budget_bytes=budget, group_ctas=args.group_ctas, quantum=quantum,
-                   rows_per_cta=args.rows_per_cta)
+                   group_scale=args.group_scale)
     # warm-up: system 0 of every sequence (autotuner, allocations), then empty spaces again
     srv.run([(0.0, c.cid, 0) for c in clients], closed_loop=True, n_systems=1)
     _reset(clients)
@@ -540,7 +540,7 @@ def run_many(args, kind):
                          f"cubes N ~ U{{{min(Ns)}..{max(Ns)}}}, budget {args.budget_gb} GB"),
             "total_dofs": int(sum(c.n for c in clients)), "recycle": "srks", "ritz_eps": args.ritz_eps,
             "theta_frac": args.theta_frac, "max_aug": 100, "tol": TOL, "precond": "block_jacobi3",
-            "group_ctas": args.group_ctas or "per solve", "rows_per_cta": bst["tuned_rows_per_cta"] or args.rows_per_cta,
+            "group_ctas": args.group_ctas or "per solve", "group_scale": bst["tuned_group_scale"] or args.group_scale,
             "quantum": quantum, "autotune": bst["tune"], "l2": "inputs larger than L2 (every sequence's matrices resident)"},
         "latency_ms": {"p50": summ["p50_ms"], "p99": summ["p99_ms"], "mean": summ["mean_ms"],
                        "what": "result returned - request arrival (host clock)"},

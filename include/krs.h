@@ -245,28 +245,29 @@ krs_status krs_release(krs_seq_t s, int32_t what);
 typedef struct krs_batch* krs_batch_t;
 
 typedef struct {
-  int32_t group_ctas;   /* CTAs per solve for every solve; 0 = per solve: its share of the
-                           SMs by estimated work, at most rows / rows_per_cta, a power of 2 */
-  int32_t rows_per_cta; /* with group_ctas = 0: fewest rows a CTA is given; 0 = chosen by
+  int32_t group_ctas;   /* CTAs per solve in every launch; 0 = chosen per launch from its
+                           queue (at least SMs / solves and the largest solve's work share
+                           of the SMs, times group_scale / 100), with draining */
+  int32_t group_scale;  /* with group_ctas = 0: percent scale of that size; 0 = chosen by
                            the autotuner on the first launch */
   int32_t quantum;      /* iterations a solve runs per launch before the engine returns
                            control (finished solves are returned, new ones admitted);
-                           0 = every launch runs until its queues are empty */
+                           0 = a launch runs until its queue is empty (or it drains) */
   int32_t reserved[5];
 } krs_batch_config;
 
 typedef struct {
-  int32_t group_ctas;          /* mean CTAs per group of the last launch */
+  int32_t group_ctas;          /* CTAs per group of the last launch */
   int32_t groups, classes;     /* groups and group sizes of the last launch */
   int32_t in_flight;           /* submitted solves not yet returned */
   int32_t last_launch_solves;  /* solves queued in the last launch */
-  int32_t tuned_rows_per_cta;  /* autotuner's choice (0 if it did not run) */
+  int32_t tuned_group_scale;   /* autotuner's choice (0 if it did not run) */
   int64_t launches;            /* batched persistent launches so far */
   int64_t kernel_launches;     /* all kernels the engine itself launched */
   double last_kernel_ms;       /* event time of the last batched launch */
   double total_kernel_ms;
-  int32_t tune_candidates;     /* entries of tune_rows / tune_ms / tune_rate */
-  int32_t tune_rows[8];        /* candidate rows_per_cta */
+  int32_t tune_candidates;     /* entries of tune_scale / tune_ms / tune_rate */
+  int32_t tune_scale[8];       /* candidate group_scale */
   double tune_ms[8];           /* probe launch time of each candidate */
   double tune_rate[8];         /* rows x iterations per second of each candidate */
 } krs_batch_stats;

@@ -62,22 +62,22 @@ class krs_solve_stats(ct.Structure):
 
 
 class krs_batch_config(ct.Structure):
-    _fields_ = [("group_ctas", ct.c_int32), ("rows_per_cta", ct.c_int32), ("quantum", ct.c_int32),
+    _fields_ = [("group_ctas", ct.c_int32), ("group_scale", ct.c_int32), ("quantum", ct.c_int32),
                 ("reserved", ct.c_int32 * 5)]
 
 
 class krs_batch_stats(ct.Structure):
     _fields_ = [("group_ctas", ct.c_int32), ("groups", ct.c_int32), ("classes", ct.c_int32),
-                ("in_flight", ct.c_int32), ("last_launch_solves", ct.c_int32), ("tuned_rows_per_cta", ct.c_int32),
+                ("in_flight", ct.c_int32), ("last_launch_solves", ct.c_int32), ("tuned_group_scale", ct.c_int32),
                 ("launches", ct.c_int64), ("kernel_launches", ct.c_int64),
                 ("last_kernel_ms", ct.c_double), ("total_kernel_ms", ct.c_double),
-                ("tune_candidates", ct.c_int32), ("tune_rows", ct.c_int32 * 8), ("tune_ms", ct.c_double * 8),
+                ("tune_candidates", ct.c_int32), ("tune_scale", ct.c_int32 * 8), ("tune_ms", ct.c_double * 8),
                 ("tune_rate", ct.c_double * 8)]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("tune_rows", "tune_ms", "tune_rate")}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("tune_scale", "tune_ms", "tune_rate")}
         k = min(self.tune_candidates, 8)
-        d["tune"] = [(self.tune_rows[i], self.tune_ms[i], self.tune_rate[i]) for i in range(k)]
+        d["tune"] = [(self.tune_scale[i], self.tune_ms[i], self.tune_rate[i]) for i in range(k)]
         return d
 
 
@@ -350,14 +350,14 @@ class Batch:
     """Batched engine (krs_batch_t): solves of many sequences in one persistent launch."""
 
     def __init__(self, device: int = 0, stream=None, group_ctas: int = 0, quantum: int = 0,
-                 rows_per_cta: int = 0, torch_allocator: bool = True):
+                 group_scale: int = 0, torch_allocator: bool = True):
         import torch
         L = lib()
         self.device = int(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._alloc = TorchAllocator(self.device, self.stream) if torch_allocator else None
         self._dev = _device_struct(self.device, self.stream, self._alloc)
-        cfg = krs_batch_config(int(group_ctas), int(rows_per_cta), int(quantum))
+        cfg = krs_batch_config(int(group_ctas), int(group_scale), int(quantum))
         h = ct.c_void_p()
         check(L.krs_batch_create(ct.byref(self._dev), ct.byref(cfg), ct.byref(h)), "krs_batch_create")
         self._h = h

@@ -72,6 +72,9 @@ struct ApcgCtx {
   int64_t vld;
   int* ctrl;           // this solve's status / done / iteration words
   int* bctrl;          // status / abort words the barrier watches (== ctrl for one solve)
+  int* gstop;          // batched: the group's drain word (nullptr for one solve)
+  const int* idle;     // batched: groups that found their queue empty
+  int drain_at;        // batched: drain once this many groups are idle (0: never)
   unsigned long long* bar;
 };
 
@@ -318,12 +321,16 @@ __device__ __forceinline__ void phase7(const ApcgCtx<T>& c, int j, Smem<T>& sm) 
 // ------------------------------------------------------------------------------------
 // persistent kernel: the whole iteration loop of one solve
 // ------------------------------------------------------------------------------------
-enum LoopResult { LOOP_ENDED = 0, LOOP_SUSPENDED = 1, LOOP_ABORTED = 2 };
+enum LoopResult { LOOP_ENDED = 0, LOOP_SUSPENDED = 1, LOOP_ABORTED = 2, LOOP_DRAINED = 3 };
 
 // The iteration loop of one solve from iteration j0, run by the CTAs of one group: at most
 // `quantum` iterations, after which the solve is suspended with CTRL_J = the next iteration
 // (every value the loop carries from one iteration to the next is in global memory).
 // `target` is the CTA's running count for the group's barrier counter.
+// Drain (batched launches): at the end of each iteration the group's first CTA compares
+// the launch's idle-group count with drain_at and publishes the outcome in the group's
+// drain word before the iteration's last barrier; every CTA of the group reads that word
+// after the barrier, so all of them suspend at the same iteration.
 template <typename T>
 __device__ __forceinline__ int apcg_loop(const ApcgCtx<T>& c, Smem<T>& sm, int j0, int quantum,
                                          unsigned long long& target) {
@@ -336,6 +343,10 @@ __device__ __forceinline__ int apcg_loop(const ApcgCtx<T>& c, Smem<T>& sm, int j
     if (j - j0 >= quantum || j >= c.jcap) {
       if (c.lb == 0 && threadIdx.x == 0) c.ctrl[CTRL_J] = j;
       return LOOP_SUSPENDED;
+    }
+    if (c.gstop && *((volatile int*)c.gstop)) {
+      if (c.lb == 0 && threadIdx.x == 0) c.ctrl[CTRL_J] = j;
+      return LOOP_DRAINED;
     }
     phase1(c, j, sm);
     KRS_SYNC();
@@ -354,6 +365,8 @@ __device__ __forceinline__ int apcg_loop(const ApcgCtx<T>& c, Smem<T>& sm, int j
     if (phase6(c, j, sm) == PH_STOP) return LOOP_ENDED;
     KRS_SYNC();
     phase7(c, j, sm);
+    if (c.gstop && c.drain_at > 0 && c.lb == 0 && threadIdx.x == 0 && *((volatile const int*)c.idle) >= c.drain_at)
+      *((volatile int*)c.gstop) = 1;
     KRS_SYNC();
   }
 #undef KRS_SYNC
@@ -389,6 +402,9 @@ struct BatchArgs {
   const int* grp_cta0;      // [groups + 1] first CTA of each group (groups are contiguous)
   const int* grp_class;     // [groups] class (queue) of each group
   int quantum;              // iteration limit per solve in this launch
+  int drain_at;             // suspend every solve once this many groups are idle (0: never)
+  int* idle;                // idle-group counter (zero at launch)
+  int* gstop;               // [groups] drain words (zero at launch)
   int* mail;                // [groups * 2] solve index handed from the group's first CTA
   unsigned long long* gbar; // [groups * 16] barrier counters (one 128-byte line each)
   double* gpart;            // [CTAs * PS_STRIDE], a group uses the rows of its CTAs
@@ -418,6 +434,7 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_batched(BatchArgs<T> B) {
     if (lb == 0 && threadIdx.x == 0) {
       const int k = atomicAdd(B.heads + cls, 1);
       *box = k < qlen ? B.queue[q0 + k] : -1;
+      if (k >= qlen) atomicAdd(B.idle, 1);
     }
     if (!grid_barrier(bar, target, (unsigned)g, B.bctrl, B.spin_limit, 6)) return;
     const int idx = *((volatile int*)box);
@@ -435,13 +452,17 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_batched(BatchArgs<T> B) {
       c.vpart = B.gvpart + (int64_t)c0 * B.vld;
       c.gpart = B.ggpart + (int64_t)c0 * B.vld;
       c.vld = B.vld;
+      c.gstop = B.gstop + group;
+      c.idle = B.idle;
+      c.drain_at = B.drain_at;
       s_ctx = c;
       s_j0 = *((volatile int*)(c.ctrl + CTRL_J));
     }
     __syncthreads();
     const ApcgCtx<T>& c = s_ctx;
     const int j0 = s_j0;
-    if (apcg_loop(c, sm, j0, B.quantum, target) == LOOP_ABORTED) return;
+    const int res = apcg_loop(c, sm, j0, B.quantum, target);
+    if (res == LOOP_ABORTED || res == LOOP_DRAINED) return;
   }
 }
 
@@ -603,6 +624,9 @@ static ApcgCtx<T> make_ctx(const IterArgs& a) {
   c.tfull = a.tfull; c.sfull = a.sfull; c.gfull = a.gfull;
   c.part = a.part; c.vpart = a.vpart; c.gpart = a.gpart; c.vld = a.vld; c.ctrl = a.ctrl; c.bar = a.bar;
   c.bctrl = a.ctrl;
+  c.gstop = nullptr;
+  c.idle = nullptr;
+  c.drain_at = 0;
   return c;
 }
 
@@ -736,6 +760,9 @@ cudaError_t apcg_launch_batched(const BatchLaunch& L, cudaStream_t st) {
   B.grp_cta0 = L.grp_cta0;
   B.grp_class = L.grp_class;
   B.quantum = L.quantum > 0 ? L.quantum : 0x7fffffff;
+  B.drain_at = L.drain_at;
+  B.idle = L.idle;
+  B.gstop = L.gstop;
   B.mail = L.mail;
   B.gbar = L.gbar;
   B.gpart = L.gpart;

@@ -23,23 +23,25 @@
 // size instead of max_iter.
 //
 // Group size.  g (CTAs per solve) is the engine's tile shape: small g gives many solves
-// in flight with little barrier cost per row, large g finishes each solve sooner.  A
-// solve's g is fixed at its first launch: with group_ctas > 0 every solve uses that size;
-// otherwise g is its fair share of the SMs by estimated work (its work / all queued work
-// x SMs, so a lone solve gets the whole device and a large solve more CTAs than a small
-// one), capped by its rows / rows_per_cta and rounded down to a power of two.  Groups of
-// one size form a class with its own queue; each launch splits the SMs among the classes
-// in proportion to their queued work (at least one group per class, at most one group
-// per queued solve).  With rows_per_cta = 0 the autotuner picks it at the first launch:
-// it runs each candidate on the queued solves for a few iterations, times the launch with
-// events, keeps the candidate with the highest rows x iterations per second, and
-// re-initialises the solves (the init stage recomputes every value the probe iterations
-// changed, so results do not depend on the probe).
+// in flight with little barrier cost per row, large g finishes each solve sooner.  With
+// group_ctas > 0 every launch uses that size.  Otherwise each launch picks g from its
+// queue: at least SMs / solves (so few solves still fill the device; a lone solve gets
+// all of it) and at least the largest solve's share of the SMs by estimated work (so that
+// solve is not the launch's critical path), times group_scale / 100, then the size near
+// it that leaves the fewest SMs idle.  Such a launch also drains: once half of its groups
+// have found the queue empty, every group suspends its solve at the end of the current
+// iteration and the launch ends, so the host relaunches the remaining solves with a larger
+// g (and admits new ones) instead of leaving half the device idle.  With group_scale = 0
+// the autotuner picks the scale at the first launch: it runs each candidate on the queued
+// solves for a few iterations, times the launch with events, keeps the one with the most
+// rows x iterations per second, and re-initialises the solves (the init stage recomputes
+// every value the probe iterations changed, so results do not depend on the probe).
 //
-// Reproducibility.  Every solve's context is built for a partition over its g CTAs, so
-// the rounding of its iteration depends on g alone: it gives the same bits whichever
-// group runs it and however its iterations are split across launches; with group_ctas
-// fixed it also gives the same bits whatever other solves share the engine.
+// Reproducibility.  A launch prepares every solve's context for a partition over g CTAs,
+// and a solve's bits depend on the partitions of its launches only: with group_ctas
+// fixed, a solve gives the same bits whichever group runs it, however its iterations are
+// split across launches and whatever other solves share the engine; with an adaptive g
+// the results of a solve in different mixes agree to rounding.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -70,12 +72,11 @@ struct Entry {
   int m = 0;
   int j = 0;           // next iteration
   double m_est = 0.0;  // expected iteration count
-  int g = 0;           // CTAs per group for this solve (0 until its first launch)
+  int g = 0;           // CTAs per group in the current launch
 };
 
 constexpr int kTuneIters = 8;
-const int kTuneRows[] = {2048, 8192, 32768};
-constexpr int kMaxGroup = 128;
+const int kTuneScale[] = {50, 100, 200};
 
 }  // namespace
 
@@ -87,7 +88,7 @@ struct krs_batch {
   void* uctx = nullptr;
   int sms = 0;
   krs_batch_config cfg{};
-  int rows_per_cta = 0;  // in use (0 until chosen)
+  int scale = 0;  // group_scale in use (0 until chosen)
 
   std::vector<Entry*> entries;  // submitted, not yet returned
   std::vector<int64_t> done_tags;
@@ -98,7 +99,7 @@ struct krs_batch {
   int ctx_cap = 0;
   int* d_tab = nullptr;               // queue | qoff | heads | cta_group | grp_cta0 | grp_class
   int* d_gather = nullptr;
-  int* d_misc = nullptr;              // head [0], bctrl [8 .. 8 + CTRL_WORDS)
+  int* d_misc = nullptr;              // idle [1], bctrl [8 .. 8 + CTRL_WORDS), drain words [64 .. 64 + SMs)
   int* d_mail = nullptr;
   unsigned long long* d_gbar = nullptr;
   double *d_gpart = nullptr, *d_gvpart = nullptr, *d_ggpart = nullptr;
@@ -253,35 +254,35 @@ static krs_status restore_stream(Entry* e) {
   return KRS_OK;
 }
 
-static int pow2_floor(double v) {
-  int p = 1;
-  while (2.0 * p <= v) p *= 2;
-  return p;
-}
-
-// Group size of entries that have none yet (their first launch).
-static void assign_groups(krs_batch* b, std::vector<Entry*>& run) {
+// Group size of a launch over `run` (see the file comment).
+static int choose_group(const krs_batch* b, const std::vector<Entry*>& run) {
   const int T = b->sms;
-  double W = 0.0;
-  for (Entry* e : run) W += remaining_work(e);
-  const int cap = std::min(kMaxGroup, T);
+  if (b->cfg.group_ctas > 0) return b->cfg.group_ctas;
+  double W = 0.0, wmax = 0.0;
   for (Entry* e : run) {
-    if (e->g > 0) continue;
-    if (b->cfg.group_ctas > 0) {
-      e->g = b->cfg.group_ctas;
-      continue;
-    }
-    double share = W > 0.0 ? remaining_work(e) / W * T : 1.0;
-    const double by_rows = (double)e->s->n / (double)(b->rows_per_cta > 0 ? b->rows_per_cta : 8192);
-    if (share > by_rows) share = by_rows;
-    if (share < 1.0) share = 1.0;
-    if (share > cap) share = cap;
-    e->g = pow2_floor(share);
+    const double w = remaining_work(e);
+    W += w;
+    wmax = std::max(wmax, w);
   }
+  double g = std::max((double)T / (double)run.size(), W > 0.0 ? wmax / W * T : 1.0);
+  g *= (b->scale > 0 ? b->scale : 100) / 100.0;
+  if (g < 1.0) g = 1.0;
+  if (g > T) g = T;
+  // among sizes within 15% of g, the one that leaves the fewest SMs idle
+  int best = std::max(1, (int)(g + 0.5));
+  int best_used = (T / best) * best;
+  for (int c = std::max(1, (int)(0.85 * g)); c <= std::min(T, (int)(1.15 * g) + 1); c++) {
+    const int used = (T / c) * c;
+    if (used > best_used) {
+      best = c;
+      best_used = used;
+    }
+  }
+  return best;
 }
 
-// Run the not-ended entries of `run` for at most `quantum` iterations in one launch.
-// Entries of a class that gets no CTAs this time stay queued for the next launch.
+// Run the not-ended entries of `run` for at most `quantum` iterations in one launch (or
+// until the launch drains).
 // *ms: the launch's event time; *rows_iters: sum over the solves that ran of n x the
 // iterations they did (the autotuner's work measure).
 static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int quantum, float* ms,
@@ -290,60 +291,16 @@ static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int quantu
   if (rows_iters) *rows_iters = 0.0;
   if (run.empty()) return KRS_OK;
   const int T = b->sms;  // one CTA per SM (the kernel's register budget)
-  assign_groups(b, run);
-
-  // classes: one per group size, with their queued work
-  std::vector<int> gs;
-  for (Entry* e : run) {
-    if (e->g > T) return failf(KRS_ERR_INVALID_ARG, "batch: group of %d CTAs exceeds the %d SMs", e->g, T);
-    if (std::find(gs.begin(), gs.end(), e->g) == gs.end()) gs.push_back(e->g);
-  }
-  const int ncls = (int)gs.size();
-  std::vector<std::vector<Entry*>> members(ncls);
-  std::vector<double> work(ncls, 0.0);
-  for (Entry* e : run) {
-    const int c = (int)(std::find(gs.begin(), gs.end(), e->g) - gs.begin());
-    members[c].push_back(e);
-    work[c] += remaining_work(e);
-  }
-  // CTAs per class: one group each by decreasing work while they fit, then one more group
-  // at a time to the class with the most work per CTA (never more groups than solves)
-  std::vector<int> cls_order(ncls), groups(ncls, 0);
-  for (int c = 0; c < ncls; c++) cls_order[c] = c;
-  std::sort(cls_order.begin(), cls_order.end(), [&](int x, int y) { return work[x] > work[y]; });
-  int left = T;
-  for (int c : cls_order)
-    if (gs[c] <= left) {
-      groups[c] = 1;
-      left -= gs[c];
-    }
-  for (;;) {
-    int best = -1;
-    double best_r = 0.0;
-    for (int c = 0; c < ncls; c++) {
-      if (groups[c] == 0 || gs[c] > left || groups[c] >= (int)members[c].size()) continue;
-      const double r = work[c] / ((double)groups[c] * gs[c]);
-      if (best < 0 || r > best_r) {
-        best = c;
-        best_r = r;
-      }
-    }
-    if (best < 0) break;
-    groups[best]++;
-    left -= gs[best];
-  }
-
-  // the solves that run, class by class, each queue largest remaining work first
-  std::vector<Entry*> queued;
-  std::vector<int> qoff(1, 0), act;  // act: classes with CTAs, in table order
-  for (int c = 0; c < ncls; c++) {
-    if (groups[c] == 0) continue;
-    std::vector<Entry*> m = members[c];
-    std::stable_sort(m.begin(), m.end(), [](Entry* x, Entry* y) { return remaining_work(x) > remaining_work(y); });
-    for (Entry* e : m) queued.push_back(e);
-    qoff.push_back((int)queued.size());
-    act.push_back(c);
-  }
+  const int g = choose_group(b, run);
+  if (g > T) return failf(KRS_ERR_INVALID_ARG, "batch: group of %d CTAs exceeds the %d SMs", g, T);
+  const int ngroups_all = T / g;
+  // one class: every solve, largest remaining work first
+  std::vector<Entry*> queued = run;
+  std::stable_sort(queued.begin(), queued.end(), [](Entry* x, Entry* y) { return remaining_work(x) > remaining_work(y); });
+  for (Entry* e : queued) e->g = g;
+  std::vector<int> qoff = {0, (int)queued.size()}, act = {0};
+  std::vector<int> gs = {g}, groups = {std::min(ngroups_all, (int)queued.size())};
+  const int drain_at = (b->cfg.group_ctas > 0 || groups[0] < 2) ? 0 : (groups[0] + 1) / 2;
   const int count = (int)queued.size();
   const int nact = (int)act.size();
   int kmax = 1;
@@ -387,7 +344,7 @@ static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int quantu
   const size_t tab_n = (size_t)(tgc + ngroups - tq);
   KRS_CUDA(cudaMemcpyAsync(b->d_ctxs, b->h_ctxs, cb * count, cudaMemcpyHostToDevice, b->stream));
   KRS_CUDA(cudaMemcpyAsync(b->d_tab, b->h_tab, sizeof(int) * tab_n, cudaMemcpyHostToDevice, b->stream));
-  KRS_CUDA(cudaMemsetAsync(b->d_misc, 0, sizeof(int) * 64, b->stream));
+  KRS_CUDA(cudaMemsetAsync(b->d_misc, 0, sizeof(int) * (64 + (size_t)T), b->stream));
   KRS_CUDA(cudaMemsetAsync(b->d_gbar, 0, sizeof(unsigned long long) * 16 * ngroups, b->stream));
   int* d = b->d_tab;
   BatchLaunch L{};
@@ -401,6 +358,9 @@ static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int quantu
   L.ctas = ctas;
   L.quantum = quantum;
   L.kmax = kmax;
+  L.drain_at = drain_at;
+  L.idle = b->d_misc + 1;
+  L.gstop = b->d_misc + 64;
   L.mail = b->d_mail;
   L.gbar = b->d_gbar;
   L.gpart = b->d_gpart;
@@ -468,20 +428,20 @@ static krs_status reinit(krs_batch* b, std::vector<Entry*>& run) {
 
 static krs_status autotune(krs_batch* b, std::vector<Entry*>& run) {
   // every candidate runs the same solves for their first iterations; compare rows x
-  // iterations per second (classes that get no CTAs under a candidate do no work)
+  // iterations per second
   int nc = 0;
   double best = -1.0;
   int best_r = 0;
-  for (int r : kTuneRows) {
+  for (int r : kTuneScale) {
     if (nc > 0) KRS_TRY(reinit(b, run));
-    b->rows_per_cta = r;
+    b->scale = r;
     float ms = 0.f;
     double ri = 0.0;
     KRS_TRY(launch_once(b, run, kTuneIters, &ms, &ri));
     for (Entry* e : run) e->ss.t_iter = 0.f;
     const double rate = ms > 0.f ? ri / ms : 0.0;
     if (nc < 8) {
-      b->st.tune_rows[nc] = r;
+      b->st.tune_scale[nc] = r;
       b->st.tune_ms[nc] = ms;
       b->st.tune_rate[nc] = rate * 1e3;
     }
@@ -493,8 +453,8 @@ static krs_status autotune(krs_batch* b, std::vector<Entry*>& run) {
   }
   b->st.tune_candidates = nc;
   KRS_TRY(reinit(b, run));
-  b->st.tuned_rows_per_cta = best_r;
-  b->rows_per_cta = best_r;
+  b->st.tuned_group_scale = best_r;
+  b->scale = best_r;
   return KRS_OK;
 }
 
@@ -542,8 +502,8 @@ krs_status krs_batch_create(const krs_device* dev, const krs_batch_config* cfg, 
     return failf(KRS_ERR_INVALID_ARG, "alloc and free must both be set or both be NULL");
   krs_batch_config c{};
   if (cfg) c = *cfg;
-  if (c.group_ctas < 0 || c.quantum < 0 || c.rows_per_cta < 0)
-    return failf(KRS_ERR_INVALID_ARG, "group_ctas, rows_per_cta and quantum must be >= 0");
+  if (c.group_ctas < 0 || c.quantum < 0 || c.group_scale < 0)
+    return failf(KRS_ERR_INVALID_ARG, "group_ctas, group_scale and quantum must be >= 0");
   krs_batch* b = new (std::nothrow) krs_batch();
   if (!b) return failf(KRS_ERR_OOM, "host allocation failed");
   b->cfg = c;
@@ -568,8 +528,8 @@ krs_status krs_batch_create(const krs_device* dev, const krs_batch_config* cfg, 
     delete b;
     return failf(KRS_ERR_INVALID_ARG, "group_ctas %d exceeds the %d SMs", c.group_ctas, b->sms);
   }
-  b->rows_per_cta = c.rows_per_cta;
-  krs_status st = b_alloc_n(b, &b->d_misc, 64);
+  b->scale = c.group_scale;
+  krs_status st = b_alloc_n(b, &b->d_misc, 64 + (size_t)b->sms);
   if (st) return bail(st);
   if (cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess)
     return bail(failf(KRS_ERR_CUDA, "cudaEventCreate failed"));
@@ -642,11 +602,11 @@ krs_status krs_batch_step(krs_batch_t b, int32_t max_done, int64_t* done_tags, i
   for (Entry* e : b->entries)
     if (!e->ended) run.push_back(e);
   if (!run.empty()) {
-    if (b->cfg.group_ctas == 0 && b->rows_per_cta == 0) {
+    if (b->cfg.group_ctas == 0 && b->scale == 0) {
       bool fresh = true;
       for (Entry* e : run) fresh = fresh && e->j == 0 && e->g == 0;
       if (fresh) KRS_TRY(autotune(b, run));
-      if (b->rows_per_cta == 0) b->rows_per_cta = 8192;
+      if (b->scale == 0) b->scale = 100;
     }
     float ms = 0.f;
     KRS_TRY(launch_once(b, run, b->cfg.quantum, &ms));

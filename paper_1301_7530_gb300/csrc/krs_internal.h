@@ -58,6 +58,9 @@ struct BatchLaunch {
   const int* grp_cta0;        // [groups + 1]
   const int* grp_class;       // [groups]
   int ctas, quantum, kmax;
+  int drain_at;               // suspend every solve once this many groups are idle (0: never)
+  int* idle;                  // idle-group counter, zeroed before the launch
+  int* gstop;                 // [groups] drain words, zeroed before the launch
   int* mail;                  // [2 * groups]
   unsigned long long* gbar;   // [16 * groups], zeroed before the launch
   double *gpart, *gvpart, *ggpart;  // [ctas * PS_STRIDE], [ctas * vld], [ctas * vld]

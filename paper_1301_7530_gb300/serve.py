@@ -83,13 +83,13 @@ def _round_up(v, m):
 
 class Server:
     def __init__(self, clients, policy, tol=1e-8, budget_bytes=150 << 30, group_ctas=0, quantum=32,
-                 release_scratch=True, device=0, rows_per_cta=0):
+                 release_scratch=True, device=0, group_scale=0):
         self.clients = clients
         self.policy = policy
         self.tol = float(tol)
         self.budget = int(budget_bytes)
         self.release_scratch = release_scratch
-        self.engine = B.Batch(device=device, group_ctas=group_ctas, quantum=quantum, rows_per_cta=rows_per_cta)
+        self.engine = B.Batch(device=device, group_ctas=group_ctas, quantum=quantum, group_scale=group_scale)
         self.evictions = 0
         self.reimports = 0
         self.steps = 0

@@ -50,18 +50,18 @@ def test_batch_lockstep_vs_oracle(gpu_lib):
             check_pair(mats[k], b, 1e-8, pol, x, st, xo, so, C)
             assert st["true_rel_res"] <= 2e-8
     bst = eng.stats()
-    assert bst["tuned_rows_per_cta"] in [r for r, _, _ in bst["tune"]]
+    assert bst["tuned_group_scale"] in [r for r, _, _ in bst["tune"]]
     assert bst["in_flight"] == 0 and bst["launches"] >= 3
 
 
-def _run_engine(probs, idx, g, quantum, pol, systems, warm_tol=None, rows_per_cta=0):
+def _run_engine(probs, idx, g, quantum, pol, systems, warm_tol=None, group_scale=0):
     """Solve `systems` systems of the sequences probs[idx] in one engine; returns the
     per-sequence list of (x, m, n_c_after, C)."""
     seqs = {i: B.Sequence(_n(probs[i][0])) for i in idx}
     if warm_tol is not None:  # a short first solve makes the storage estimate small
         for i in idx:
             seqs[i].solve(probs[i][2][0], probs[i][1], warm_tol, B.make_policy("none", "block_jacobi3"), version=99)
-    eng = B.Batch(group_ctas=g, quantum=quantum, rows_per_cta=rows_per_cta)
+    eng = B.Batch(group_ctas=g, quantum=quantum, group_scale=group_scale)
     res = {i: [] for i in idx}
     for k in range(systems):
         xs, sts = eng.solve([seqs[i] for i in idx], [probs[i][2][k] for i in idx], [probs[i][1] for i in idx],
@@ -101,15 +101,15 @@ def test_quantum_and_storage_growth_bitwise(gpu_lib):
 
 
 def test_autotuned_equals_fixed_choice(gpu_lib):
-    """The autotuner's probe iterations leave no trace: an engine that tuned rows_per_cta
-    gives the bits of an engine created with that value (same submissions, so the same
-    group sizes)."""
+    """The autotuner's probe iterations leave no trace: an engine that tuned its group
+    scale gives the bits of an engine created with that scale (same submissions, so the
+    same group size in every launch)."""
     probs = _damage_set([5, 7, 4, 6], 2, seed0=110)
     pol = B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, theta_frac=0.1, max_aug=60)
     tuned, eng = _run_engine(probs, [0, 1, 2, 3], 0, 0, pol, 2)
-    r = eng.stats()["tuned_rows_per_cta"]
+    r = eng.stats()["tuned_group_scale"]
     assert r > 0
-    fixed, _ = _run_engine(probs, [0, 1, 2, 3], 0, 0, pol, 2, rows_per_cta=r)
+    fixed, _ = _run_engine(probs, [0, 1, 2, 3], 0, 0, pol, 2, group_scale=r)
     for i in range(4):
         for (xa, ma, *_), (xb, mb, *_) in zip(tuned[i], fixed[i]):
             assert ma == mb and np.array_equal(xa, xb)
