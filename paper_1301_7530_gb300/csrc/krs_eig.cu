@@ -2,8 +2,8 @@
 //   * H_m = tridiag(eta_{j-1}, delta_j, eta_j) from the CG coefficients (Section 4.1):
 //     beta~_j = rho_{j+1}/rho_j, delta_0 = 1/alpha_0,
 //     delta_j = 1/alpha_j + beta~_{j-1}/alpha_{j-1}, eta_j = sqrt(beta~_j)/alpha_j;
-//   * its eigenvalues and those of H_{m-1} by bisection on Sturm counts (a warp per
-//     eigenvalue; each round the 32 lanes test 32 points, so an interval shrinks 33x);
+//   * its eigenvalues and those of H_{m-1} by multisection on Sturm counts (a group of
+//     L lanes per eigenvalue tests L points per round, so an interval shrinks (L+1)x);
 //   * the stagnation selection of Eq. 16 (union of both tests), the optional
 //     theta < theta_frac * theta_max filter, ascending-theta order, the cap;
 //   * eigenvectors of the selected values by inverse iteration (a lane per vector,
@@ -57,14 +57,17 @@ __device__ __forceinline__ int sturm_count(int m, const double* d, const double*
   return cnt;
 }
 
-// One CTA per group of 8 eigenvalues (8 warps).  Job index g in [0, m + m1): g < m is
-// eigenvalue g (descending) of T_m, else eigenvalue g - m of T_{m1} (leading block).
-// Output: theta_m[m], theta_m1[m1], descending.
-constexpr int EIG_WARPS = 8;
-
-__global__ void __launch_bounds__(EIG_WARPS * 32) k_bisect(int m, int m1, const double* __restrict__ delta,
-                                                           const double* __restrict__ eta, double* theta_m,
-                                                           double* theta_m1) {
+// Multisection over lane groups.  Each eigenvalue (a "job") gets a group of L lanes of a
+// one-warp CTA (L a power of two); every round the L lanes evaluate Sturm counts at L
+// interior points of the job's interval, which shrinks (L + 1)-fold.  GB300's FP64 pipe
+// costs the same per warp instruction whatever the number of active lanes, so the cost
+// of a job is rounds x m, and the number of jobs per warp is 32 / L: the launcher picks L
+// so that the warps about fill the SMs (one warp per SM keeps the FP64 pipe of every SM
+// busy without contention, and a Sturm count is a dependent chain).
+// Job index q in [0, m + m1): q < m is eigenvalue q (descending) of T_m, else eigenvalue
+// q - m of T_{m1} (leading block).  Output: theta_m[m], theta_m1[m1], descending.
+__global__ void __launch_bounds__(32) k_bisect(int m, int m1, int L, const double* __restrict__ delta,
+                                               const double* __restrict__ eta, double* theta_m, double* theta_m1) {
   extern __shared__ double sh[];
   double* d = sh;
   double* e2 = sh + m;
@@ -73,11 +76,13 @@ __global__ void __launch_bounds__(EIG_WARPS * 32) k_bisect(int m, int m1, const 
     if (i < m - 1) e2[i] = eta[i] * eta[i];
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int job = blockIdx.x * EIG_WARPS + warp;
-  if (job >= m + m1) return;
-  const int order = (job < m) ? m : m1;
-  const int idx_desc = (job < m) ? job : job - m;
+  const int lane = threadIdx.x & 31;
+  const int per_warp = 32 / L;
+  const int grp = lane / L, sub = lane % L;
+  const int job = blockIdx.x * per_warp + grp;
+  const bool active = job < m + m1;
+  const int order = !active ? m : (job < m ? m : m1);
+  const int idx_desc = !active ? 0 : (job < m ? job : job - m);
   const int k = order - 1 - idx_desc;  // ascending index
   // Gershgorin interval of the order-`order` leading block
   double lo = d[0], hi = d[0], emax = 0.0;
@@ -92,23 +97,30 @@ __global__ void __launch_bounds__(EIG_WARPS * 32) k_bisect(int m, int m1, const 
   const double pivmin = DBL_MIN * fmax(1.0, emax);
   lo -= 2.0 * DBL_EPSILON * tnorm + pivmin;
   hi += 2.0 * DBL_EPSILON * tnorm + pivmin;
+  const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (grp * L));
+  bool done = !active;
   // invariant: count(lo) <= k < count(hi)
-  for (int round = 0; round < 40; round++) {
-    const double width = hi - lo;
-    if (width <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
-    const double x = lo + width * ((double)(lane + 1) / 33.0);
-    const int c = sturm_count(order, d, e2, x, pivmin);
-    const unsigned above = __ballot_sync(0xffffffffu, c > k);
-    const int L = above ? (__ffs(above) - 1) : 32;
-    const double xL = __shfl_sync(0xffffffffu, x, L & 31);
-    const double xLm = __shfl_sync(0xffffffffu, x, (L - 1) & 31);
-    const double nhi = (L < 32) ? xL : hi;
-    const double nlo = (L > 0) ? xLm : lo;
-    if (nhi == hi && nlo == lo) break;  // no representable progress
-    lo = nlo;
-    hi = nhi;
+  for (int round = 0; round < 400; round++) {
+    if (!done) {
+      const double width = hi - lo;
+      if (width <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) done = true;
+    }
+    if (!__any_sync(0xffffffffu, !done)) break;
+    const double x = lo + (hi - lo) * ((double)(sub + 1) / (double)(L + 1));
+    const int c = done ? 0 : sturm_count(order, d, e2, x, pivmin);
+    const unsigned above = __ballot_sync(0xffffffffu, !done && c > k) & gmask;
+    const int first = above ? (__ffs(above) - 1) - grp * L : L;  // first point above, in the group
+    const double xF = __shfl_sync(0xffffffffu, x, grp * L + (first < L ? first : 0));
+    const double xFm = __shfl_sync(0xffffffffu, x, grp * L + (first > 0 ? first - 1 : 0));
+    if (!done) {
+      const double nhi = (first < L) ? xF : hi;
+      const double nlo = (first > 0) ? xFm : lo;
+      if (nhi == hi && nlo == lo) done = true;  // no representable progress
+      lo = nlo;
+      hi = nhi;
+    }
   }
-  if (lane == 0) {
+  if (active && sub == 0) {
     const double v = 0.5 * (lo + hi);
     if (job < m) theta_m[idx_desc] = v;
     else theta_m1[idx_desc] = v;
@@ -119,12 +131,18 @@ cudaError_t launch_tridiag_eigvals2(int m, int m1, const double* delta, const do
                                     double* theta_m1, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   const int jobs = m + m1;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // lanes per job: the largest power of two whose warps (32 / L jobs each) still fit the SMs
+  int L = 32;
+  while (L > 1 && (int64_t)jobs * L > 32 * (int64_t)sms) L >>= 1;
+  const int per_warp = 32 / L;
   const size_t sm = sizeof(double) * (size_t)(2 * m + 1);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute((const void*)k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  k_bisect<<<(jobs + EIG_WARPS - 1) / EIG_WARPS, EIG_WARPS * 32, sm, st>>>(m, m1, delta, eta, theta_m, theta_m1);
+  k_bisect<<<(jobs + per_warp - 1) / per_warp, 32, sm, st>>>(m, m1, L, delta, eta, theta_m, theta_m1);
   return cudaGetLastError();
 }
 

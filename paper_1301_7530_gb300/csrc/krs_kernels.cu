@@ -157,10 +157,13 @@ cudaError_t launch_spmm(int nbr, const int* rp, const int* ci, const double* val
 // ------------------------------------------------------------------------------------
 constexpr int GT = 32;          // tile edge
 constexpr int GROWS = 32;       // rows staged per step
-constexpr int GSPLIT_ROWS = 8192;
+constexpr int GSPLIT_ROWS = 8192;   // most rows per split
+constexpr int GSPLIT_MIN = 512;     // fewest rows per split
+constexpr int GTARGET_CTAS = 304;   // splits are added until the grid has about this many CTAs
 
 struct GramGeom {
   int ntile, qt0, ntiles_pairs, nsplit;
+  int64_t rows;  // rows per split (a multiple of GROWS)
 };
 
 __host__ __device__ inline GramGeom gram_geom(int64_t n, int nc, int q0) {
@@ -171,8 +174,15 @@ __host__ __device__ inline GramGeom gram_geom(int64_t n, int nc, int q0) {
   int cnt = 0;
   for (int qt = g.qt0; qt < g.ntile; qt++) cnt += qt + 1;
   g.ntiles_pairs = cnt;
-  g.nsplit = (int)((n + GSPLIT_ROWS - 1) / GSPLIT_ROWS);
-  if (g.nsplit < 1) g.nsplit = 1;
+  // enough splits to fill the device (two CTAs per SM) when there are few tiles, each
+  // split a multiple of GROWS rows
+  int64_t nsplit = (n + GSPLIT_ROWS - 1) / GSPLIT_ROWS;
+  const int64_t want = (GTARGET_CTAS + cnt - 1) / (cnt > 0 ? cnt : 1);
+  const int64_t most = (n + GSPLIT_MIN - 1) / GSPLIT_MIN;
+  if (nsplit < want) nsplit = want < most ? want : most;
+  if (nsplit < 1) nsplit = 1;
+  g.nsplit = (int)nsplit;
+  g.rows = ((n + nsplit - 1) / nsplit + GROWS - 1) / GROWS * GROWS;
   return g;
 }
 
@@ -192,15 +202,18 @@ __device__ __forceinline__ void pair_of(int idx, int qt0, int& pt, int& qt) {
 
 __global__ void __launch_bounds__(256) k_gram_part(int64_t n, const double* __restrict__ C,
                                                    const double* __restrict__ AC, int64_t ld, int nc,
-                                                   int qt0, double* __restrict__ scratch) {
+                                                   int qt0, int64_t rows, double* __restrict__ scratch) {
   __shared__ double sa[GROWS][GT + 1];
   __shared__ double sb[GROWS][GT + 1];
   int pt, qt;
   pair_of(blockIdx.x, qt0, pt, qt);
   const int split = blockIdx.y;
-  const int64_t ra = (int64_t)split * GSPLIT_ROWS;
-  const int64_t rb = kmin64(n, ra + GSPLIT_ROWS);
+  const int64_t ra = (int64_t)split * rows;
+  const int64_t rb = kmin64(n, ra + rows);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2 x 2 each
+  // a thread whose 2 x 2 patch lies past column nc - 1 of either tile does no arithmetic
+  // (tiles at the edge of a small n_c are mostly padding)
+  const bool live = (pt * GT + 2 * ty < nc) && (qt * GT + 2 * tx < nc);
   double acc00 = 0.0, acc01 = 0.0, acc10 = 0.0, acc11 = 0.0;
   for (int64_t r = ra; r < rb; r += GROWS) {
     // stage C[r:r+32, pt*32 : pt*32+32] and AC[r:r+32, qt*32 : ...]
@@ -212,14 +225,16 @@ __global__ void __launch_bounds__(256) k_gram_part(int64_t n, const double* __re
       sb[rr][col] = (row < rb && cq < nc) ? AC[(int64_t)cq * ld + row] : 0.0;
     }
     __syncthreads();
+    if (live) {
 #pragma unroll 8
-    for (int rr = 0; rr < GROWS; rr++) {
-      const double a0 = sa[rr][2 * ty], a1 = sa[rr][2 * ty + 1];
-      const double b0 = sb[rr][2 * tx], b1 = sb[rr][2 * tx + 1];
-      acc00 += a0 * b0;
-      acc01 += a0 * b1;
-      acc10 += a1 * b0;
-      acc11 += a1 * b1;
+      for (int rr = 0; rr < GROWS; rr++) {
+        const double a0 = sa[rr][2 * ty], a1 = sa[rr][2 * ty + 1];
+        const double b0 = sb[rr][2 * tx], b1 = sb[rr][2 * tx + 1];
+        acc00 += a0 * b0;
+        acc01 += a0 * b1;
+        acc10 += a1 * b0;
+        acc11 += a1 * b1;
+      }
     }
     __syncthreads();
   }
@@ -250,7 +265,7 @@ cudaError_t launch_gram(int64_t n, const double* C, const double* AC, int64_t ld
   if (nc <= 0 || q0 >= nc) return cudaSuccess;
   GramGeom g = gram_geom(n, nc, q0);
   if ((size_t)g.ntiles_pairs * g.nsplit * GT * GT > scratch_doubles) return cudaErrorInvalidValue;
-  k_gram_part<<<dim3(g.ntiles_pairs, g.nsplit), 256, 0, st>>>(n, C, AC, ld, nc, g.qt0, scratch);
+  k_gram_part<<<dim3(g.ntiles_pairs, g.nsplit), 256, 0, st>>>(n, C, AC, ld, nc, g.qt0, g.rows, scratch);
   k_gram_reduce<<<g.ntiles_pairs, 256, 0, st>>>(nc, g.qt0, g.nsplit, scratch, G, ldg);
   return cudaGetLastError();
 }
