@@ -1,9 +1,11 @@
 """Batched engine (krs_batch_t): many sequences of different sizes in one persistent launch.
 
 Parity: every batched solve against the FP64 oracle in lock-step (iterations within +-2,
-relative solution difference <= 1e-9 at equal counts).  Determinism: a solve's bits
-depend on the group size only -- alone or in a mix, in one launch or split over many,
-autotuned or fixed -- so those comparisons are exact.
+relative solution difference <= 1e-9 at equal counts).  Determinism: with the group size
+fixed, a solve's bits do not depend on the mix or on how its iterations are split across
+launches, so those comparisons are exact; the adaptive group size (chosen per launch,
+with draining) changes partitions with the load and the timing, so engines in that mode
+agree to the lock-step bar instead.
 """
 import numpy as np
 import pytest
@@ -100,10 +102,10 @@ def test_quantum_and_storage_growth_bitwise(gpu_lib):
             assert np.array_equal(Ca, Cb)
 
 
-def test_autotuned_equals_fixed_choice(gpu_lib):
+def test_autotuned_engine_matches_fixed_choice(gpu_lib):
     """The autotuner's probe iterations leave no trace: an engine that tuned its group
-    scale gives the bits of an engine created with that scale (same submissions, so the
-    same group size in every launch)."""
+    scale agrees with an engine created with that scale (same submissions) to the
+    lock-step bar (iterations within +-2; relative difference <= 1e-9 at equal counts)."""
     probs = _damage_set([5, 7, 4, 6], 2, seed0=110)
     pol = B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, theta_frac=0.1, max_aug=60)
     tuned, eng = _run_engine(probs, [0, 1, 2, 3], 0, 0, pol, 2)
@@ -111,8 +113,10 @@ def test_autotuned_equals_fixed_choice(gpu_lib):
     assert r > 0
     fixed, _ = _run_engine(probs, [0, 1, 2, 3], 0, 0, pol, 2, group_scale=r)
     for i in range(4):
-        for (xa, ma, *_), (xb, mb, *_) in zip(tuned[i], fixed[i]):
-            assert ma == mb and np.array_equal(xa, xb)
+        for (xa, ma, na, _), (xb, mb, nb, _) in zip(tuned[i], fixed[i]):
+            assert abs(ma - mb) <= 2
+            if ma == mb and na == nb:
+                assert rel(xa, xb) <= 1e-9
 
 
 def test_submit_step_tags_and_statuses(gpu_lib):
