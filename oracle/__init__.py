@@ -11,6 +11,9 @@ Parity status of each function (what pins it; the pins live under tests/):
   lanczos                  -- V^T A V = H_m with V built from the solve's Z (any size)
   sym_eig / tridiag_eig    -- numpy.linalg.eigh (library reference), orthonormality
   srks_select              -- hand-built (theta_m, theta_{m-1}) arrays with known sets
+  cluster_reselect         -- hand-worked gap sequences, evenly spaced values, and an
+                              exhaustive three-piece least-squares fit written in numpy
+                              on random tiny inputs (Section 4.4, end)
   Sequence.solve           -- dense Cholesky solution, textbook CG/PCG written in the test,
                               C^T r = 0, A-conjugacy, finite termination, Proposition 1 /
                               Corollary 1 / Proposition 2 reductions, TRKS m = 0 case,
@@ -42,7 +45,8 @@ CAP = {"truncate": 0, "restart": 1}
 class Policy(ct.Structure):
     _fields_ = [("recycle", ct.c_int32), ("precond", ct.c_int32), ("reorth", ct.c_int32),
                 ("cap_mode", ct.c_int32), ("max_aug", ct.c_int32), ("max_iter", ct.c_int32),
-                ("ritz_eps", ct.c_double), ("theta_frac", ct.c_double)]
+                ("ritz_eps", ct.c_double), ("theta_frac", ct.c_double),
+                ("reselect", ct.c_int32), ("pad", ct.c_int32)]
 
 
 class Stats(ct.Structure):
@@ -83,6 +87,9 @@ def lib():
         L.orc_sym_eig.argtypes = [ct.c_int, dp, dp, dp]
         L.orc_tridiag_eig.argtypes = [ct.c_int, dp, dp, dp, dp]
         L.orc_srks_select.argtypes = [ct.c_int, dp, dp, ct.c_double, ct.c_double, ct.c_int, ip]
+        L.orc_srks_select2.argtypes = [ct.c_int, dp, dp, ct.c_double, ct.c_double, ct.c_int, ct.c_int, ip]
+        L.orc_cluster_reselect.argtypes = [ct.c_int, dp, ip]
+        L.orc_cluster_reselect.restype = None
         L.orc_seq_create.argtypes = [ct.c_int64]
         L.orc_seq_create.restype = ct.c_void_p
         L.orc_seq_destroy.argtypes = [ct.c_void_p]
@@ -195,20 +202,29 @@ def tridiag_eig(delta, eta, vectors=True):
     return (th, np.asarray(Q)) if vectors else th
 
 
-def srks_select(theta_m, theta_m1, eps, theta_frac=0.0, room=1 << 30):
+def srks_select(theta_m, theta_m1, eps, theta_frac=0.0, room=1 << 30, reselect=0):
     theta_m, theta_m1 = _f64(theta_m), _f64(theta_m1)
     m = theta_m.shape[0]
     out = np.zeros(max(m, 1), dtype=np.int32)
     t1 = theta_m1 if theta_m1.size else np.zeros(1)
-    cnt = lib().orc_srks_select(m, _d(theta_m), _d(t1), float(eps), float(theta_frac),
-                                int(min(room, 1 << 30)), _i(out))
+    cnt = lib().orc_srks_select2(m, _d(theta_m), _d(t1), float(eps), float(theta_frac), int(reselect),
+                                 int(min(room, 1 << 30)), _i(out))
     return out[:cnt].copy()
 
 
+def cluster_reselect(values):
+    """keep mask of cluster reselection on ascending values (Section 4.4, end)."""
+    v = _f64(values)
+    keep = np.ones(max(v.shape[0], 1), dtype=np.int32)
+    lib().orc_cluster_reselect(int(v.shape[0]), _d(v), _i(keep))
+    return keep[:v.shape[0]].astype(bool)
+
+
 def make_policy(recycle="none", precond="jacobi", reorth="full", cap_mode="truncate",
-                max_aug=0, max_iter=5000, ritz_eps=1e-14, theta_frac=0.0) -> Policy:
+                max_aug=0, max_iter=5000, ritz_eps=1e-14, theta_frac=0.0, reselect="none") -> Policy:
     return Policy(RECYCLE[recycle], PRECOND[precond], REORTH[reorth], CAP[cap_mode],
-                  int(max_aug), int(max_iter), float(ritz_eps), float(theta_frac))
+                  int(max_aug), int(max_iter), float(ritz_eps), float(theta_frac),
+                  {"none": 0, "cluster": 1}[reselect], 0)
 
 
 class Sequence:

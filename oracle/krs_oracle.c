@@ -44,6 +44,7 @@ enum { ORC_CAP_TRUNCATE = 0, ORC_CAP_RESTART = 1 };
 typedef struct {
   int32_t recycle, precond, reorth, cap_mode, max_aug, max_iter;
   double ritz_eps, theta_frac;
+  int32_t reselect, pad;  /* 0: none, 1: cluster reselection (Section 4.4, end) */
 } orc_policy;
 
 typedef struct {
@@ -237,8 +238,68 @@ int orc_tridiag_eig(int m, const double* delta, const double* eta, double* theta
  * theta < theta_frac * theta_max filter, then ascending-theta order, then at most `room`
  * indices.  theta_m: m values (descending), theta_m1: m-1 values (descending).
  * Writes 0-based indices into theta_m; returns their count. */
-int orc_srks_select(int m, const double* theta_m, const double* theta_m1, double eps,
-                    double theta_frac, int room, int32_t* out) {
+/* Cluster reselection (Section 4.4, end): among the s preselected Ritz values, sorted
+ * ascending v_0 < ... < v_{s-1}, the gaps d_i = v_{i+1} - v_i (i = 0..s-2) are fitted by the
+ * piecewise-constant function with three pieces -- gaps [0, a), [a, b], (b, s-2] -- that is
+ * nearest in least squares; the central piece is the candidate cluster, the values
+ * v_a .. v_{b+1} (at least max(2, ceil(s/5)) of them).  Those values are dropped when the
+ * central piece is strictly denser than every non-empty outer piece (its mean gap is
+ * smaller) and at least one outer piece is non-empty; otherwise nothing is dropped.  Ties in
+ * the fit keep the first (a, b) in lexicographic order.  keep[i] = 0 for a dropped value.
+ * Every piece's mean and squared deviations are computed directly from the gaps. */
+static double piece_sse(const double* d, int lo, int hi, double* mean) {
+  /* gaps [lo, hi] inclusive; empty when hi < lo */
+  if (hi < lo) {
+    *mean = 0.0;
+    return 0.0;
+  }
+  double sum = 0.0;
+  for (int i = lo; i <= hi; i++) sum += d[i];
+  const double mu = sum / (double)(hi - lo + 1);
+  double e = 0.0;
+  for (int i = lo; i <= hi; i++) e += (d[i] - mu) * (d[i] - mu);
+  *mean = mu;
+  return e;
+}
+
+void orc_cluster_reselect(int s, const double* v, int32_t* keep) {
+  for (int i = 0; i < s; i++) keep[i] = 1;
+  if (s < 3) return;
+  int minsize = (s + 4) / 5;
+  if (minsize < 2) minsize = 2;
+  const int ng = s - 1;
+  double* d = (double*)malloc(sizeof(double) * (size_t)ng);
+  if (!d) return;
+  for (int i = 0; i < ng; i++) d[i] = v[i + 1] - v[i];
+  double best = -1.0;
+  int ba = -1, bb = -1;
+  for (int a = 0; a < ng; a++) {
+    for (int b = a; b < ng; b++) {
+      if (b - a + 2 < minsize) continue;
+      double m0, m1, m2;
+      const double e = piece_sse(d, 0, a - 1, &m0) + piece_sse(d, a, b, &m1) + piece_sse(d, b + 1, ng - 1, &m2);
+      if (best < 0.0 || e < best) {
+        best = e;
+        ba = a;
+        bb = b;
+      }
+    }
+  }
+  if (ba >= 0) {
+    double m0, m1, m2;
+    piece_sse(d, 0, ba - 1, &m0);
+    piece_sse(d, ba, bb, &m1);
+    piece_sse(d, bb + 1, ng - 1, &m2);
+    const int left = ba > 0, right = bb < ng - 1;
+    const int denser = (left || right) && (!left || m1 < m0) && (!right || m1 < m2);
+    if (denser)
+      for (int i = ba; i <= bb + 1; i++) keep[i] = 0;
+  }
+  free(d);
+}
+
+int orc_srks_select2(int m, const double* theta_m, const double* theta_m1, double eps, double theta_frac,
+                     int reselect, int room, int32_t* out) {
   if (m < 2 || room <= 0) return 0;
   char* sel = (char*)calloc((size_t)m, 1);
   if (!sel) return 0;
@@ -253,11 +314,39 @@ int orc_srks_select(int m, const double* theta_m, const double* theta_m1, double
     for (int i = 0; i < m; i++)
       if (sel[i] && !(theta_m[i] < theta_frac * theta_m[0])) sel[i] = 0;
   }
+  if (reselect == 1) {
+    /* preselected values in ascending order (theta_m is descending) */
+    int s = 0;
+    for (int i = 0; i < m; i++) s += sel[i];
+    double* v = (double*)malloc(sizeof(double) * (size_t)(s > 0 ? s : 1));
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s > 0 ? s : 1));
+    int32_t* keep = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s > 0 ? s : 1));
+    if (v && idx && keep) {
+      int c = 0;
+      for (int i = m - 1; i >= 0; i--)
+        if (sel[i]) {
+          v[c] = theta_m[i];
+          idx[c] = i;
+          c++;
+        }
+      orc_cluster_reselect(s, v, keep);
+      for (int k = 0; k < s; k++)
+        if (!keep[k]) sel[idx[k]] = 0;
+    }
+    free(v);
+    free(idx);
+    free(keep);
+  }
   int cnt = 0;
   for (int i = m - 1; i >= 0 && cnt < room; i--)  /* descending order -> ascending theta */
     if (sel[i]) out[cnt++] = i;
   free(sel);
   return cnt;
+}
+
+int orc_srks_select(int m, const double* theta_m, const double* theta_m1, double eps,
+                    double theta_frac, int room, int32_t* out) {
+  return orc_srks_select2(m, theta_m, theta_m1, eps, theta_frac, 0, room, out);
 }
 
 /* ----------------------------------------------------------------------------------- */
@@ -517,7 +606,8 @@ converged:
       if (!status) status = orc_tridiag_eig(m - 1, delta, eta, s->theta_m1, NULL);
       if (status) { free(delta); free(eta); free(Q); goto done; }
       int room = (p->cap_mode == ORC_CAP_TRUNCATE) ? (cap - nc) : m;
-      s->n_sel = orc_srks_select(m, s->theta_m, s->theta_m1, p->ritz_eps, p->theta_frac, room, s->sel);
+      s->n_sel = orc_srks_select2(m, s->theta_m, s->theta_m1, p->ritz_eps, p->theta_frac, p->reselect, room,
+                                  s->sel);
       add = s->n_sel;
       if (add > 0) {
         /* y^s = V q^s / sqrt|theta^s|, V = [(-1)^j z_j / sqrt(rho_j)] (Section 4.1) */

@@ -561,3 +561,84 @@ def test_zero_rhs():
     A, b = small_problem(2, seed=27)
     s, x, st = run(A, np.zeros(A.n), 1e-8)
     assert st["status"] == 0 and st["m"] == 0 and np.all(x == 0)
+
+
+# ----------------------------------------------------------------------------------------
+# Cluster reselection (Section 4.4, end): three-piece least-squares fit of the gaps
+# ----------------------------------------------------------------------------------------
+
+def _brute_cluster(v):
+    """Every three-piece split of the gap sequence, fitted by its piece means, in plain
+    numpy; returns the keep mask the reading prescribes (drop the central piece's values
+    when it is strictly denser than every non-empty outer piece)."""
+    v = np.asarray(v, dtype=float)
+    s = v.size
+    keep = np.ones(s, dtype=bool)
+    if s < 3:
+        return keep
+    d = np.diff(v)
+    ng = d.size
+    minsize = max(2, -(-s // 5))
+    best = None
+    for a in range(ng):
+        for b in range(a, ng):
+            if b - a + 2 < minsize:
+                continue
+            pieces = [d[:a], d[a:b + 1], d[b + 1:]]
+            err = sum(float(((p - p.mean()) ** 2).sum()) if p.size else 0.0 for p in pieces)
+            if best is None or err < best[0]:
+                best = (err, a, b, [p.mean() if p.size else None for p in pieces])
+    _, a, b, (m0, m1, m2) = best
+    outer = [m for m in (m0, m2) if m is not None]
+    if outer and all(m1 < m for m in outer):
+        keep[a:b + 2] = False
+    return keep
+
+
+def test_cluster_hand_example():
+    """Values with a dense run in the middle (gaps 0.1) between sparse ends (gaps 1): the
+    three-piece fit is exact and the run 2.0 .. 2.5 is the central cluster."""
+    v = [0.0, 1.0, 2.0, 2.1, 2.2, 2.3, 2.4, 2.5, 3.5, 4.5]
+    keep = O.cluster_reselect(v)
+    assert keep.tolist() == [True, True, False, False, False, False, False, False, True, True]
+
+
+def test_cluster_uniform_and_small():
+    """Evenly spaced values have no denser piece: nothing is dropped; fewer than three
+    values are never touched."""
+    assert O.cluster_reselect(np.arange(12.0)).all()
+    assert O.cluster_reselect([1.0, 2.0]).all()
+    assert O.cluster_reselect([]).size == 0
+
+
+def test_cluster_matches_brute_force_and_invariants():
+    rng = np.random.Generator(np.random.PCG64(77))
+    for trial in range(60):
+        s = int(rng.integers(3, 13))
+        gaps = rng.uniform(0.5, 2.0, s - 1)
+        if trial % 2 == 0 and s >= 5:  # plant a dense run
+            a = int(rng.integers(0, s - 3))
+            L = int(rng.integers(2, s - a))
+            gaps[a:a + L - 1] *= 0.01
+        v = np.concatenate([[0.0], np.cumsum(gaps)])
+        keep = O.cluster_reselect(v)
+        assert keep.tolist() == _brute_cluster(v).tolist(), (trial, v)
+        dropped = np.flatnonzero(~keep)
+        if dropped.size:
+            assert np.all(np.diff(dropped) == 1)              # one contiguous run
+            assert dropped.size >= max(2, -(-s // 5))         # minimum cluster size
+            assert keep.any()                                 # an outer piece survives
+
+
+def test_srks_select_with_cluster_reselection():
+    """theta_{m-1} = the first m-1 values of theta_m: Eq. 16's first test preselects
+    indices 0..m-2 (ascending: 2.0, 3.0 .. 3.5, 4.5, 5.5); reselection drops the dense run
+    3.0 .. 3.5 (gaps 0.1 between gaps of 1.0); the result is in ascending theta order and
+    the cap applies after reselection."""
+    vals_desc = np.array([4.5, 3.5, 2.5, 2.4, 2.3, 2.2, 2.1, 2.0, 1.0, 0.0]) + 1.0
+    tm1 = vals_desc[:-1].copy()
+    sel_all = O.srks_select(vals_desc, tm1, 1e-12)
+    assert sel_all.tolist() == list(range(8, -1, -1))
+    sel = O.srks_select(vals_desc, tm1, 1e-12, reselect=1)
+    assert sel.tolist() == [8, 1, 0]
+    assert O.srks_select(vals_desc, tm1, 1e-12, reselect=1, room=2).tolist() == [8, 1]
