@@ -52,6 +52,7 @@ enum { KRS_REORTH_FULL = 0, KRS_REORTH_NONE = 1 };
 enum { KRS_FP64 = 0, KRS_MIXED_IR = 1 };
 enum { KRS_CAP_TRUNCATE = 0, KRS_CAP_RESTART = 1 };
 enum { KRS_EXEC_PERSISTENT = 0, KRS_EXEC_KERNELS = 1 };
+enum { KRS_RESELECT_NONE = 0, KRS_RESELECT_CLUSTER = 1 };
 
 typedef struct krs_seq* krs_seq_t;
 
@@ -103,7 +104,14 @@ typedef struct {
  *   inner_tol:  KRS_MIXED_IR: relative residual each inner solve aims for (<= 0: 0.1);
  *               the last one is loosened to what the outer tolerance still needs.
  *   max_outer:  KRS_MIXED_IR: limit of refinement steps (<= 0: 30).  max_iter bounds the
- *               total of inner iterations. */
+ *               total of inner iterations.
+ *   reselect:   SRKS only.  KRS_RESELECT_NONE (0), or KRS_RESELECT_CLUSTER (1): after the
+ *               Eq. 16 test and the theta filter, drop the preselected Ritz values of the
+ *               central cluster (Section 4.4, end): the gaps between the sorted preselected
+ *               values are fitted in least squares by a three-piece constant function
+ *               (pieces: gaps before, inside and after the cluster; the cluster holds at least
+ *               max(2, ceil(s/5)) of the s preselected values); the cluster's values are dropped
+ *               when its mean gap is smaller than that of every non-empty outer piece. */
 typedef struct {
   int32_t recycle;
   int32_t precond;
@@ -117,7 +125,7 @@ typedef struct {
   int32_t exec;
   double inner_tol;
   int32_t max_outer;
-  int32_t reserved;
+  int32_t reselect;
 } krs_policy;
 
 /* Device memory and stream.  alloc/free may be NULL (cudaMalloc/cudaFree are used);

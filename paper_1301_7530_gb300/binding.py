@@ -25,6 +25,7 @@ REORTH = {"full": 0, "none": 1}
 PRECISION = {"fp64": 0, "mixed_ir": 1}
 CAP = {"truncate": 0, "restart": 1}
 EXEC = {"persistent": 0, "kernels": 1}
+RESELECT = {"none": 0, "cluster": 1}
 
 
 class krs_bsr(ct.Structure):
@@ -38,7 +39,7 @@ class krs_policy(ct.Structure):
                 ("precision", ct.c_int32), ("ritz_eps", ct.c_double), ("theta_frac", ct.c_double),
                 ("max_aug", ct.c_int32), ("cap_mode", ct.c_int32), ("max_iter", ct.c_int32),
                 ("exec", ct.c_int32), ("inner_tol", ct.c_double), ("max_outer", ct.c_int32),
-                ("reserved", ct.c_int32)]
+                ("reselect", ct.c_int32)]
 
 
 ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p)
@@ -172,10 +173,10 @@ def ptr(a) -> int:
 
 def make_policy(recycle="none", precond="block_jacobi3", reorth="full", precision="fp64",
                 ritz_eps=1e-14, theta_frac=0.0, max_aug=0, cap_mode="truncate", max_iter=2000,
-                exec="persistent", inner_tol=0.0, max_outer=0) -> krs_policy:
+                exec="persistent", inner_tol=0.0, max_outer=0, reselect="none") -> krs_policy:
     return krs_policy(RECYCLE[recycle], PRECOND[precond], REORTH[reorth], PRECISION[precision],
                       float(ritz_eps), float(theta_frac), int(max_aug), CAP[cap_mode], int(max_iter),
-                      EXEC[exec], float(inner_tol), int(max_outer), 0)
+                      EXEC[exec], float(inner_tol), int(max_outer), RESELECT[reselect])
 
 
 _versions = itertools.count(1)

@@ -195,7 +195,7 @@ static krs_status ensure_eig(krs_seq* s, int m) {
   KRS_TRY(alloc_n(s, &s->eta, cap));
   KRS_TRY(alloc_n(s, &s->theta_m, cap));
   KRS_TRY(alloc_n(s, &s->theta_m1, cap));
-  KRS_TRY(alloc_n(s, &s->tsel, 2 * cap));
+  KRS_TRY(alloc_n(s, &s->tsel, 5 * (size_t)cap));
   KRS_TRY(alloc_n(s, &s->sel, cap));
   s->eig_cap = cap;
   return KRS_OK;
@@ -492,7 +492,7 @@ krs_status krs_last_vectors(krs_seq_t s, int32_t which, double* out) {
 // ------------------------------------------------------------------------------------
 // the solve
 // ------------------------------------------------------------------------------------
-static krs_status validate_policy(const krs_policy* p) {
+krs_status krs::validate_policy(const krs_policy* p) {
   if (!p) return fail(KRS_ERR_INVALID_ARG, "policy is NULL");
   if (p->recycle < 0 || p->recycle > 2) return fail(KRS_ERR_INVALID_ARG, "bad recycle %d", p->recycle);
   if (p->precond < 0 || p->precond > 2) return fail(KRS_ERR_INVALID_ARG, "bad precond %d", p->precond);
@@ -505,6 +505,7 @@ static krs_status validate_policy(const krs_policy* p) {
   if (p->max_iter < 1 || p->max_iter > 16000) return fail(KRS_ERR_INVALID_ARG, "max_iter %d outside [1, 16000]", p->max_iter);
   if (p->exec < 0 || p->exec > 1) return fail(KRS_ERR_INVALID_ARG, "bad exec %d", p->exec);
   if (!(p->ritz_eps == p->ritz_eps) || !(p->theta_frac == p->theta_frac)) return fail(KRS_ERR_INVALID_ARG, "NaN policy field");
+  if (p->reselect < 0 || p->reselect > 1) return fail(KRS_ERR_INVALID_ARG, "bad reselect %d", p->reselect);
   return KRS_OK;
 }
 
@@ -692,7 +693,8 @@ static krs_status srks_extract(krs_seq* s, int m, int nc, int room, const krs_po
   KRS_TRY(ensure_eig(s, m));
   KRS_CUDA(launch_lanczos(m, s->alpha, s->rho, s->delta, s->eta, s->stream));
   KRS_CUDA(launch_tridiag_eigvals2(m, m - 1, s->delta, s->eta, s->theta_m, s->theta_m1, s->stream));
-  KRS_CUDA(launch_srks_select(m, s->theta_m, s->theta_m1, p->ritz_eps, p->theta_frac, room, s->sel, s->selcount,
+  KRS_CUDA(launch_srks_select(m, s->theta_m, s->theta_m1, p->ritz_eps, p->theta_frac, p->reselect, room, s->sel,
+                              s->selcount,
                               s->tsel, s->stream));
   *launches += 3;
   KRS_CUDA(cudaMemcpyAsync(&s->h_ctrl[16], s->selcount, sizeof(int), cudaMemcpyDeviceToHost, s->stream));

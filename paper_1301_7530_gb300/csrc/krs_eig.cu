@@ -154,39 +154,150 @@ cudaError_t launch_tridiag_eigvals(int m, const double* delta, const double* eta
 // ------------------------------------------------------------------------------------
 // selection (one thread; O(m))
 // ------------------------------------------------------------------------------------
-__global__ void k_srks_select(int m, const double* tm, const double* tm1, double eps, double theta_frac,
-                              int room, int* sel, int* count, double* tsel, unsigned char* flag) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int cnt = 0;
-  if (m >= 2 && room > 0 && eps > 0.0) {
-    for (int i = 0; i < m; i++) flag[i] = 0;
-    for (int j = 1; j <= m - 1; j++) {  // paper's 1-based j
-      const double a = tm[j - 1], b = tm1[j - 1], c = tm[j];
-      if (fabs(a - b) <= eps * fabs(a)) flag[j - 1] = 1;
-      if (fabs(c - b) <= eps * fabs(c)) flag[j] = 1;
+// Cluster reselection on the s preselected values (ascending) v[0..s): the three-piece
+// least-squares fit of the gaps d_i = v_{i+1} - v_i (pieces [0, a), [a, b], (b, s-2]),
+// central piece = values v_a .. v_{b+1}, at least max(2, ceil(s/5)) of them; the values of
+// the central piece are dropped when it is strictly denser (smaller mean gap) than every
+// non-empty outer piece and an outer piece exists.  Piece sums come from prefix sums of d
+// and d^2; the warp's lanes split the a range, ties go to the smallest (a, b).
+// keep[k] = 0 for a dropped value.  P1, P2: s doubles each (scratch).
+__device__ void cluster_reselect_warp(int s, const double* v, double* P1, double* P2, unsigned char* keep) {
+  const int lane = threadIdx.x & 31;
+  for (int k = lane; k < s; k += 32) keep[k] = 1;
+  __syncwarp();
+  if (s < 3) return;
+  const int ng = s - 1;
+  int minsize = (s + 4) / 5;
+  if (minsize < 2) minsize = 2;
+  if (lane == 0) {
+    double a1 = 0.0, a2 = 0.0;
+    P1[0] = 0.0;
+    P2[0] = 0.0;
+    for (int i = 0; i < ng; i++) {
+      const double d = v[i + 1] - v[i];
+      a1 += d;
+      a2 += d * d;
+      P1[i + 1] = a1;
+      P2[i + 1] = a2;
     }
-    if (theta_frac > 0.0) {
-      const double lim = theta_frac * tm[0];
-      for (int i = 0; i < m; i++)
-        if (flag[i] && !(tm[i] < lim)) flag[i] = 0;
+  }
+  __syncwarp();
+  auto sse = [&](int lo, int hi, double* mean) -> double {  // gaps [lo, hi], empty if hi < lo
+    if (hi < lo) {
+      *mean = 0.0;
+      return 0.0;
     }
-    for (int i = m - 1; i >= 0 && cnt < room; i--) {
-      if (flag[i]) {
-        sel[cnt] = i;
-        tsel[cnt] = tm[i];
-        cnt++;
+    const double len = (double)(hi - lo + 1);
+    const double s1 = P1[hi + 1] - P1[lo], s2 = P2[hi + 1] - P2[lo];
+    *mean = s1 / len;
+    const double e = s2 - s1 * s1 / len;
+    return e > 0.0 ? e : 0.0;
+  };
+  double best = -1.0;
+  int ba = ng, bb = ng;
+  for (int a = lane; a < ng; a += 32) {
+    for (int b = a; b < ng; b++) {
+      if (b - a + 2 < minsize) continue;
+      double m0, m1, m2;
+      const double e = sse(0, a - 1, &m0) + sse(a, b, &m1) + sse(b + 1, ng - 1, &m2);
+      if (best < 0.0 || e < best) {  // within a lane, (a, b) increase: the first minimum stays
+        best = e;
+        ba = a;
+        bb = b;
       }
     }
   }
-  *count = cnt;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double e2 = __shfl_xor_sync(0xffffffffu, best, o);
+    const int a2 = __shfl_xor_sync(0xffffffffu, ba, o), b2 = __shfl_xor_sync(0xffffffffu, bb, o);
+    const bool take = (e2 >= 0.0) && (best < 0.0 || e2 < best || (e2 == best && (a2 < ba || (a2 == ba && b2 < bb))));
+    if (take) {
+      best = e2;
+      ba = a2;
+      bb = b2;
+    }
+  }
+  if (lane == 0 && best >= 0.0) {
+    double m0, m1, m2;
+    sse(0, ba - 1, &m0);
+    sse(ba, bb, &m1);
+    sse(bb + 1, ng - 1, &m2);
+    const bool left = ba > 0, right = bb < ng - 1;
+    const bool denser = (left || right) && (!left || m1 < m0) && (!right || m1 < m2);
+    if (denser)
+      for (int i = ba; i <= bb + 1; i++) keep[i] = 0;
+  }
+  __syncwarp();
+}
+
+// Selection (one warp).  scratch: 4m doubles after the m selected values in tsel:
+// [m, 2m) flags (bytes), [2m, 3m) ascending preselected values, [3m, 5m) prefix sums.
+__global__ void k_srks_select(int m, const double* tm, const double* tm1, double eps, double theta_frac,
+                              int reselect, int room, int* sel, int* count, double* tsel) {
+  if (blockIdx.x != 0) return;
+  unsigned char* flag = reinterpret_cast<unsigned char*>(tsel + m);
+  double* v = tsel + 2 * (size_t)m;
+  double* P1 = tsel + 3 * (size_t)m;
+  double* P2 = tsel + 4 * (size_t)m;
+  unsigned char* keep = reinterpret_cast<unsigned char*>(sel);  // sel is rewritten below
+  const int lane = threadIdx.x & 31;
+  const bool run = m >= 2 && room > 0 && eps > 0.0;
+  __shared__ int s_cnt;
+  if (lane == 0) {
+    s_cnt = 0;
+    if (run) {
+      for (int i = 0; i < m; i++) flag[i] = 0;
+      for (int j = 1; j <= m - 1; j++) {  // paper's 1-based j
+        const double a = tm[j - 1], b = tm1[j - 1], c = tm[j];
+        if (fabs(a - b) <= eps * fabs(a)) flag[j - 1] = 1;
+        if (fabs(c - b) <= eps * fabs(c)) flag[j] = 1;
+      }
+      if (theta_frac > 0.0) {
+        const double lim = theta_frac * tm[0];
+        for (int i = 0; i < m; i++)
+          if (flag[i] && !(tm[i] < lim)) flag[i] = 0;
+      }
+      if (reselect == 1) {
+        int c = 0;
+        for (int i = m - 1; i >= 0; i--)
+          if (flag[i]) v[c++] = tm[i];
+        s_cnt = c;
+      }
+    }
+  }
+  __syncwarp();
+  if (run && reselect == 1) {
+    const int s = s_cnt;
+    cluster_reselect_warp(s, v, P1, P2, keep);
+    if (lane == 0) {
+      int c = 0;
+      for (int i = m - 1; i >= 0; i--)
+        if (flag[i]) {
+          if (!keep[c]) flag[i] = 0;
+          c++;
+        }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    int cnt = 0;
+    if (run) {
+      for (int i = m - 1; i >= 0 && cnt < room; i--) {
+        if (flag[i]) {
+          sel[cnt] = i;
+          tsel[cnt] = tm[i];
+          cnt++;
+        }
+      }
+    }
+    *count = cnt;
+  }
 }
 
 cudaError_t launch_srks_select(int m, const double* theta_m, const double* theta_m1, double eps,
-                               double theta_frac, int room, int* sel, int* count, double* tsel,
+                               double theta_frac, int reselect, int room, int* sel, int* count, double* tsel,
                                cudaStream_t st) {
-  // the flag array lives after tsel's m entries (caller provides 2m doubles for tsel)
-  k_srks_select<<<1, 32, 0, st>>>(m, theta_m, theta_m1, eps, theta_frac, room, sel, count, tsel,
-                                   reinterpret_cast<unsigned char*>(tsel + m));
+  k_srks_select<<<1, 32, 0, st>>>(m, theta_m, theta_m1, eps, theta_frac, reselect, room, sel, count, tsel);
   return cudaGetLastError();
 }
 

@@ -132,8 +132,9 @@ cudaError_t launch_tridiag_eigvecs(int m, const double* delta, const double* eta
                                    const double* theta_sel, double* Q, double* work, cudaStream_t st);
 size_t eigvecs_work_doubles(int m, int k);
 // SRKS selection on device: sel[0..cnt) (ascending theta), cnt in *count, theta values in tsel
+// reselect: 1 = cluster reselection (Section 4.4, end); tsel: 5m doubles of scratch
 cudaError_t launch_srks_select(int m, const double* theta_m, const double* theta_m1, double eps,
-                               double theta_frac, int room, int* sel, int* count, double* tsel,
+                               double theta_frac, int reselect, int room, int* sel, int* count, double* tsel,
                                cudaStream_t st);
 // Y[:, c] = sum_j Z[:, j] (-1)^j Q[j, c] / sqrt(rho_j) / sqrt|theta_c|  for c < k
 cudaError_t launch_ritz_vectors(int64_t n, int64_t ld, int m, int k, const double* Z, const double* rho,

@@ -136,6 +136,8 @@ krs_status alloc_n(krs_seq* s, T** p, size_t count) {
   return KRS_OK;
 }
 bool is_device_ptr(const void* p);
+// KRS_OK when every policy field is in range (message in krs_last_error otherwise)
+krs_status validate_policy(const krs_policy* p);
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 // One FP64 solve split into the stages around its iteration loop.

@@ -18,7 +18,8 @@ def oracle_policy(gpol):
     pre = {0: "jacobi", 1: "block_jacobi3", 2: "identity"}[gpol.precond]
     reo = {0: "full", 1: "none"}[gpol.reorth]
     cap = {0: "truncate", 1: "restart"}[gpol.cap_mode]
-    return O.make_policy(rec, pre, reo, cap, gpol.max_aug, gpol.max_iter, gpol.ritz_eps, gpol.theta_frac)
+    res = {0: "none", 1: "cluster"}[gpol.reselect]
+    return O.make_policy(rec, pre, reo, cap, gpol.max_aug, gpol.max_iter, gpol.ritz_eps, gpol.theta_frac, res)
 
 
 def rel(a, b):

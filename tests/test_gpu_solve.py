@@ -289,3 +289,25 @@ def test_misaligned_device_matrix_is_copied(gpu_lib):
     x, st = B.Sequence(A.n).solve(Ad, torch.as_tensor(bs[0], device="cuda"), 1e-10, pol, version=1)
     torch.cuda.synchronize()
     assert st["m"] == st_ref["m"] and np.array_equal(x.cpu().numpy(), x_ref)
+
+
+def test_srks_cluster_reselection_lockstep(gpu_lib):
+    """SRKS with cluster reselection (Section 4.4, end): lock-step with the oracle; the
+    GPU's selection equals the oracle's selection function applied to the GPU's Ritz values,
+    and it is a subset of plain Eq. 16 selection."""
+    N = 6
+    mask, b, gen = P.elasticity_sequence_damage(N, 5, 13, 2300)
+    seq = B.Sequence(3 * N * (N + 1) ** 2)
+    pol = B.make_policy("srks", "block_jacobi3", ritz_eps=1e-10, max_aug=80, reselect="cluster")
+    dropped = 0
+    for k, Ak in gen:
+        x, st, xo, so, ora, C = solve_pair(seq, Ak, b, 1e-8, pol, version=k + 1)
+        check_pair(Ak, b, 1e-8, pol, x, st, xo, so, C)
+        tm, tm1, sel = seq.last_ritz()
+        if st["m"] >= 2:
+            room = 80 - st["n_c"]
+            assert list(O.srks_select(tm, tm1, 1e-10, 0.0, room, reselect=1)) == list(sel)
+            plain = set(O.srks_select(tm, tm1, 1e-10, 0.0, room))
+            assert set(sel) <= plain
+            dropped += len(plain) - len(sel)
+    assert dropped > 0
