@@ -307,7 +307,8 @@ def test_srks_cluster_reselection_lockstep(gpu_lib):
         if st["m"] >= 2:
             room = 80 - st["n_c"]
             assert list(O.srks_select(tm, tm1, 1e-10, 0.0, room, reselect=1)) == list(sel)
-            plain = set(O.srks_select(tm, tm1, 1e-10, 0.0, room))
-            assert set(sel) <= plain
-            dropped += len(plain) - len(sel)
+            plain = set(O.srks_select(tm, tm1, 1e-10, 0.0))
+            full = set(O.srks_select(tm, tm1, 1e-10, 0.0, reselect=1))
+            assert set(sel) <= full <= plain
+            dropped += len(plain) - len(full)
     assert dropped > 0
