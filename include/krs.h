@@ -49,7 +49,7 @@ typedef enum {
 enum { KRS_RECYCLE_NONE = 0, KRS_RECYCLE_TRKS = 1, KRS_RECYCLE_SRKS = 2 };
 enum { KRS_PRECOND_JACOBI = 0, KRS_PRECOND_BLOCK_JACOBI3 = 1, KRS_PRECOND_IDENTITY = 2 };
 enum { KRS_REORTH_FULL = 0, KRS_REORTH_NONE = 1 };
-enum { KRS_FP64 = 0, KRS_MIXED_IR = 1 };
+enum { KRS_FP64 = 0, KRS_MIXED_IR = 1, KRS_MIXED_PROJ = 2 };
 enum { KRS_CAP_TRUNCATE = 0, KRS_CAP_RESTART = 1 };
 enum { KRS_EXEC_PERSISTENT = 0, KRS_EXEC_KERNELS = 1 };
 enum { KRS_RESELECT_NONE = 0, KRS_RESELECT_CLUSTER = 1 };
@@ -101,6 +101,12 @@ typedef struct {
  *               does not restart the Krylov space.  The recycling step (TRKS / SRKS) between
  *               systems uses the first inner solve.  An FP32 breakdown ((w, Aw) <= 0 or
  *               (r, z) <= 0) after some progress ends that inner solve only.
+ *               KRS_MIXED_PROJ: one APCG solve whose operator product, preconditioner and
+ *               x / r recurrences (and so the residual it converges on) are FP64, while the
+ *               projection (C, AC) and the reorthogonalisation (W, AW, Z) are stored and
+ *               combined in FP32 -- on GB300 those tall-skinny products are most of the FP64
+ *               arithmetic of an iteration.  chol(C^T A C), x_0 / r_0 and H_m stay FP64; SRKS
+ *               forms Ritz vectors from the FP32 z's; krs_last_vectors returns nothing.
  *   inner_tol:  KRS_MIXED_IR: relative residual each inner solve aims for (<= 0: 0.1);
  *               the last one is loosened to what the outer tolerance still needs.
  *   max_outer:  KRS_MIXED_IR: limit of refinement steps (<= 0: 30).  max_iter bounds the

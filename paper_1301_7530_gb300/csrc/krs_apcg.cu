@@ -24,17 +24,33 @@
 // block products and the coarse solve are the items of Section 2.3.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "krs_device.cuh"
 #include "krs_internal.h"
 
 namespace krs {
 
-template <typename T>
+// Precision of a solve: V = vectors x, r, u (and q in PrecP), M = multi-vectors C, AC, W,
+// AW, Z, A = matrix values and M^-1.  Partial sums that cross CTAs and every scalar are
+// doubles in all three.
+//   PrecD  FP64 throughout;
+//   PrecF  FP32 throughout (inner solves of the mixed-precision refinement);
+//   PrecP  FP64 operator product, preconditioner, x and r recurrences; FP32 projection and
+//          reorthogonalisation (C, AC, W, AW, Z stored and combined in FP32).
+struct PrecD { using V = double; using M = double; using A = double; static constexpr int id = 0; };
+struct PrecF { using V = float;  using M = float;  using A = float;  static constexpr int id = 1; };
+struct PrecP { using V = double; using M = float;  using A = double; static constexpr int id = 2; };
+
+template <typename Pr>
 struct ApcgCtx {
+  using V = typename Pr::V;
+  using M = typename Pr::M;
+  using A = typename Pr::A;
   int64_t n, ld;       // order, leading dimension of multi-vectors and vector padding
   int nbr, npc, P;     // block rows, nodes per CTA, CTAs of this problem's group
   int cta0;            // first CTA of the group in a batched launch (0 otherwise)
@@ -49,17 +65,18 @@ struct ApcgCtx {
   const double* dinv;  // 1/(w_i, A w_i) of the tail columns
   const int* rp;
   const int* ci;
-  const T* vals;
-  const T* minv;
-  const T* C;
-  const T* AC;
+  const A* vals;
+  const A* minv;
+  const M* C;
+  const M* AC;
   const double* Ginv;
-  T* W;
-  T* AW;
-  T* Z;
-  T* x;
-  T* r;
-  T* u;
+  M* W;
+  M* AW;
+  M* Z;
+  V* x;
+  V* r;
+  V* u;
+  V* q;                // PrecP: the FP64 operator product A w_j (AW keeps its FP32 copy)
   double* alpha;
   double* gamma;
   double* rho;
@@ -79,27 +96,27 @@ struct ApcgCtx {
 };
 
 // shared-memory layout (in doubles): su[ROW_CHUNK] | red[4*TPB] | sv[kmax]
-// (su and sv hold values of T)
-template <typename T>
+// (su and sv hold values of the multi-vector type M)
+template <typename Pr>
 struct Smem {
-  T* su;
+  typename Pr::M* su;
   double* red;
-  T* sv;
+  typename Pr::M* sv;
 };
 
-template <typename T>
-__device__ __forceinline__ Smem<T> smem_layout(double* base) {
-  Smem<T> s;
-  s.su = reinterpret_cast<T*>(base);
+template <typename Pr>
+__device__ __forceinline__ Smem<Pr> smem_layout(double* base) {
+  Smem<Pr> s;
+  s.su = reinterpret_cast<typename Pr::M*>(base);
   s.red = base + ROW_CHUNK;
-  s.sv = reinterpret_cast<T*>(base + ROW_CHUNK + 4 * TPB);
+  s.sv = reinterpret_cast<typename Pr::M*>(base + ROW_CHUNK + 4 * TPB);
   return s;
 }
 
 enum PhaseResult { PH_CONTINUE = 0, PH_STOP = 1 };
 
-template <typename T>
-__device__ __forceinline__ void finish(const ApcgCtx<T>& c, int status, int m) {
+template <typename Pr>
+__device__ __forceinline__ void finish(const ApcgCtx<Pr>& c, int status, int m) {
   if (c.lb == 0 && threadIdx.x == 0) {
     if (status) atomicCAS(c.ctrl + CTRL_STATUS, 0, status);
     c.ctrl[CTRL_M] = m;
@@ -151,14 +168,20 @@ __device__ __forceinline__ double coarse_coef(const double* Ginv, int ldg, int n
   return s;
 }
 
-template <typename T>
-__device__ __forceinline__ void phase1(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
+template <typename Pr>
+__device__ __forceinline__ void phase1(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm) {
+  using V = typename Pr::V;
+  using M = typename Pr::M;
+  using A = typename Pr::A;
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, c.lb, r0, r1);
-  const T* w = c.W + (int64_t)j * c.ld;
-  T* q = c.AW + (int64_t)j * c.ld;
+  const M* w = c.W + (int64_t)j * c.ld;
+  M* aw = c.AW + (int64_t)j * c.ld;
   double wq = 0.0, rw = 0.0;
-  cta_spmv<T>(c.rp, c.ci, c.vals, w, q, c.r, r0, r1, wq, rw);
+  if constexpr (Pr::id == 2)  // q in FP64 for the recurrences, its FP32 copy into AW
+    cta_spmv<A, M, V, V>(c.rp, c.ci, c.vals, w, c.q, c.r, r0, r1, wq, rw, aw);
+  else
+    cta_spmv<A, M, M, V>(c.rp, c.ci, c.vals, w, aw, c.r, r0, r1, wq, rw);
   block_sum2(wq, rw, sm.red);
   if (threadIdx.x == 0) {
     c.part[c.lb * PS_STRIDE + PS_WQ] = wq;
@@ -166,8 +189,11 @@ __device__ __forceinline__ void phase1(const ApcgCtx<T>& c, int j, Smem<T>& sm) 
   }
 }
 
-template <typename T>
-__device__ __forceinline__ int phase2(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
+template <typename Pr>
+__device__ __forceinline__ int phase2(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm) {
+  using V = typename Pr::V;
+  using M = typename Pr::M;
+  using A = typename Pr::A;
   double gam, rws;
   grid_scalar2(c.part, c.P, PS_WQ, PS_RW, sm.red, gam, rws);
   if (!(gam > 0.0)) {
@@ -179,25 +205,27 @@ __device__ __forceinline__ int phase2(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
     c.alpha[j] = al;
     c.gamma[j] = gam;
   }
-  const T alT = (T)al;
+  const V alT = (V)al;
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, c.lb, r0, r1);
-  const T* w = c.W + (int64_t)j * c.ld;
-  const T* q = c.AW + (int64_t)j * c.ld;
+  const M* w = c.W + (int64_t)j * c.ld;
+  const V* q;
+  if constexpr (Pr::id == 2) q = c.q;
+  else q = c.AW + (int64_t)j * c.ld;
   double rr = 0.0;
   for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
-    c.x[row] += alT * w[row];
-    const T rn = c.r[row] - alT * q[row];
+    c.x[row] += alT * (V)w[row];
+    const V rn = c.r[row] - alT * q[row];
     c.r[row] = rn;
     rr += (double)rn * (double)rn;
   }
   __syncthreads();
   for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB)
-    c.u[row] = precond_row<T>(c.precond, c.minv, c.r, row);
+    c.u[row] = precond_row<A, V>(c.precond, c.minv, c.r, row);
   rr = block_sum(rr, sm.red);
   if (threadIdx.x == 0) c.part[c.lb * PS_STRIDE + PS_RR] = rr;
   if (c.nc > 0)
-    cta_gemv_t<true, T>(c.AC, c.ld, c.nc, c.u, r0, r1, c.vpart + c.lb * c.vld, sm.su, sm.red);
+    cta_gemv_t<true, M, V>(c.AC, c.ld, c.nc, c.u, r0, r1, c.vpart + c.lb * c.vld, sm.su, sm.red);
   return PH_CONTINUE;
 }
 
@@ -208,8 +236,9 @@ __device__ __forceinline__ void col_slice(int k, int P, int b, int& a, int& e) {
   e = min(k, a + per);
 }
 
-template <typename T>
-__device__ __forceinline__ int phase3(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
+template <typename Pr>
+__device__ __forceinline__ int phase3(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm) {
+  using M = typename Pr::M;
   const double rr = grid_scalar(c.part, c.P, PS_RR, sm.red);
   if (rr <= c.tol2) {
     finish(c, 0, j + 1);
@@ -238,7 +267,7 @@ __device__ __forceinline__ int phase3(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
     for (int col = warp; col < c.nc; col += TPB / 32) {
       const double sacc = coarse_coef(c.Ginv, c.ldg, c.nc_dense, c.dinv, col, sm.red);
       if (lane == 0) {
-        sm.sv[col] = (T)sacc;
+        sm.sv[col] = (M)sacc;
         if (c.lb == 0) c.sfull[col] = sacc;  // for the per-phase kernel mode
       }
     }
@@ -247,8 +276,8 @@ __device__ __forceinline__ int phase3(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
   return PH_CONTINUE;
 }
 
-template <typename T>
-__device__ __forceinline__ void phase4(const ApcgCtx<T>& c) {
+template <typename Pr>
+__device__ __forceinline__ void phase4(const ApcgCtx<Pr>& c) {
   int a, e;
   col_slice(c.nc, c.P, c.lb, a, e);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -260,19 +289,21 @@ __device__ __forceinline__ void phase4(const ApcgCtx<T>& c) {
 
 // s_in_smem: s = Ginv t is already in sm.sv (small-augmentation path of phase 3 in the
 // same kernel); otherwise it is read from sfull.
-template <typename T>
-__device__ __forceinline__ void phase5(const ApcgCtx<T>& c, int j, Smem<T>& sm, bool s_in_smem) {
+template <typename Pr>
+__device__ __forceinline__ void phase5(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm, bool s_in_smem) {
+  using V = typename Pr::V;
+  using M = typename Pr::M;
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, c.lb, r0, r1);
-  T* z = c.Z + (int64_t)(j + 1) * c.ld;
+  M* z = c.Z + (int64_t)(j + 1) * c.ld;
   if (c.nc > 0) {
     if (!s_in_smem) {
-      for (int k = threadIdx.x; k < c.nc; k += TPB) sm.sv[k] = (T)c.sfull[k];
+      for (int k = threadIdx.x; k < c.nc; k += TPB) sm.sv[k] = (M)c.sfull[k];
     }
     __syncthreads();
-    cta_gemv_n<true, T>(c.C, c.ld, c.nc, sm.sv, T(-1), c.u, z, r0, r1, sm.red);
+    cta_gemv_n<true, M, V, M>(c.C, c.ld, c.nc, sm.sv, M(-1), c.u, z, r0, r1, sm.red);
   } else {
-    for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) z[row] = c.u[row];
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) z[row] = (M)c.u[row];
     __syncthreads();
   }
   double rz = 0.0;
@@ -281,12 +312,12 @@ __device__ __forceinline__ void phase5(const ApcgCtx<T>& c, int j, Smem<T>& sm, 
   if (threadIdx.x == 0) c.part[c.lb * PS_STRIDE + PS_RZ] = rz;
   const int base = c.reorth_full ? 0 : j;
   const int kk = j + 1 - base;
-  cta_gemv_t<false, T>(c.AW + (int64_t)base * c.ld, c.ld, kk, z, r0, r1, c.gpart + c.lb * c.vld,
-                       sm.su, sm.red);
+  cta_gemv_t<false, M, M>(c.AW + (int64_t)base * c.ld, c.ld, kk, z, r0, r1, c.gpart + c.lb * c.vld,
+                          sm.su, sm.red);
 }
 
-template <typename T>
-__device__ __forceinline__ int phase6(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
+template <typename Pr>
+__device__ __forceinline__ int phase6(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm) {
   const double rz = grid_scalar(c.part, c.P, PS_RZ, sm.red);
   if (!(rz > 0.0)) {
     finish(c, 2 /* KRS_ERR_NOT_SPD */, j + 1);
@@ -305,17 +336,18 @@ __device__ __forceinline__ int phase6(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
   return PH_CONTINUE;
 }
 
-template <typename T>
-__device__ __forceinline__ void phase7(const ApcgCtx<T>& c, int j, Smem<T>& sm) {
+template <typename Pr>
+__device__ __forceinline__ void phase7(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm) {
+  using M = typename Pr::M;
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, c.lb, r0, r1);
   const int base = c.reorth_full ? 0 : j;
   const int kk = j + 1 - base;
-  for (int k = threadIdx.x; k < kk; k += TPB) sm.sv[k] = (T)c.gfull[k];
+  for (int k = threadIdx.x; k < kk; k += TPB) sm.sv[k] = (M)c.gfull[k];
   __syncthreads();
-  const T* z = c.Z + (int64_t)(j + 1) * c.ld;
-  T* wn = c.W + (int64_t)(j + 1) * c.ld;
-  cta_gemv_n<false, T>(c.W + (int64_t)base * c.ld, c.ld, kk, sm.sv, T(-1), z, wn, r0, r1, sm.red);
+  const M* z = c.Z + (int64_t)(j + 1) * c.ld;
+  M* wn = c.W + (int64_t)(j + 1) * c.ld;
+  cta_gemv_n<false, M, M, M>(c.W + (int64_t)base * c.ld, c.ld, kk, sm.sv, M(-1), z, wn, r0, r1, sm.red);
 }
 
 // ------------------------------------------------------------------------------------
@@ -331,8 +363,8 @@ enum LoopResult { LOOP_ENDED = 0, LOOP_SUSPENDED = 1, LOOP_ABORTED = 2, LOOP_DRA
 // the launch's idle-group count with drain_at and publishes the outcome in the group's
 // drain word before the iteration's last barrier; every CTA of the group reads that word
 // after the barrier, so all of them suspend at the same iteration.
-template <typename T>
-__device__ __forceinline__ int apcg_loop(const ApcgCtx<T>& c, Smem<T>& sm, int j0, int quantum,
+template <typename Pr>
+__device__ __forceinline__ int apcg_loop(const ApcgCtx<Pr>& c, Smem<Pr>& sm, int j0, int quantum,
                                          unsigned long long& target) {
   const int TO = 6;  // KRS_ERR_TIMEOUT
 #define KRS_SYNC()                                                                         \
@@ -373,10 +405,10 @@ __device__ __forceinline__ int apcg_loop(const ApcgCtx<T>& c, Smem<T>& sm, int j
 }
 
 // persistent kernel: one solve, all CTAs in one group
-template <typename T>
-__global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx<T> c) {
+template <typename Pr>
+__global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx<Pr> c) {
   extern __shared__ double4_32a smem_raw4[];
-  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
+  Smem<Pr> sm = smem_layout<Pr>(reinterpret_cast<double*>(smem_raw4));
   c.lb = blockIdx.x;
   unsigned long long target = 0;
   apcg_loop(c, sm, 0, 0x7fffffff, target);
@@ -392,9 +424,9 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_persistent(ApcgCtx<T> c) {
 // queued only in the class whose group size its context was prepared for, so its
 // arithmetic (the partition and the order of every reduction) depends on its group size
 // only -- not on which group runs it or on which other solves share the launch.
-template <typename T>
+template <typename Pr>
 struct BatchArgs {
-  const ApcgCtx<T>* ctxs;   // one per solve in the table
+  const ApcgCtx<Pr>* ctxs;   // one per solve in the table
   const int* queue;         // per class, indices into ctxs in the order groups take them
   const int* qoff;          // [classes + 1] offsets of the classes' queues
   int* heads;               // [classes] queue positions (zero at launch)
@@ -415,10 +447,10 @@ struct BatchArgs {
   int* bctrl;               // launch-wide status / abort words
 };
 
-template <typename T>
-__global__ void __launch_bounds__(TPB, 1) k_apcg_batched(BatchArgs<T> B) {
+template <typename Pr>
+__global__ void __launch_bounds__(TPB, 1) k_apcg_batched(BatchArgs<Pr> B) {
   extern __shared__ double4_32a smem_raw4[];
-  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
+  Smem<Pr> sm = smem_layout<Pr>(reinterpret_cast<double*>(smem_raw4));
   const int group = B.cta_group[blockIdx.x];
   const int c0 = B.grp_cta0[group];
   const int g = B.grp_cta0[group + 1] - c0;
@@ -427,7 +459,7 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_batched(BatchArgs<T> B) {
   const int q0 = B.qoff[cls], qlen = B.qoff[cls + 1] - q0;
   unsigned long long* bar = B.gbar + (int64_t)group * 16;
   unsigned long long target = 0;
-  __shared__ ApcgCtx<T> s_ctx;
+  __shared__ ApcgCtx<Pr> s_ctx;
   __shared__ int s_j0;
   for (int round = 0;; round++) {
     int* box = B.mail + 2 * group + (round & 1);
@@ -443,7 +475,7 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_batched(BatchArgs<T> B) {
     // single-solve kernel has no per-solve equivalent; registers would spill)
     __syncthreads();  // every thread is done with the previous solve's context
     if (threadIdx.x == 0) {
-      ApcgCtx<T> c = B.ctxs[idx];
+      ApcgCtx<Pr> c = B.ctxs[idx];
       c.lb = lb;
       c.P = g;
       c.bar = bar;
@@ -459,7 +491,7 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_batched(BatchArgs<T> B) {
       s_j0 = *((volatile int*)(c.ctrl + CTRL_J));
     }
     __syncthreads();
-    const ApcgCtx<T>& c = s_ctx;
+    const ApcgCtx<Pr>& c = s_ctx;
     const int j0 = s_j0;
     const int res = apcg_loop(c, sm, j0, B.quantum, target);
     if (res == LOOP_ABORTED || res == LOOP_DRAINED) return;
@@ -469,16 +501,16 @@ __global__ void __launch_bounds__(TPB, 1) k_apcg_batched(BatchArgs<T> B) {
 // ------------------------------------------------------------------------------------
 // per-phase kernels (kernels mode).  Each returns at once when the solve has ended.
 // ------------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ bool ended(const ApcgCtx<T>& c) {
+template <typename Pr>
+__device__ __forceinline__ bool ended(const ApcgCtx<Pr>& c) {
   return *((volatile int*)(c.ctrl + CTRL_DONE)) != 0;
 }
 
 #define KRS_PHASE_KERNEL(NAME, BODY)                                          \
-  template <typename T>                                                       \
-  __global__ void __launch_bounds__(TPB, 1) NAME(ApcgCtx<T> c, int j) {      \
+  template <typename Pr>                                                       \
+  __global__ void __launch_bounds__(TPB, 1) NAME(ApcgCtx<Pr> c, int j) {      \
     extern __shared__ double4_32a smem_raw4[];                                \
-    Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));       \
+    Smem<Pr> sm = smem_layout<Pr>(reinterpret_cast<double*>(smem_raw4));       \
     c.lb = blockIdx.x;                                                        \
     if (ended(c)) return;                                                     \
     (void)sm;                                                                 \
@@ -498,14 +530,15 @@ KRS_PHASE_KERNEL(k_phase7, phase7(c, j, sm))
 // ------------------------------------------------------------------------------------
 
 // partial t = V^T y over the CTA's rows (y global)
-template <typename T>
-__global__ void __launch_bounds__(TPB, 1) k_gemv_t_part(const T* V, int64_t ld, int k, const T* y, int nbr,
+template <typename TM, typename TU>
+__global__ void __launch_bounds__(TPB, 1) k_gemv_t_part(const TM* V, int64_t ld, int k, const TU* y, int nbr,
                                                         int npc, double* vpart, int64_t vld) {
   extern __shared__ double4_32a smem_raw4[];
-  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
+  double* base = reinterpret_cast<double*>(smem_raw4);
   int64_t r0, r1;
   cta_rows(nbr, npc, blockIdx.x, r0, r1);
-  cta_gemv_t<false, T>(V, ld, k, y, r0, r1, vpart + blockIdx.x * vld, sm.su, sm.red);
+  cta_gemv_t<false, TM, TU>(V, ld, k, y, r0, r1, vpart + blockIdx.x * vld, reinterpret_cast<TM*>(base),
+                            base + ROW_CHUNK);
 }
 
 // out[c] = sum_b vpart[b*vld + c]  (c < k)
@@ -525,21 +558,23 @@ __global__ void k_small_gemv(const double* G, int ldg, int k, int k_dense, const
 }
 
 // x = C s, r = b - AC s (or x = 0, r = b when k == 0); partials (b, b) and (r, r)
-template <typename T>
-__global__ void __launch_bounds__(TPB, 1) k_init_xr(const T* C, const T* AC, int64_t ld, int k, const double* s,
-                                                    const T* b, T* x, T* r, int nbr, int npc, double* part) {
+template <typename TC, typename TV>
+__global__ void __launch_bounds__(TPB, 1) k_init_xr(const TC* C, const TC* AC, int64_t ld, int k, const double* s,
+                                                    const TV* b, TV* x, TV* r, int nbr, int npc, double* part) {
   extern __shared__ double4_32a smem_raw4[];
-  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
+  double* base = reinterpret_cast<double*>(smem_raw4);
+  double* red = base + ROW_CHUNK;
+  TC* sv = reinterpret_cast<TC*>(base + ROW_CHUNK + 4 * TPB);
   int64_t r0, r1;
   cta_rows(nbr, npc, blockIdx.x, r0, r1);
   if (k > 0) {
-    for (int i = threadIdx.x; i < k; i += TPB) sm.sv[i] = (T)s[i];
+    for (int i = threadIdx.x; i < k; i += TPB) sv[i] = (TC)s[i];
     __syncthreads();
-    cta_gemv_n<false, T>(C, ld, k, sm.sv, T(1), nullptr, x, r0, r1, sm.red);
-    cta_gemv_n<false, T>(AC, ld, k, sm.sv, T(-1), b, r, r0, r1, sm.red);
+    cta_gemv_n<false, TC, TV, TV>(C, ld, k, sv, TC(1), nullptr, x, r0, r1, red);
+    cta_gemv_n<false, TC, TV, TV>(AC, ld, k, sv, TC(-1), b, r, r0, r1, red);
   } else {
     for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
-      x[row] = T(0);
+      x[row] = TV(0);
       r[row] = b[row];
     }
     __syncthreads();
@@ -549,7 +584,7 @@ __global__ void __launch_bounds__(TPB, 1) k_init_xr(const T* C, const T* AC, int
     bb += (double)b[row] * (double)b[row];
     rr += (double)r[row] * (double)r[row];
   }
-  block_sum2(bb, rr, sm.red);
+  block_sum2(bb, rr, red);
   if (threadIdx.x == 0) {
     part[blockIdx.x * PS_STRIDE + 0] = bb;
     part[blockIdx.x * PS_STRIDE + 1] = rr;
@@ -557,26 +592,28 @@ __global__ void __launch_bounds__(TPB, 1) k_init_xr(const T* C, const T* AC, int
 }
 
 // u = M^-1 r
-template <typename T>
-__global__ void k_precond_rows(int kind, const T* minv, const T* r, T* u, int64_t n) {
+template <typename TA, typename TV>
+__global__ void k_precond_rows(int kind, const TA* minv, const TV* r, TV* u, int64_t n) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row < n) u[row] = precond_row<T>(kind, minv, r, row);
+  if (row < n) u[row] = precond_row<TA, TV>(kind, minv, r, row);
 }
 
-// z0 = u - C s (or u), W[:,0] = Z[:,0] = z0, partial (r, z0)
-template <typename T>
-__global__ void __launch_bounds__(TPB, 1) k_init_z(const T* C, int64_t ld, int k, const double* s, const T* u,
-                                                   const T* r, T* Z, T* W, int nbr, int npc, double* part) {
+// z0 = u - C s (or u), stored as TZ: W[:,0] = Z[:,0] = z0, partial (r, z0) of the stored z0
+template <typename TC, typename TV, typename TZ>
+__global__ void __launch_bounds__(TPB, 1) k_init_z(const TC* C, int64_t ld, int k, const double* s, const TV* u,
+                                                   const TV* r, TZ* Z, TZ* W, int nbr, int npc, double* part) {
   extern __shared__ double4_32a smem_raw4[];
-  Smem<T> sm = smem_layout<T>(reinterpret_cast<double*>(smem_raw4));
+  double* base = reinterpret_cast<double*>(smem_raw4);
+  double* red = base + ROW_CHUNK;
+  TC* sv = reinterpret_cast<TC*>(base + ROW_CHUNK + 4 * TPB);
   int64_t r0, r1;
   cta_rows(nbr, npc, blockIdx.x, r0, r1);
   if (k > 0) {
-    for (int i = threadIdx.x; i < k; i += TPB) sm.sv[i] = (T)s[i];
+    for (int i = threadIdx.x; i < k; i += TPB) sv[i] = (TC)s[i];
     __syncthreads();
-    cta_gemv_n<false, T>(C, ld, k, sm.sv, T(-1), u, Z, r0, r1, sm.red);
+    cta_gemv_n<false, TC, TV, TZ>(C, ld, k, sv, TC(-1), u, Z, r0, r1, red);
   } else {
-    for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) Z[row] = u[row];
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) Z[row] = (TZ)u[row];
     __syncthreads();
   }
   double rz = 0.0;
@@ -584,7 +621,7 @@ __global__ void __launch_bounds__(TPB, 1) k_init_z(const T* C, int64_t ld, int k
     W[row] = Z[row];
     rz += (double)r[row] * (double)Z[row];
   }
-  rz = block_sum(rz, sm.red);
+  rz = block_sum(rz, red);
   if (threadIdx.x == 0) part[blockIdx.x * PS_STRIDE + 2] = rz;
 }
 
@@ -607,19 +644,23 @@ size_t apcg_smem_bytes(int kmax) {
   return sizeof(double) * (size_t)(ROW_CHUNK + 4 * TPB + ((kmax + 3) & ~3));
 }
 
-template <typename T>
-static ApcgCtx<T> make_ctx(const IterArgs& a) {
-  ApcgCtx<T> c;
+template <typename Pr>
+static ApcgCtx<Pr> make_ctx(const IterArgs& a) {
+  using V = typename Pr::V;
+  using M = typename Pr::M;
+  using A = typename Pr::A;
+  ApcgCtx<Pr> c;
   c.n = a.n; c.ld = a.ld; c.nbr = a.nbr; c.npc = a.npc; c.P = a.P;
   c.nc = a.nc; c.ldg = a.ldg; c.max_iter = a.max_iter; c.reorth_full = a.reorth_full;
   c.nc_dense = a.nc_dense; c.dinv = a.dinv;
   c.cta0 = 0; c.lb = 0; c.jcap = a.jcap > 0 ? a.jcap : 0x7fffffff;
   c.precond = a.precond; c.tol2 = a.tol2; c.spin_limit = a.spin_limit;
   c.rp = a.rp; c.ci = a.ci;
-  c.vals = static_cast<const T*>(a.vals); c.minv = static_cast<const T*>(a.minv);
-  c.C = static_cast<const T*>(a.C); c.AC = static_cast<const T*>(a.AC); c.Ginv = a.Ginv;
-  c.W = static_cast<T*>(a.W); c.AW = static_cast<T*>(a.AW); c.Z = static_cast<T*>(a.Z);
-  c.x = static_cast<T*>(a.x); c.r = static_cast<T*>(a.r); c.u = static_cast<T*>(a.u);
+  c.vals = static_cast<const A*>(a.vals); c.minv = static_cast<const A*>(a.minv);
+  c.C = static_cast<const M*>(a.C); c.AC = static_cast<const M*>(a.AC); c.Ginv = a.Ginv;
+  c.W = static_cast<M*>(a.W); c.AW = static_cast<M*>(a.AW); c.Z = static_cast<M*>(a.Z);
+  c.x = static_cast<V*>(a.x); c.r = static_cast<V*>(a.r); c.u = static_cast<V*>(a.u);
+  c.q = static_cast<V*>(a.q);
   c.alpha = a.alpha; c.gamma = a.gamma; c.rho = a.rho;
   c.tfull = a.tfull; c.sfull = a.sfull; c.gfull = a.gfull;
   c.part = a.part; c.vpart = a.vpart; c.gpart = a.gpart; c.vld = a.vld; c.ctrl = a.ctrl; c.bar = a.bar;
@@ -630,12 +671,22 @@ static ApcgCtx<T> make_ctx(const IterArgs& a) {
   return c;
 }
 
-template <typename T>
+// init element types: the init stage of PrecP works from the FP64 C and AC (x_0 and r_0 in
+// FP64, consistent with the FP64 recurrences) and stores z_0 in FP32
+template <typename Pr>
+struct InitTypes {
+  using TC = typename std::conditional<Pr::id == 2, double, typename Pr::M>::type;
+};
+
+template <typename Pr>
 static cudaError_t prepare_attributes_t(size_t sm) {
-  const void* fns[] = {(const void*)k_apcg_persistent<T>, (const void*)k_phase1<T>, (const void*)k_phase2<T>,
-                       (const void*)k_phase3<T>, (const void*)k_phase4<T>, (const void*)k_phase5<T>,
-                       (const void*)k_phase6<T>, (const void*)k_phase7<T>, (const void*)k_gemv_t_part<T>,
-                       (const void*)k_init_xr<T>, (const void*)k_init_z<T>};
+  using V = typename Pr::V;
+  using M = typename Pr::M;
+  using TC = typename InitTypes<Pr>::TC;
+  const void* fns[] = {(const void*)k_apcg_persistent<Pr>, (const void*)k_phase1<Pr>, (const void*)k_phase2<Pr>,
+                       (const void*)k_phase3<Pr>, (const void*)k_phase4<Pr>, (const void*)k_phase5<Pr>,
+                       (const void*)k_phase6<Pr>, (const void*)k_phase7<Pr>, (const void*)k_gemv_t_part<TC, V>,
+                       (const void*)k_init_xr<TC, V>, (const void*)k_init_z<TC, V, M>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -643,62 +694,80 @@ static cudaError_t prepare_attributes_t(size_t sm) {
   return cudaSuccess;
 }
 
+// Dispatch on the precision id of IterArgs (0 PrecD, 1 PrecF, 2 PrecP).
+#define KRS_DISPATCH(prec, CALL)           \
+  do {                                     \
+    if ((prec) == 1) {                     \
+      using PR = PrecF;                    \
+      CALL;                                \
+    } else if ((prec) == 2) {              \
+      using PR = PrecP;                    \
+      CALL;                                \
+    } else {                               \
+      using PR = PrecD;                    \
+      CALL;                                \
+    }                                      \
+  } while (0)
+
 // The dynamic shared-memory limit is a per-function attribute of the device: it only ever
 // grows here, so a launch prepared for one solve stays valid after another solve (of a
 // smaller kmax) prepared the same kernels.
-cudaError_t apcg_prepare_attributes(int kmax, bool fp32) {
+cudaError_t apcg_prepare_attributes(int kmax, int prec) {
   static std::mutex mu;
-  static size_t set_bytes[64][2] = {};
+  static size_t set_bytes[64][3] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (dev < 0 || dev >= 64 || prec < 0 || prec > 2) return cudaErrorInvalidValue;
   const size_t sm = apcg_smem_bytes(kmax);
   std::lock_guard<std::mutex> lock(mu);
-  size_t& cur = set_bytes[dev][fp32 ? 1 : 0];
+  size_t& cur = set_bytes[dev][prec];
   if (sm <= cur) return cudaSuccess;
-  e = fp32 ? prepare_attributes_t<float>(sm) : prepare_attributes_t<double>(sm);
+  KRS_DISPATCH(prec, e = prepare_attributes_t<PR>(sm));
   if (e == cudaSuccess) cur = sm;
   return e;
 }
 
-cudaError_t apcg_max_coresident(int kmax, bool fp32, int* blocks_per_sm) {
-  if (fp32)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_apcg_persistent<float>, TPB,
-                                                         apcg_smem_bytes(kmax));
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_apcg_persistent<double>, TPB,
-                                                       apcg_smem_bytes(kmax));
+cudaError_t apcg_max_coresident(int kmax, int prec, int* blocks_per_sm) {
+  cudaError_t e = cudaSuccess;
+  KRS_DISPATCH(prec, e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_apcg_persistent<PR>, TPB,
+                                                                       apcg_smem_bytes(kmax)));
+  return e;
 }
 
-template <typename T>
+template <typename Pr>
 static cudaError_t launch_init_t(const IterArgs& a, const void* bv, double* scal, cudaStream_t st,
                                  int64_t* launches) {
+  using V = typename Pr::V;
+  using M = typename Pr::M;
+  using A = typename Pr::A;
+  using TC = typename InitTypes<Pr>::TC;
   const size_t sm = apcg_smem_bytes(a.kmax);
   const int k = a.nc;
-  const T* b = static_cast<const T*>(bv);
-  const T* C = static_cast<const T*>(a.C);
-  const T* AC = static_cast<const T*>(a.AC);
-  T* x = static_cast<T*>(a.x);
-  T* r = static_cast<T*>(a.r);
-  T* u = static_cast<T*>(a.u);
+  const V* b = static_cast<const V*>(bv);
+  const TC* C = static_cast<const TC*>(a.Ci ? a.Ci : a.C);
+  const TC* AC = static_cast<const TC*>(a.ACi ? a.ACi : a.AC);
+  V* x = static_cast<V*>(a.x);
+  V* r = static_cast<V*>(a.r);
+  V* u = static_cast<V*>(a.u);
   if (k > 0) {
-    k_gemv_t_part<T><<<a.P, TPB, sm, st>>>(C, a.ld, k, b, a.nbr, a.npc, a.vpart, a.vld);
+    k_gemv_t_part<TC, V><<<a.P, TPB, sm, st>>>(C, a.ld, k, b, a.nbr, a.npc, a.vpart, a.vld);
     k_reduce_cols<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.vpart, a.vld, a.P, k, a.tfull);
     k_small_gemv<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.Ginv, a.ldg, k, a.nc_dense, a.dinv, a.tfull, a.sfull);
     *launches += 3;
   }
-  k_init_xr<T><<<a.P, TPB, sm, st>>>(C, AC, a.ld, k, a.sfull, b, x, r, a.nbr, a.npc, a.part);
-  k_precond_rows<T><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a.precond, static_cast<const T*>(a.minv), r, u,
-                                                                     a.n);
+  k_init_xr<TC, V><<<a.P, TPB, sm, st>>>(C, AC, a.ld, k, a.sfull, b, x, r, a.nbr, a.npc, a.part);
+  k_precond_rows<A, V><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a.precond, static_cast<const A*>(a.minv), r,
+                                                                        u, a.n);
   *launches += 2;
   if (k > 0) {
-    k_gemv_t_part<T><<<a.P, TPB, sm, st>>>(AC, a.ld, k, u, a.nbr, a.npc, a.vpart, a.vld);
+    k_gemv_t_part<TC, V><<<a.P, TPB, sm, st>>>(AC, a.ld, k, u, a.nbr, a.npc, a.vpart, a.vld);
     k_reduce_cols<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.vpart, a.vld, a.P, k, a.tfull);
     k_small_gemv<<<(k * 32 + 255) / 256, 256, 0, st>>>(a.Ginv, a.ldg, k, a.nc_dense, a.dinv, a.tfull, a.sfull);
     *launches += 3;
   }
-  k_init_z<T><<<a.P, TPB, sm, st>>>(C, a.ld, k, a.sfull, u, r, static_cast<T*>(a.Z), static_cast<T*>(a.W), a.nbr,
-                                    a.npc, a.part);
+  k_init_z<TC, V, M><<<a.P, TPB, sm, st>>>(C, a.ld, k, a.sfull, u, r, static_cast<M*>(a.Z), static_cast<M*>(a.W),
+                                           a.nbr, a.npc, a.part);
   k_init_finish<<<1, 96, 0, st>>>(a.part, a.P, scal, a.rho);
   *launches += 2;
   return cudaGetLastError();
@@ -706,53 +775,69 @@ static cudaError_t launch_init_t(const IterArgs& a, const void* bv, double* scal
 
 // Set-up of x_0, r_0, z_0, w_0, rho_0, ||b||^2, ||r_0||^2 (scal[0..1]).  Counts launches.
 cudaError_t apcg_launch_init(const IterArgs& a, const void* b, double* scal, cudaStream_t st, int64_t* launches) {
-  return a.fp32 ? launch_init_t<float>(a, b, scal, st, launches) : launch_init_t<double>(a, b, scal, st, launches);
+  cudaError_t e = cudaSuccess;
+  KRS_DISPATCH(a.prec, e = launch_init_t<PR>(a, b, scal, st, launches));
+  return e;
+}
+
+template <typename Pr>
+static cudaError_t launch_persistent_t(const IterArgs& a, cudaStream_t st) {
+  ApcgCtx<Pr> c = make_ctx<Pr>(a);
+  void* args[] = {&c};
+  return cudaLaunchCooperativeKernel((const void*)k_apcg_persistent<Pr>, dim3(a.P), dim3(TPB), args,
+                                     apcg_smem_bytes(a.kmax), st);
 }
 
 cudaError_t apcg_launch_persistent(const IterArgs& a, cudaStream_t st, int64_t* launches) {
   *launches += 1;
-  if (a.fp32) {
-    ApcgCtx<float> c = make_ctx<float>(a);
-    void* args[] = {&c};
-    return cudaLaunchCooperativeKernel((const void*)k_apcg_persistent<float>, dim3(a.P), dim3(TPB), args,
-                                       apcg_smem_bytes(a.kmax), st);
-  }
-  ApcgCtx<double> c = make_ctx<double>(a);
-  void* args[] = {&c};
-  return cudaLaunchCooperativeKernel((const void*)k_apcg_persistent<double>, dim3(a.P), dim3(TPB), args,
-                                     apcg_smem_bytes(a.kmax), st);
+  cudaError_t e = cudaSuccess;
+  KRS_DISPATCH(a.prec, e = launch_persistent_t<PR>(a, st));
+  return e;
 }
 
-size_t apcg_ctx_bytes() { return sizeof(ApcgCtx<double>); }
+size_t apcg_ctx_bytes() {
+  static_assert(sizeof(ApcgCtx<PrecD>) == sizeof(ApcgCtx<PrecP>) && sizeof(ApcgCtx<PrecD>) == sizeof(ApcgCtx<PrecF>),
+                "one context size for every precision");
+  return sizeof(ApcgCtx<PrecD>);
+}
 
 void apcg_fill_ctx(const IterArgs& a, void* dst) {
-  ApcgCtx<double> c = make_ctx<double>(a);
-  memcpy(dst, &c, sizeof(c));
+  KRS_DISPATCH(a.prec, {
+    ApcgCtx<PR> c = make_ctx<PR>(a);
+    memcpy(dst, &c, sizeof(c));
+  });
 }
 
-cudaError_t apcg_batched_coresident(int kmax, int* blocks_per_sm) {
+cudaError_t apcg_batched_coresident(int kmax, int prec, int* blocks_per_sm) {
   const size_t sm = apcg_smem_bytes(kmax);
-  cudaError_t e = cudaFuncSetAttribute((const void*)k_apcg_batched<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_apcg_batched<double>, TPB, sm);
+  cudaError_t e = cudaSuccess;
+  KRS_DISPATCH(prec, {
+    e = cudaFuncSetAttribute((const void*)k_apcg_batched<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_apcg_batched<PR>, TPB, sm);
+  });
+  return e;
 }
 
-// out[4 p + w] = word w (status, done, m, j) of solve p's control block
-__global__ void k_gather_ctrl(const ApcgCtx<double>* __restrict__ ctxs, int count, int* __restrict__ out) {
+// out[4 p + w] = word w (status, done, m, j) of solve p's control block (the control
+// pointer sits at the same offset in every precision's context)
+__global__ void k_gather_ctrl(const ApcgCtx<PrecD>* __restrict__ ctxs, int count, int* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < 4 * count) out[i] = *((volatile const int*)(ctxs[i >> 2].ctrl + (i & 3)));
 }
 
 cudaError_t apcg_gather_ctrl(const void* ctxs, int count, int* out, cudaStream_t st) {
+  static_assert(offsetof(ApcgCtx<PrecD>, ctrl) == offsetof(ApcgCtx<PrecP>, ctrl) &&
+                    offsetof(ApcgCtx<PrecD>, ctrl) == offsetof(ApcgCtx<PrecF>, ctrl),
+                "control pointer at one offset");
   if (count <= 0) return cudaSuccess;
-  k_gather_ctrl<<<(4 * count + 255) / 256, 256, 0, st>>>(static_cast<const ApcgCtx<double>*>(ctxs), count, out);
+  k_gather_ctrl<<<(4 * count + 255) / 256, 256, 0, st>>>(static_cast<const ApcgCtx<PrecD>*>(ctxs), count, out);
   return cudaGetLastError();
 }
 
-cudaError_t apcg_launch_batched(const BatchLaunch& L, cudaStream_t st) {
-  BatchArgs<double> B;
-  B.ctxs = static_cast<const ApcgCtx<double>*>(L.ctxs);
+template <typename Pr>
+static cudaError_t launch_batched_t(const BatchLaunch& L, cudaStream_t st) {
+  BatchArgs<Pr> B;
+  B.ctxs = static_cast<const ApcgCtx<Pr>*>(L.ctxs);
   B.queue = L.queue;
   B.qoff = L.qoff;
   B.heads = L.heads;
@@ -772,25 +857,31 @@ cudaError_t apcg_launch_batched(const BatchLaunch& L, cudaStream_t st) {
   B.spin_limit = L.spin_limit;
   B.bctrl = L.bctrl;
   void* args[] = {&B};
-  return cudaLaunchCooperativeKernel((const void*)k_apcg_batched<double>, dim3(L.ctas), dim3(TPB), args,
+  return cudaLaunchCooperativeKernel((const void*)k_apcg_batched<Pr>, dim3(L.ctas), dim3(TPB), args,
                                      apcg_smem_bytes(L.kmax), st);
 }
 
-template <typename T>
+cudaError_t apcg_launch_batched(const BatchLaunch& L, int prec, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  KRS_DISPATCH(prec, e = launch_batched_t<PR>(L, st));
+  return e;
+}
+
+template <typename Pr>
 static cudaError_t launch_phases_t(const IterArgs& a, int j0, int j1, cudaStream_t st, int64_t* launches) {
-  ApcgCtx<T> c = make_ctx<T>(a);
+  ApcgCtx<Pr> c = make_ctx<Pr>(a);
   const size_t sm = apcg_smem_bytes(a.kmax);
   for (int j = j0; j < j1; j++) {
-    k_phase1<T><<<a.P, TPB, sm, st>>>(c, j);
-    k_phase2<T><<<a.P, TPB, sm, st>>>(c, j);
-    k_phase3<T><<<a.P, TPB, sm, st>>>(c, j);
+    k_phase1<Pr><<<a.P, TPB, sm, st>>>(c, j);
+    k_phase2<Pr><<<a.P, TPB, sm, st>>>(c, j);
+    k_phase3<Pr><<<a.P, TPB, sm, st>>>(c, j);
     if (a.nc > SMALL_NC) {
-      k_phase4<T><<<a.P, TPB, sm, st>>>(c, j);
+      k_phase4<Pr><<<a.P, TPB, sm, st>>>(c, j);
       *launches += 1;
     }
-    k_phase5<T><<<a.P, TPB, sm, st>>>(c, j);
-    k_phase6<T><<<a.P, TPB, sm, st>>>(c, j);
-    k_phase7<T><<<a.P, TPB, sm, st>>>(c, j);
+    k_phase5<Pr><<<a.P, TPB, sm, st>>>(c, j);
+    k_phase6<Pr><<<a.P, TPB, sm, st>>>(c, j);
+    k_phase7<Pr><<<a.P, TPB, sm, st>>>(c, j);
     *launches += 6;
   }
   return cudaGetLastError();
@@ -798,7 +889,9 @@ static cudaError_t launch_phases_t(const IterArgs& a, int j0, int j1, cudaStream
 
 // Launch the phases of iterations [j0, j1) (kernels mode).
 cudaError_t apcg_launch_phases(const IterArgs& a, int j0, int j1, cudaStream_t st, int64_t* launches) {
-  return a.fp32 ? launch_phases_t<float>(a, j0, j1, st, launches) : launch_phases_t<double>(a, j0, j1, st, launches);
+  cudaError_t e = cudaSuccess;
+  KRS_DISPATCH(a.prec, e = launch_phases_t<PR>(a, j0, j1, st, launches));
+  return e;
 }
 
 }  // namespace krs

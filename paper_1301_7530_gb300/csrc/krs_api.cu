@@ -138,27 +138,75 @@ static krs_status ensure_cap_c(krs_seq* s, int need) {
   return KRS_OK;
 }
 
-// direction storage and everything sized by the iteration limit
+// scalar arrays of the iteration (alpha, gamma, rho, g) for `need` iterations; the first
+// `keep` iterations' values are kept
+static krs_status ensure_scalars(krs_seq* s, int need, int keep) {
+  if (need <= s->cap_sc) return KRS_OK;
+  const int cap = (int)round_up(need, 32);
+  double *al = nullptr, *ga = nullptr, *rh = nullptr, *gf = nullptr;
+  KRS_TRY(alloc_n(s, &al, cap));
+  KRS_TRY(alloc_n(s, &ga, cap));
+  KRS_TRY(alloc_n(s, &rh, cap + 1));
+  KRS_TRY(alloc_n(s, &gf, cap));
+  if (keep > s->cap_sc) keep = s->cap_sc;
+  if (keep > 0) {
+    KRS_CUDA(cudaMemcpyAsync(al, s->alpha, sizeof(double) * keep, cudaMemcpyDeviceToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(ga, s->gamma, sizeof(double) * keep, cudaMemcpyDeviceToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(rh, s->rho, sizeof(double) * (keep + 1), cudaMemcpyDeviceToDevice, s->stream));
+  }
+  dev_free(s, s->alpha);
+  dev_free(s, s->gamma);
+  dev_free(s, s->rho);
+  dev_free(s, s->gfull);
+  s->alpha = al;
+  s->gamma = ga;
+  s->rho = rh;
+  s->gfull = gf;
+  s->cap_sc = cap;
+  return KRS_OK;
+}
+
+// FP64 direction storage (W, AW, Z) and the scalars for max_iter iterations
 static krs_status ensure_cap_w(krs_seq* s, int max_iter) {
   const int need = max_iter + 1;
+  KRS_TRY(ensure_scalars(s, need, 0));
   if (need <= s->cap_w) return KRS_OK;
   int cap = (int)round_up(need, 32);
   dev_free(s, s->W);
   dev_free(s, s->AW);
   dev_free(s, s->Z);
-  dev_free(s, s->alpha);
-  dev_free(s, s->gamma);
-  dev_free(s, s->rho);
-  dev_free(s, s->gfull);
   s->W = s->AW = s->Z = nullptr;
   KRS_TRY(alloc_n(s, &s->W, (size_t)cap * s->ld));
   KRS_TRY(alloc_n(s, &s->AW, (size_t)cap * s->ld));
   KRS_TRY(alloc_n(s, &s->Z, (size_t)cap * s->ld));
-  KRS_TRY(alloc_n(s, &s->alpha, cap));
-  KRS_TRY(alloc_n(s, &s->gamma, cap));
-  KRS_TRY(alloc_n(s, &s->rho, cap + 1));
-  KRS_TRY(alloc_n(s, &s->gfull, cap));
   s->cap_w = cap;
+  return KRS_OK;
+}
+
+// FP32 direction storage (W32, AW32, Z32) for `need` columns and the scalars; the first
+// `keep` columns / iterations are kept
+static krs_status ensure_w32(krs_seq* s, int need, int keep) {
+  KRS_TRY(ensure_scalars(s, need, keep));
+  if (need <= s->cap_w32) return KRS_OK;
+  const int cap = (int)round_up(need, 32);
+  float *W = nullptr, *AW = nullptr, *Z = nullptr;
+  KRS_TRY(alloc_n(s, &W, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &AW, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &Z, (size_t)cap * s->ld));
+  if (keep > s->cap_w32) keep = s->cap_w32;
+  if (keep > 0) {
+    const size_t vb = sizeof(float) * (size_t)keep * s->ld;
+    KRS_CUDA(cudaMemcpyAsync(W, s->W32, vb, cudaMemcpyDeviceToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(AW, s->AW32, vb, cudaMemcpyDeviceToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(Z, s->Z32, vb, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  dev_free(s, s->W32);
+  dev_free(s, s->AW32);
+  dev_free(s, s->Z32);
+  s->W32 = W;
+  s->AW32 = AW;
+  s->Z32 = Z;
+  s->cap_w32 = cap;
   return KRS_OK;
 }
 
@@ -397,6 +445,8 @@ krs_status krs_release(krs_seq_t s, int32_t what) {
     drop(s->W); drop(s->AW); drop(s->Z);
     drop(s->alpha); drop(s->gamma); drop(s->rho); drop(s->gfull);
     s->cap_w = 0;
+    s->cap_sc = 0;
+    drop(s->q64);
     drop(s->vpart); drop(s->gpart); drop(s->part); drop(s->tfull); drop(s->sfull);
     s->vpart_P = 0;
     s->vld = 0;
@@ -479,7 +529,8 @@ krs_status krs_last_vectors(krs_seq_t s, int32_t which, double* out) {
   if (!out) return fail(KRS_ERR_INVALID_ARG, "NULL output");
   KRS_CUDA(cudaSetDevice(s->device));
   const double* src = which == 0 ? s->W : (which == 1 ? s->AW : s->Z);
-  if (!src) return fail(KRS_ERR_INVALID_ARG, "the last solve stored no FP64 vectors (mixed precision)");
+  if (!src || s->last_prec != KRS_FP64)
+    return fail(KRS_ERR_INVALID_ARG, "the last solve stored no FP64 vectors (mixed precision)");
   const bool dv = is_device_ptr(out);
   KRS_CUDA(cudaMemcpy2DAsync(out, sizeof(double) * s->n, src, sizeof(double) * s->ld, sizeof(double) * s->n, m,
                              dv ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
@@ -497,7 +548,7 @@ krs_status krs::validate_policy(const krs_policy* p) {
   if (p->recycle < 0 || p->recycle > 2) return fail(KRS_ERR_INVALID_ARG, "bad recycle %d", p->recycle);
   if (p->precond < 0 || p->precond > 2) return fail(KRS_ERR_INVALID_ARG, "bad precond %d", p->precond);
   if (p->reorth < 0 || p->reorth > 1) return fail(KRS_ERR_INVALID_ARG, "bad reorth %d", p->reorth);
-  if (p->precision != KRS_FP64 && p->precision != KRS_MIXED_IR)
+  if (p->precision != KRS_FP64 && p->precision != KRS_MIXED_IR && p->precision != KRS_MIXED_PROJ)
     return fail(KRS_ERR_INVALID_ARG, "bad precision %d", p->precision);
   if (!(p->inner_tol == p->inner_tol) || p->inner_tol >= 1.0) return fail(KRS_ERR_INVALID_ARG, "inner_tol must be < 1");
   if (p->cap_mode < 0 || p->cap_mode > 1) return fail(KRS_ERR_INVALID_ARG, "bad cap_mode %d", p->cap_mode);
@@ -581,30 +632,7 @@ static krs_status ensure_mixed(krs_seq* s, int max_iter, int64_t nnzb) {
     s->vals32_cap = nnzb;
     s->vals32_valid = false;
   }
-  const int needw = max_iter + 1;
-  if (needw > s->cap_w32) {
-    const int cap = (int)round_up(needw, 32);
-    dev_free(s, s->W32);
-    dev_free(s, s->AW32);
-    dev_free(s, s->Z32);
-    s->W32 = s->AW32 = s->Z32 = nullptr;
-    KRS_TRY(alloc_n(s, &s->W32, (size_t)cap * s->ld));
-    KRS_TRY(alloc_n(s, &s->AW32, (size_t)cap * s->ld));
-    KRS_TRY(alloc_n(s, &s->Z32, (size_t)cap * s->ld));
-    s->cap_w32 = cap;
-    // the scalar arrays (alpha, gamma, rho, g) are shared with the FP64 path
-    KRS_TRY(ensure_cap_w(s, 0));
-    if (s->cap_w < needw) {
-      dev_free(s, s->alpha);
-      dev_free(s, s->gamma);
-      dev_free(s, s->rho);
-      dev_free(s, s->gfull);
-      KRS_TRY(alloc_n(s, &s->alpha, cap));
-      KRS_TRY(alloc_n(s, &s->gamma, cap));
-      KRS_TRY(alloc_n(s, &s->rho, cap + 1));
-      KRS_TRY(alloc_n(s, &s->gfull, cap));
-    }
-  }
+  KRS_TRY(ensure_w32(s, max_iter + 1, 0));
   // C32 / AC32 hold C, then the directions of the earlier inner solves of the same system
   if (s->cap_c + s->cap_w32 > s->cap_c32) {
     const int cap = s->cap_c + s->cap_w32;
@@ -618,6 +646,23 @@ static krs_status ensure_mixed(krs_seq* s, int max_iter, int64_t nnzb) {
     KRS_TRY(alloc_n(s, &s->dinv, (size_t)s->cap_w32));
     s->cap_c32 = cap;
   }
+  return KRS_OK;
+}
+
+// FP32 storage of the FP32-projection precision: directions, copies of C and AC, and the
+// FP64 operator product q
+static krs_status ensure_proj(krs_seq* s, int cap_iter, int nc) {
+  KRS_TRY(ensure_w32(s, cap_iter + 1, 0));
+  const int need = nc > s->cap_c ? nc : s->cap_c;
+  if (need > s->cap_c32) {
+    dev_free(s, s->C32);
+    dev_free(s, s->AC32);
+    s->C32 = s->AC32 = nullptr;
+    KRS_TRY(alloc_n(s, &s->C32, (size_t)need * s->ld));
+    KRS_TRY(alloc_n(s, &s->AC32, (size_t)need * s->ld));
+    s->cap_c32 = need;
+  }
+  if (!s->q64) KRS_TRY(alloc_n(s, &s->q64, s->ld));
   return KRS_OK;
 }
 
@@ -686,7 +731,7 @@ static krs_status run_apcg(krs_seq* s, IterArgs& a, const void* b_in, double tol
 // (FP64 or FP32): selected Ritz vectors written to C[:, nc .. nc + *cnt) (not yet counted in
 // s->nc).  room: how many may be appended.
 static krs_status srks_extract(krs_seq* s, int m, int nc, int room, const krs_policy* p, const double* Z,
-                               const float* Z32, int* cnt, int64_t* launches) {
+                               const float* Z32, int* cnt, int64_t* launches, bool can_grow) {
   *cnt = 0;
   s->last_srks = 1;
   s->last_ritz_m = m;
@@ -703,8 +748,8 @@ static krs_status srks_extract(krs_seq* s, int m, int nc, int room, const krs_po
   s->last_nsel = k;
   if (k <= 0) return KRS_OK;
   if (nc + k > s->cap_c) {
-    if (Z32) return fail(KRS_ERR_INVALID_ARG, "internal: augmentation capacity not reserved");
-    KRS_TRY(ensure_cap_c(s, nc + k));  // FP64 path: nothing else uses C, AC, G^-1 now
+    if (!can_grow) return fail(KRS_ERR_INVALID_ARG, "internal: augmentation capacity not reserved");
+    KRS_TRY(ensure_cap_c(s, nc + k));  // one APCG solve: nothing else uses C, AC, G^-1 now
   }
   const size_t wneed = eigvecs_work_doubles(m, k) + (size_t)m * k * 2;
   dev_free(s, s->eigwork);
@@ -748,6 +793,9 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   s->last_nsel = 0;
   int64_t& launches = ss->launches;
   const bool mixed = p->precision == KRS_MIXED_IR;
+  const bool proj = p->precision == KRS_MIXED_PROJ;
+  const int prec = mixed ? 1 : (proj ? 2 : 0);
+  s->last_prec = p->precision;
   KRS_CUDA(cudaSetDevice(s->device));
   KRS_CUDA(cudaEventRecord(s->ev[0], s->stream));
 
@@ -788,6 +836,9 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   if (mixed) {
     KRS_TRY(ensure_cap_c(s, nc + room));
     KRS_TRY(ensure_mixed(s, p->max_iter, A->nnzb));
+  } else if (proj) {
+    KRS_TRY(ensure_cap_c(s, nc));
+    KRS_TRY(ensure_proj(s, cap_iter, nc));
   } else {
     KRS_TRY(ensure_cap_c(s, nc));
     KRS_TRY(ensure_cap_w(s, cap_iter));
@@ -795,9 +846,9 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   // largest column count a tall-skinny phase sees (mixed: C plus earlier inner directions)
   const int kmax = mixed ? nc + p->max_iter + 1 : ((nc > cap_iter + 1) ? nc : cap_iter + 1);
   ss->kmax = kmax;
-  KRS_CUDA(apcg_prepare_attributes(kmax, mixed));
+  KRS_CUDA(apcg_prepare_attributes(kmax, prec));
   int bps = 0;
-  KRS_CUDA(apcg_max_coresident(kmax, mixed, &bps));
+  KRS_CUDA(apcg_max_coresident(kmax, prec, &bps));
   if (bps < 1) return fail(KRS_ERR_CUDA, "persistent kernel cannot be resident (kmax %d)", kmax);
   ss->bps = bps;
   int P = 0, npc = 0;
@@ -840,6 +891,13 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
     }
   }
 
+  // ---- FP32 copies of C and AC for the projection
+  if (proj && nc > 0) {
+    KRS_CUDA(launch_d2f(s->C, s->C32, (int64_t)nc * s->ld, s->stream));
+    KRS_CUDA(launch_d2f(s->AC, s->AC32, (int64_t)nc * s->ld, s->stream));
+    launches += 2;
+  }
+
   // ---- FP32 copies for the inner solves
   if (mixed) {
     if (!s->vals32_valid) {
@@ -865,7 +923,7 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   a.n = s->n; a.ld = s->ld; a.nbr = s->nbr; a.npc = npc; a.P = P;
   a.nc = nc; a.nc_dense = nc; a.dinv = s->dinv;
   a.ldg = s->cap_c; a.max_iter = p->max_iter; a.reorth_full = (p->reorth == KRS_REORTH_FULL);
-  a.precond = p->precond; a.kmax = kmax; a.spin_limit = s->spin_limit; a.fp32 = mixed;
+  a.precond = p->precond; a.kmax = kmax; a.spin_limit = s->spin_limit; a.prec = prec;
   a.rp = s->rp_use; a.ci = s->ci_use; a.Ginv = s->Ginv;
   a.alpha = s->alpha; a.gamma = s->gamma; a.rho = s->rho;
   a.tfull = s->tfull; a.sfull = s->sfull; a.gfull = s->gfull;
@@ -873,6 +931,9 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   if (mixed) {
     a.vals = s->vals32; a.minv = s->minv32; a.C = s->C32; a.AC = s->AC32;
     a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.x = s->x32; a.r = s->r32; a.u = s->u32;
+  } else if (proj) {
+    a.vals = s->vals_use; a.minv = s->minv; a.C = s->C32; a.AC = s->AC32; a.Ci = s->C; a.ACi = s->AC;
+    a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.x = s->x; a.r = s->r; a.u = s->u; a.q = s->q64;
   } else {
     a.vals = s->vals_use; a.minv = s->minv; a.C = s->C; a.AC = s->AC;
     a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.x = s->x; a.r = s->r; a.u = s->u;
@@ -883,7 +944,7 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
 
 krs_status krs::seq_begin(krs_seq* s, const krs_bsr* A, const double* b, double tol, const krs_policy* p,
                           int cap_iter, SolveState* ss) {
-  if (p->precision != KRS_FP64) return fail(KRS_ERR_INVALID_ARG, "internal: seq_begin is the FP64 path");
+  if (p->precision == KRS_MIXED_IR) return fail(KRS_ERR_INVALID_ARG, "internal: seq_begin runs one APCG solve");
   ss->tol = tol;
   KRS_TRY(seq_setup(s, A, b, p, cap_iter, ss));
   KRS_TRY(run_init(s, ss->a, s->b, tol, &ss->bb, &ss->rr0, &ss->launches));
@@ -891,37 +952,27 @@ krs_status krs::seq_begin(krs_seq* s, const krs_bsr* A, const double* b, double 
   return KRS_OK;
 }
 
-krs_status krs::seq_grow_directions(krs_seq* s, int cap_iter, int keep) {
+krs_status krs::seq_grow_directions(krs_seq* s, int cap_iter, int keep, int prec) {
   const int need = cap_iter + 1;
+  if (prec == KRS_MIXED_PROJ) return ensure_w32(s, need, keep);
+  KRS_TRY(ensure_scalars(s, need, keep));
   if (need <= s->cap_w) return KRS_OK;
   const int cap = (int)round_up(need, 32);
-  double *W = nullptr, *AW = nullptr, *Z = nullptr, *al = nullptr, *ga = nullptr, *rh = nullptr, *gf = nullptr;
+  double *W = nullptr, *AW = nullptr, *Z = nullptr;
   KRS_TRY(alloc_n(s, &W, (size_t)cap * s->ld));
   KRS_TRY(alloc_n(s, &AW, (size_t)cap * s->ld));
   KRS_TRY(alloc_n(s, &Z, (size_t)cap * s->ld));
-  KRS_TRY(alloc_n(s, &al, cap));
-  KRS_TRY(alloc_n(s, &ga, cap));
-  KRS_TRY(alloc_n(s, &rh, cap + 1));
-  KRS_TRY(alloc_n(s, &gf, cap));
   if (keep > s->cap_w) keep = s->cap_w;
   if (keep > 0) {
     const size_t vb = sizeof(double) * (size_t)keep * s->ld;
     KRS_CUDA(cudaMemcpyAsync(W, s->W, vb, cudaMemcpyDeviceToDevice, s->stream));
     KRS_CUDA(cudaMemcpyAsync(AW, s->AW, vb, cudaMemcpyDeviceToDevice, s->stream));
     KRS_CUDA(cudaMemcpyAsync(Z, s->Z, vb, cudaMemcpyDeviceToDevice, s->stream));
-    KRS_CUDA(cudaMemcpyAsync(al, s->alpha, sizeof(double) * keep, cudaMemcpyDeviceToDevice, s->stream));
-    KRS_CUDA(cudaMemcpyAsync(ga, s->gamma, sizeof(double) * keep, cudaMemcpyDeviceToDevice, s->stream));
-    KRS_CUDA(cudaMemcpyAsync(rh, s->rho, sizeof(double) * (keep + 1), cudaMemcpyDeviceToDevice, s->stream));
   }
   dev_free(s, s->W);
   dev_free(s, s->AW);
   dev_free(s, s->Z);
-  dev_free(s, s->alpha);
-  dev_free(s, s->gamma);
-  dev_free(s, s->rho);
-  dev_free(s, s->gfull);
   s->W = W; s->AW = AW; s->Z = Z;
-  s->alpha = al; s->gamma = ga; s->rho = rh; s->gfull = gf;
   s->cap_w = cap;
   return KRS_OK;
 }
@@ -936,7 +987,23 @@ krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x
     s->last_m = m;
     KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
     ss->add = 0;
-    if (status == KRS_OK) {
+    const bool proj = p->precision == KRS_MIXED_PROJ;
+    if (status == KRS_OK && proj) {
+      // FP32 directions: TRKS appends them as FP64 columns (A C of the new columns is
+      // formed by the next set-up); SRKS forms the Ritz vectors from the FP32 z's
+      if (p->recycle == KRS_RECYCLE_TRKS && m > 0) {
+        const int add = m < ss->room ? m : ss->room;
+        if (add > 0) {
+          KRS_TRY(ensure_cap_c(s, nc + add));
+          k_f2d_cols<<<1216, 256, 0, s->stream>>>(s->W32, s->C + (size_t)nc * s->ld, (int64_t)add * s->ld);
+          KRS_CUDA(cudaGetLastError());
+          launches++;
+        }
+        ss->add = add;
+      } else if (p->recycle == KRS_RECYCLE_SRKS && m >= 2) {
+        KRS_TRY(srks_extract(s, m, nc, ss->room, p, nullptr, s->Z32, &ss->add, &launches, true));
+      }
+    } else if (status == KRS_OK) {
       if (p->recycle == KRS_RECYCLE_TRKS && m > 0) {
         const int add = m < ss->room ? m : ss->room;
         if (add > 0) {
@@ -952,7 +1019,7 @@ krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x
         }
         ss->add = add;
       } else if (p->recycle == KRS_RECYCLE_SRKS && m >= 2) {
-        KRS_TRY(srks_extract(s, m, nc, ss->room, p, s->Z, nullptr, &ss->add, &launches));
+        KRS_TRY(srks_extract(s, m, nc, ss->room, p, s->Z, nullptr, &ss->add, &launches, true));
       }
     }
   }
@@ -1081,7 +1148,7 @@ static krs_status mixed_refine(krs_seq* s, const krs_policy* p, double tol, Solv
           launches++;
         }
       } else if (p->recycle == KRS_RECYCLE_SRKS && m_in >= 2) {
-        KRS_TRY(srks_extract(s, m_in, nc, room, p, nullptr, s->Z32, &add, &launches));
+        KRS_TRY(srks_extract(s, m_in, nc, room, p, nullptr, s->Z32, &add, &launches, false));
       }
       first = false;
     }

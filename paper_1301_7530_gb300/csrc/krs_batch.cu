@@ -236,13 +236,17 @@ static IterArgs group_args(const Entry* e, int64_t vld) {
   const int g = e->g;
   krs_seq* s = e->s;
   IterArgs a = e->ss.a;
-  a.W = s->W; a.AW = s->AW; a.Z = s->Z;
+  if (e->p.precision == KRS_MIXED_PROJ) {
+    a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.q = s->q64;
+  } else {
+    a.W = s->W; a.AW = s->AW; a.Z = s->Z;
+  }
   a.alpha = s->alpha; a.gamma = s->gamma; a.rho = s->rho; a.gfull = s->gfull;
   a.tfull = s->tfull; a.sfull = s->sfull;
   a.P = g;
   int64_t per = (s->nbr + g - 1) / g;
   a.npc = (int)round_up(per, 4);
-  a.jcap = s->cap_w - 1;  // iteration j writes direction column j + 1
+  a.jcap = dir_cap(s, e->p.precision) - 1;  // iteration j writes direction column j + 1
   a.vld = vld;
   a.ctrl = s->ctrl;
   return a;
@@ -304,10 +308,11 @@ static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int quantu
   const int count = (int)queued.size();
   const int nact = (int)act.size();
   int kmax = 1;
-  for (Entry* e : queued) kmax = std::max(kmax, std::max(e->ss.nc, e->s->cap_w));
+  for (Entry* e : queued) kmax = std::max(kmax, std::max(e->ss.nc, dir_cap(e->s, e->p.precision)));
   const int64_t vld = round_up(kmax + 1, 32);
   int bps = 0;
-  KRS_CUDA(apcg_batched_coresident(kmax, &bps));
+  const int prec = queued[0]->p.precision == KRS_MIXED_PROJ ? 2 : 0;
+  KRS_CUDA(apcg_batched_coresident(kmax, prec, &bps));
   if (bps < 1) return failf(KRS_ERR_CUDA, "batch: persistent kernel cannot be resident (kmax %d)", kmax);
   KRS_TRY(ensure_table(b, count));
   KRS_TRY(ensure_groups(b, T, vld));
@@ -370,7 +375,7 @@ static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int quantu
   L.spin_limit = queued[0]->s->spin_limit;
   L.bctrl = b->d_misc + 8;
   KRS_CUDA(cudaEventRecord(b->e0, b->stream));
-  KRS_CUDA(apcg_launch_batched(L, b->stream));
+  KRS_CUDA(apcg_launch_batched(L, prec, b->stream));
   KRS_CUDA(cudaEventRecord(b->e1, b->stream));
   KRS_CUDA(apcg_gather_ctrl(b->d_ctxs, count, b->d_gather, b->stream));
   KRS_CUDA(cudaMemcpyAsync(b->h_gather, b->d_gather, sizeof(int) * 4 * count, cudaMemcpyDeviceToHost, b->stream));
@@ -437,7 +442,16 @@ static krs_status autotune(krs_batch* b, std::vector<Entry*>& run) {
     b->scale = r;
     float ms = 0.f;
     double ri = 0.0;
-    KRS_TRY(launch_once(b, run, kTuneIters, &ms, &ri));
+    std::vector<Entry*> part[2];
+    for (Entry* e : run) part[e->p.precision == KRS_MIXED_PROJ ? 1 : 0].push_back(e);
+    for (auto& pr : part) {
+      if (pr.empty()) continue;
+      float ms1 = 0.f;
+      double ri1 = 0.0;
+      KRS_TRY(launch_once(b, pr, kTuneIters, &ms1, &ri1));
+      ms += ms1;
+      ri += ri1;
+    }
     for (Entry* e : run) e->ss.t_iter = 0.f;
     const double rate = ms > 0.f ? ri / ms : 0.0;
     if (nc < 8) {
@@ -482,10 +496,11 @@ static krs_status grow_full(krs_batch* b) {
   for (Entry* e : b->entries) {
     if (e->ended) continue;
     krs_seq* s = e->s;
-    if (e->j < s->cap_w - 1) continue;
-    int cap = (int)round_up((int64_t)(1.5 * (s->cap_w - 1)) + 1, 32) - 1;
+    const int dc = dir_cap(s, e->p.precision);
+    if (e->j < dc - 1) continue;
+    int cap = (int)round_up((int64_t)(1.5 * (dc - 1)) + 1, 32) - 1;
     if (cap > e->p.max_iter) cap = e->p.max_iter;
-    KRS_TRY(seq_grow_directions(s, cap, e->j + 1));
+    KRS_TRY(seq_grow_directions(s, cap, e->j + 1, e->p.precision));
   }
   return KRS_OK;
 }
@@ -564,7 +579,8 @@ krs_status krs_batch_submit(krs_batch_t b, krs_seq_t s, const krs_bsr* A, const 
   if (s->busy) return failf(KRS_ERR_INVALID_ARG, "the sequence already has a solve in flight");
   if (s->device != b->device) return failf(KRS_ERR_INVALID_ARG, "sequence and batch are on different devices");
   KRS_TRY(validate_policy(p));
-  if (p->precision != KRS_FP64) return failf(KRS_ERR_INVALID_ARG, "batched solves run in FP64 (precision KRS_FP64)");
+  if (p->precision == KRS_MIXED_IR)
+    return failf(KRS_ERR_INVALID_ARG, "batched solves run one APCG solve each (KRS_FP64 or KRS_MIXED_PROJ)");
   if (p->max_iter < 1 || p->max_iter > 16000) return failf(KRS_ERR_INVALID_ARG, "max_iter %d outside [1, 16000]", p->max_iter);
   Entry* e = new (std::nothrow) Entry();
   if (!e) return failf(KRS_ERR_OOM, "host allocation failed");
@@ -609,8 +625,14 @@ krs_status krs_batch_step(krs_batch_t b, int32_t max_done, int64_t* done_tags, i
       if (fresh) KRS_TRY(autotune(b, run));
       if (b->scale == 0) b->scale = 100;
     }
-    float ms = 0.f;
-    KRS_TRY(launch_once(b, run, b->cfg.quantum, &ms));
+    // one launch per precision present (each launch runs one kernel instantiation)
+    std::vector<Entry*> part[2];
+    for (Entry* e : run) part[e->p.precision == KRS_MIXED_PROJ ? 1 : 0].push_back(e);
+    for (auto& pr : part) {
+      if (pr.empty()) continue;
+      float ms = 0.f;
+      KRS_TRY(launch_once(b, pr, b->cfg.quantum, &ms));
+    }
     KRS_TRY(grow_full(b));
   }
   KRS_TRY(finish_ended(b));

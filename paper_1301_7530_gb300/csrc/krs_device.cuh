@@ -200,6 +200,13 @@ __device__ __forceinline__ float4 ld4<false, float>(const float* p) {
   return *reinterpret_cast<const float4*>(p);
 }
 
+// Four consecutive rows of a vector of type TU, as the four-row vector of type T.
+template <typename T, typename TU>
+__device__ __forceinline__ typename VT<T>::V4 load4_as(const TU* p) {
+  const typename VT<TU>::V4 y = *reinterpret_cast<const typename VT<TU>::V4*>(p);
+  return VT<T>::make4((T)y.x, (T)y.y, (T)y.z, (T)y.w);
+}
+
 // ------------------------------------------------------------------------------------
 // Tall-skinny kernels on one CTA's rows [r0, r1) (r0 a multiple of 4).
 // V: column-major, leading dimension ld (multiple of 4), rows >= n padded with zeros.
@@ -209,9 +216,9 @@ __device__ __forceinline__ float4 ld4<false, float>(const float* p) {
 // warps per column split the rows, lanes read consecutive four-row pieces of the column
 // (contiguous per warp load), each warp folds its lanes with one shuffle tree, and the Gw
 // warp partials are summed in a fixed order.  Used by cta_gemv_t.
-template <bool NC, typename T>
+template <bool NC, typename T, typename TU>
 __device__ __forceinline__ void cta_gemv_t_few(const T* __restrict__ V, int64_t ld, int k,
-                                               const T* __restrict__ u, int64_t r0, int64_t r1,
+                                               const TU* __restrict__ u, int64_t r0, int64_t r1,
                                                double* __restrict__ out, double* red) {
   using V4 = typename VT<T>::V4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -222,11 +229,11 @@ __device__ __forceinline__ void cta_gemv_t_few(const T* __restrict__ V, int64_t 
     const int c = warp / Gw, g = warp % Gw;
     const int qa = (int)((int64_t)q4 * g / Gw), qb = (int)((int64_t)q4 * (g + 1) / Gw);
     const T* col = V + (int64_t)c * ld + r0;
-    const T* uu = u + r0;
+    const TU* uu = u + r0;
     T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     for (int q = qa + lane; q < qb; q += 32) {
       const V4 x = ld4<NC, T>(col + 4 * q);
-      const V4 y = *reinterpret_cast<const V4*>(uu + 4 * q);
+      const V4 y = load4_as<T, TU>(uu + 4 * q);
       a0 += x.x * y.x; a1 += x.y * y.y; a2 += x.z * y.z; a3 += x.w * y.w;
     }
     double v = (double)((a0 + a1) + (a2 + a3));
@@ -250,13 +257,13 @@ __device__ __forceinline__ void cta_gemv_t_few(const T* __restrict__ V, int64_t 
 // whatever k is; the groups are combined by a pairwise tree in a fixed order.
 // u: global vector (zero padded past n).  su: shared (ROW_CHUNK values of T); red: shared
 // (TPB doubles).
-template <bool NC, typename T>
+template <bool NC, typename T, typename TU = T>
 __device__ __forceinline__ void cta_gemv_t(const T* __restrict__ V, int64_t ld, int k,
-                                           const T* __restrict__ u, int64_t r0, int64_t r1,
+                                           const TU* __restrict__ u, int64_t r0, int64_t r1,
                                            double* __restrict__ out, T* su, double* red) {
   using V4 = typename VT<T>::V4;
   if (k <= TPB / 32) {
-    cta_gemv_t_few<NC, T>(V, ld, k, u, r0, r1, out, red);
+    cta_gemv_t_few<NC, T, TU>(V, ld, k, u, r0, r1, out, red);
     return;
   }
   const int t = threadIdx.x;
@@ -264,7 +271,7 @@ __device__ __forceinline__ void cta_gemv_t(const T* __restrict__ V, int64_t ld, 
   const bool one_chunk = rows4 <= ROW_CHUNK;
   if (one_chunk) {
     __syncthreads();
-    for (int i = t; i < (int)rows4; i += TPB) su[i] = u[r0 + i];
+    for (int i = t; i < (int)rows4; i += TPB) su[i] = (T)u[r0 + i];
     __syncthreads();
   }
   int cb = 0;
@@ -279,7 +286,7 @@ __device__ __forceinline__ void cta_gemv_t(const T* __restrict__ V, int64_t ld, 
       const int len = (int)kmin64(ROW_CHUNK, rows4 - ch);
       if (!one_chunk) {
         __syncthreads();
-        for (int i = t; i < len; i += TPB) su[i] = u[r0 + ch + i];
+        for (int i = t; i < len; i += TPB) su[i] = (T)u[r0 + ch + i];
         __syncthreads();
       }
       if (g < G) {
@@ -322,9 +329,9 @@ __device__ __forceinline__ void cta_gemv_t(const T* __restrict__ V, int64_t ld, 
 // in blocks of qc with G = ceil(TPB / remaining quads) column groups each (qc = TPB / G),
 // combined by a pairwise tree in a fixed order.  s: shared (k values of T).  red: shared
 // scratch of TPB four-row vectors of T.
-template <bool NC, typename T>
+template <bool NC, typename T, typename TU = T, typename TZ = T>
 __device__ __forceinline__ void cta_gemv_n(const T* __restrict__ V, int64_t ld, int k, const T* s, T sgn,
-                                           const T* u, T* z, int64_t r0, int64_t r1, void* red) {
+                                           const TU* u, TZ* z, int64_t r0, int64_t r1, void* red) {
   using V4 = typename VT<T>::V4;
   const int t = threadIdx.x;
   const int64_t L = r1 - r0;
@@ -384,7 +391,7 @@ __device__ __forceinline__ void cta_gemv_n(const T* __restrict__ V, int64_t ld, 
       const T aa[4] = {a0, a1, a2, a3};
 #pragma unroll
       for (int e = 0; e < 4; e++) {
-        if (row + e < r1) z[row + e] = (u ? u[row + e] : T(0)) + sgn * aa[e];
+        if (row + e < r1) z[row + e] = (TZ)((u ? (T)u[row + e] : T(0)) + sgn * aa[e]);
       }
     }
     qb0 += nq;
@@ -401,11 +408,11 @@ __device__ __forceinline__ void cta_gemv_n(const T* __restrict__ V, int64_t ld, 
 // loads (16-byte loads for FP64 values: 16-byte aligned values and 8-byte aligned col_idx
 // required).  The matrix goes through the non-coherent path; w (written by other CTAs of a
 // persistent kernel) does not.
-template <typename T>
+template <typename T, typename TW = T, typename TQ = T, typename TR = T>
 __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* __restrict__ ci,
-                                         const T* __restrict__ vals, const T* __restrict__ w,
-                                         T* __restrict__ q, const T* __restrict__ r, int64_t r0, int64_t r1,
-                                         double& wq, double& rw) {
+                                         const T* __restrict__ vals, const TW* __restrict__ w,
+                                         TQ* __restrict__ q, const TR* __restrict__ r, int64_t r0, int64_t r1,
+                                         double& wq, double& rw, TW* __restrict__ qw = nullptr) {
   using V2 = typename VT<T>::V2;
   const int64_t n0 = r0 / 3;
   const int64_t items = 2 * ((r1 - r0) / 3);
@@ -423,7 +430,7 @@ __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* 
       if ((k & 1) && k < kend) {  // a leading odd block alone (not aligned for pair loads)
         const int64_t cc = 3 * (int64_t)__ldg(ci + k);
         const T* v = vals + 9 * (int64_t)k;
-        const T w0 = w[cc], w1 = w[cc + 1], w2 = w[cc + 2];
+        const T w0 = (T)w[cc], w1 = (T)w[cc + 1], w2 = (T)w[cc + 2];
         a0 += __ldg(v + 0) * w0; a1 += __ldg(v + 3) * w0; a2 += __ldg(v + 6) * w0;
         a0 += __ldg(v + 1) * w1; a1 += __ldg(v + 4) * w1; a2 += __ldg(v + 7) * w1;
         a0 += __ldg(v + 2) * w2; a1 += __ldg(v + 5) * w2; a2 += __ldg(v + 8) * w2;
@@ -440,8 +447,8 @@ __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* 
 #pragma unroll 1
         for (; k + 2 <= kend; k += 2) {
           const int64_t c0 = 3 * (int64_t)cp.x, c1 = 3 * (int64_t)cp.y;
-          const T x0 = w[c0], x1 = w[c0 + 1], x2 = w[c0 + 2];
-          const T y0 = w[c1], y1 = w[c1 + 1], y2 = w[c1 + 2];
+          const T x0 = (T)w[c0], x1 = (T)w[c0 + 1], x2 = (T)w[c0 + 2];
+          const T y0 = (T)w[c1], y1 = (T)w[c1 + 1], y2 = (T)w[c1 + 2];
           const V2 q0 = p0, q1 = p1, q2 = p2, q3 = p3, q4 = p4, q5 = p5, q6 = p6, q7 = p7, q8 = p8;
           if (k + 4 <= kend) {
             cp = __ldg(reinterpret_cast<const int2*>(ci + k + 2));
@@ -462,7 +469,7 @@ __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* 
       if (k < kend) {  // a trailing single block
         const int64_t cc = 3 * (int64_t)__ldg(ci + k);
         const T* v = vals + 9 * (int64_t)k;
-        const T w0 = w[cc], w1 = w[cc + 1], w2 = w[cc + 2];
+        const T w0 = (T)w[cc], w1 = (T)w[cc + 1], w2 = (T)w[cc + 2];
         a0 += __ldg(v + 0) * w0; a1 += __ldg(v + 3) * w0; a2 += __ldg(v + 6) * w0;
         a0 += __ldg(v + 1) * w1; a1 += __ldg(v + 4) * w1; a2 += __ldg(v + 7) * w1;
         a0 += __ldg(v + 2) * w2; a1 += __ldg(v + 5) * w2; a2 += __ldg(v + 8) * w2;
@@ -475,10 +482,15 @@ __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* 
     if (active && !(it & 1)) {
       const T q0 = a0 + b0, q1 = a1 + b1, q2 = a2 + b2;
       const int64_t row = 3 * node;
-      q[row] = q0;
-      q[row + 1] = q1;
-      q[row + 2] = q2;
-      const T w0 = w[row], w1 = w[row + 1], w2 = w[row + 2];
+      q[row] = (TQ)q0;
+      q[row + 1] = (TQ)q1;
+      q[row + 2] = (TQ)q2;
+      if (qw) {
+        qw[row] = (TW)q0;
+        qw[row + 1] = (TW)q1;
+        qw[row + 2] = (TW)q2;
+      }
+      const T w0 = (T)w[row], w1 = (T)w[row + 1], w2 = (T)w[row + 2];
       wq += (double)w0 * (double)q0;
       wq += (double)w1 * (double)q1;
       wq += (double)w2 * (double)q2;
@@ -493,15 +505,15 @@ __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* 
 
 // u = M^-1 r for one row (Jacobi: minv[row]; block Jacobi: minv[9*node + 3*d + e];
 // identity: r).
-template <typename T>
-__device__ __forceinline__ T precond_row(int kind, const T* __restrict__ minv, const T* __restrict__ r,
-                                         int64_t row) {
-  if (kind == 0) return minv[row] * r[row];
+template <typename T, typename TV = T>
+__device__ __forceinline__ TV precond_row(int kind, const T* __restrict__ minv, const TV* __restrict__ r,
+                                          int64_t row) {
+  if (kind == 0) return (TV)(minv[row] * (T)r[row]);
   if (kind == 1) {
     const int64_t node = row / 3;
     const int d = (int)(row - 3 * node);
     const T* m = minv + 9 * node + 3 * d;
-    return m[0] * r[3 * node] + m[1] * r[3 * node + 1] + m[2] * r[3 * node + 2];
+    return (TV)(m[0] * (T)r[3 * node] + m[1] * (T)r[3 * node + 1] + m[2] * (T)r[3 * node + 2]);
   }
   return r[row];
 }

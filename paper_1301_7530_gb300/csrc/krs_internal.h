@@ -10,10 +10,10 @@ namespace krs {
 // Records msg as the calling thread's krs_last_error() and returns st.
 krs_status set_error(krs_status st, const char* msg);
 
-// Everything the iteration kernels need (device pointers, sizes, partition).  The value
-// arrays (matrix values, M^-1, C, AC, W, AW, Z, x, r, u) are doubles when fp32 is false and
-// floats when it is true (inner solve of the mixed-precision refinement); scalars, partial
-// sums and G^-1 are doubles in both.
+// Everything the iteration kernels need (device pointers, sizes, partition).  The element
+// types of the arrays follow `prec` (matrix values, M^-1, x, r, u: FP32 for prec 1, FP64
+// otherwise; C, AC, W, AW, Z: FP64 for prec 0, FP32 otherwise); scalars, partial sums and
+// G^-1 are doubles in all.
 struct IterArgs {
   int64_t n, ld;
   int nbr, npc, P;
@@ -23,7 +23,8 @@ struct IterArgs {
   int max_iter, reorth_full, precond;
   int jcap;  // iterations j >= jcap do not start in one launch (0: no limit)
   int kmax;  // largest k a tall-skinny phase sees: max(nc, max_iter)
-  bool fp32;
+  int prec;  // 0: FP64; 1: FP32 (mixed-precision inner solves); 2: FP64 recurrences with FP32
+             // projection / reorthogonalisation (C, AC, W, AW, Z in FP32, q in FP64)
   double tol2;
   long long spin_limit;
   const int* rp;
@@ -32,8 +33,11 @@ struct IterArgs {
   const void* minv;
   const void* C;
   const void* AC;
+  const void* Ci;   // C and AC of the init stage (nullptr: C, AC); FP64 for prec 2
+  const void* ACi;
   const double* Ginv;
   void *W, *AW, *Z, *x, *r, *u;
+  void* q;          // prec 2: FP64 product A w_j
   double *alpha, *gamma, *rho;
   double *tfull, *sfull, *gfull;
   double* part;
@@ -73,12 +77,12 @@ struct BatchLaunch {
 size_t apcg_smem_bytes(int kmax);
 size_t apcg_ctx_bytes();
 void apcg_fill_ctx(const IterArgs& a, void* dst);
-cudaError_t apcg_batched_coresident(int kmax, int* blocks_per_sm);
-cudaError_t apcg_launch_batched(const BatchLaunch& L, cudaStream_t st);
+cudaError_t apcg_batched_coresident(int kmax, int prec, int* blocks_per_sm);
+cudaError_t apcg_launch_batched(const BatchLaunch& L, int prec, cudaStream_t st);
 // out[4 p + w], w = CTRL_STATUS, CTRL_DONE, CTRL_M, CTRL_J of the control block of ctxs[p]
 cudaError_t apcg_gather_ctrl(const void* ctxs, int count, int* out, cudaStream_t st);
-cudaError_t apcg_prepare_attributes(int kmax, bool fp32);
-cudaError_t apcg_max_coresident(int kmax, bool fp32, int* blocks_per_sm);
+cudaError_t apcg_prepare_attributes(int kmax, int prec);
+cudaError_t apcg_max_coresident(int kmax, int prec, int* blocks_per_sm);
 cudaError_t apcg_launch_init(const IterArgs& a, const void* b, double* scal, cudaStream_t st, int64_t* launches);
 cudaError_t apcg_launch_persistent(const IterArgs& a, cudaStream_t st, int64_t* launches);
 cudaError_t apcg_launch_phases(const IterArgs& a, int j0, int j1, cudaStream_t st, int64_t* launches);

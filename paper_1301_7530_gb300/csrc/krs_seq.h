@@ -73,7 +73,8 @@ struct krs_seq {
   double* C0 = nullptr;
 
   // Krylov storage and vectors
-  int cap_w = 0;
+  int cap_w = 0;   // columns of the FP64 W, AW, Z
+  int cap_sc = 0;  // iterations the scalar arrays alpha, gamma, rho, gfull hold
   double *W = nullptr, *AW = nullptr, *Z = nullptr;
   double *x = nullptr, *r = nullptr, *u = nullptr, *b = nullptr, *tmp = nullptr;
 
@@ -104,6 +105,8 @@ struct krs_seq {
   float *vals32 = nullptr, *minv32 = nullptr, *C32 = nullptr, *AC32 = nullptr;
   float *W32 = nullptr, *AW32 = nullptr, *Z32 = nullptr;
   float *x32 = nullptr, *r32 = nullptr, *u32 = nullptr, *b32 = nullptr;
+  double* q64 = nullptr;   // FP32-projection precision: the FP64 product A w_j
+  int last_prec = 0;       // precision of the last solve (what its stored directions are)
   double* dinv = nullptr;  // 1/(w, Aw) of the inner directions appended within one system
   int64_t vals32_cap = 0;
   int cap_c32 = 0, cap_w32 = 0;
@@ -163,9 +166,12 @@ struct SolveState {
 // one read of ||b||^2 and ||r_0||^2.  On return ss->need_iter says whether iterations run.
 krs_status seq_begin(krs_seq* s, const krs_bsr* A, const double* b, double tol, const krs_policy* p, int cap_iter,
                      SolveState* ss);
-// Grow the direction storage to at least cap_iter + 1 columns keeping the first `keep`
-// columns of W, AW, Z and the scalars of the first `keep` iterations (between launches).
-krs_status seq_grow_directions(krs_seq* s, int cap_iter, int keep);
+// Grow the direction storage of precision `prec` (FP64 W, AW, Z, or FP32 W32, AW32, Z32
+// for KRS_MIXED_PROJ) to at least cap_iter + 1 columns keeping the first `keep` columns and
+// the scalars of the first `keep` iterations (between launches).
+krs_status seq_grow_directions(krs_seq* s, int cap_iter, int keep, int prec);
+// columns of the direction storage a solve of precision `prec` uses
+inline int dir_cap(const krs_seq* s, int prec) { return prec == KRS_MIXED_PROJ ? s->cap_w32 : s->cap_w; }
 // Stage 3: recycling step (TRKS / SRKS), result copy to x (host or device), true residual,
 // statistics and the commit of the new augmentation space.  `status` and `m` are the
 // iteration loop's outcome.
