@@ -92,6 +92,8 @@ struct ApcgCtx {
   int* gstop;          // batched: the group's drain word (nullptr for one solve)
   const int* idle;     // batched: groups that found their queue empty
   int drain_at;        // batched: drain once this many groups are idle (0: never)
+  int stall_win;       // > 0: end with status 7 when ||r||^2 fell < 4x over stall_win iterations
+  double* rrh;         // ||r_j||^2 history for the stall test
   unsigned long long* bar;
 };
 
@@ -243,6 +245,15 @@ __device__ __forceinline__ int phase3(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm)
   if (rr <= c.tol2) {
     finish(c, 0, j + 1);
     return PH_STOP;
+  }
+  if (c.stall_win > 0) {
+    // the history entry stall_win iterations back was written before many grid barriers,
+    // so every CTA reads the same value and takes the same decision
+    if (c.lb == 0 && threadIdx.x == 0) c.rrh[j] = rr;
+    if (j >= c.stall_win && rr > 0.25 * c.rrh[j - c.stall_win]) {
+      finish(c, 7 /* KRS_STALLED */, j + 1);
+      return PH_STOP;
+    }
   }
   if (j + 1 >= c.max_iter) {
     finish(c, 3 /* KRS_ERR_NO_CONVERGENCE */, j + 1);
@@ -668,6 +679,8 @@ static ApcgCtx<Pr> make_ctx(const IterArgs& a) {
   c.gstop = nullptr;
   c.idle = nullptr;
   c.drain_at = 0;
+  c.stall_win = a.stall_win;
+  c.rrh = a.rrh;
   return c;
 }
 
@@ -686,7 +699,8 @@ static cudaError_t prepare_attributes_t(size_t sm) {
   const void* fns[] = {(const void*)k_apcg_persistent<Pr>, (const void*)k_phase1<Pr>, (const void*)k_phase2<Pr>,
                        (const void*)k_phase3<Pr>, (const void*)k_phase4<Pr>, (const void*)k_phase5<Pr>,
                        (const void*)k_phase6<Pr>, (const void*)k_phase7<Pr>, (const void*)k_gemv_t_part<TC, V>,
-                       (const void*)k_init_xr<TC, V>, (const void*)k_init_z<TC, V, M>};
+                       (const void*)k_init_xr<TC, V>, (const void*)k_init_z<TC, V, M>,
+                       (const void*)k_gemv_t_part<M, V>, (const void*)k_init_xr<M, V>, (const void*)k_init_z<M, V, M>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -735,13 +749,12 @@ cudaError_t apcg_max_coresident(int kmax, int prec, int* blocks_per_sm) {
   return e;
 }
 
-template <typename Pr>
+template <typename Pr, typename TC>
 static cudaError_t launch_init_t(const IterArgs& a, const void* bv, double* scal, cudaStream_t st,
                                  int64_t* launches) {
   using V = typename Pr::V;
   using M = typename Pr::M;
   using A = typename Pr::A;
-  using TC = typename InitTypes<Pr>::TC;
   const size_t sm = apcg_smem_bytes(a.kmax);
   const int k = a.nc;
   const V* b = static_cast<const V*>(bv);
@@ -775,9 +788,14 @@ static cudaError_t launch_init_t(const IterArgs& a, const void* bv, double* scal
 
 // Set-up of x_0, r_0, z_0, w_0, rho_0, ||b||^2, ||r_0||^2 (scal[0..1]).  Counts launches.
 cudaError_t apcg_launch_init(const IterArgs& a, const void* b, double* scal, cudaStream_t st, int64_t* launches) {
-  cudaError_t e = cudaSuccess;
-  KRS_DISPATCH(a.prec, e = launch_init_t<PR>(a, b, scal, st, launches));
-  return e;
+  // PrecP's first pass works from the FP64 C and AC (x_0, r_0 consistent with the FP64
+  // recurrences); restarted passes use the FP32 copies that also hold the earlier passes'
+  // directions
+  if (a.prec == 2)
+    return a.init32 ? launch_init_t<PrecP, float>(a, b, scal, st, launches)
+                    : launch_init_t<PrecP, double>(a, b, scal, st, launches);
+  if (a.prec == 1) return launch_init_t<PrecF, float>(a, b, scal, st, launches);
+  return launch_init_t<PrecD, double>(a, b, scal, st, launches);
 }
 
 template <typename Pr>

@@ -446,7 +446,8 @@ krs_status krs_release(krs_seq_t s, int32_t what) {
     drop(s->alpha); drop(s->gamma); drop(s->rho); drop(s->gfull);
     s->cap_w = 0;
     s->cap_sc = 0;
-    drop(s->q64);
+    drop(s->q64); drop(s->xacc); drop(s->rres); drop(s->rrh);
+    s->rrh_cap = 0;
     drop(s->vpart); drop(s->gpart); drop(s->part); drop(s->tfull); drop(s->sfull);
     s->vpart_P = 0;
     s->vld = 0;
@@ -649,20 +650,33 @@ static krs_status ensure_mixed(krs_seq* s, int max_iter, int64_t nnzb) {
   return KRS_OK;
 }
 
-// FP32 storage of the FP32-projection precision: directions, copies of C and AC, and the
-// FP64 operator product q
-static krs_status ensure_proj(krs_seq* s, int cap_iter, int nc) {
-  KRS_TRY(ensure_w32(s, cap_iter + 1, 0));
-  const int need = nc > s->cap_c ? nc : s->cap_c;
-  if (need > s->cap_c32) {
+// Storage of the FP32-projection precision: FP32 directions for max_iter iterations (all
+// passes of one system), FP32 copies of C and AC followed by room for the earlier passes'
+// directions and their diagonal coarse block, the FP64 product q, the residual history of
+// the stall test, the pass right-hand side and the accumulated solution.
+static krs_status ensure_proj(krs_seq* s, int max_iter) {
+  KRS_TRY(ensure_w32(s, max_iter + 1, 0));
+  if (s->cap_c + s->cap_w32 > s->cap_c32) {
+    const int cap = s->cap_c + s->cap_w32;
     dev_free(s, s->C32);
     dev_free(s, s->AC32);
+    dev_free(s, s->dinv);
     s->C32 = s->AC32 = nullptr;
-    KRS_TRY(alloc_n(s, &s->C32, (size_t)need * s->ld));
-    KRS_TRY(alloc_n(s, &s->AC32, (size_t)need * s->ld));
-    s->cap_c32 = need;
+    s->dinv = nullptr;
+    KRS_TRY(alloc_n(s, &s->C32, (size_t)cap * s->ld));
+    KRS_TRY(alloc_n(s, &s->AC32, (size_t)cap * s->ld));
+    KRS_TRY(alloc_n(s, &s->dinv, (size_t)s->cap_w32));
+    s->cap_c32 = cap;
+  }
+  if (s->rrh_cap < s->cap_w32) {
+    dev_free(s, s->rrh);
+    s->rrh = nullptr;
+    KRS_TRY(alloc_n(s, &s->rrh, (size_t)s->cap_w32));
+    s->rrh_cap = s->cap_w32;
   }
   if (!s->q64) KRS_TRY(alloc_n(s, &s->q64, s->ld));
+  if (!s->xacc) KRS_TRY(alloc_n(s, &s->xacc, s->ld));
+  if (!s->rres) KRS_TRY(alloc_n(s, &s->rres, s->ld));
   return KRS_OK;
 }
 
@@ -837,14 +851,14 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
     KRS_TRY(ensure_cap_c(s, nc + room));
     KRS_TRY(ensure_mixed(s, p->max_iter, A->nnzb));
   } else if (proj) {
-    KRS_TRY(ensure_cap_c(s, nc));
-    KRS_TRY(ensure_proj(s, cap_iter, nc));
+    KRS_TRY(ensure_cap_c(s, nc + room));
+    KRS_TRY(ensure_proj(s, p->max_iter));
   } else {
     KRS_TRY(ensure_cap_c(s, nc));
     KRS_TRY(ensure_cap_w(s, cap_iter));
   }
   // largest column count a tall-skinny phase sees (mixed: C plus earlier inner directions)
-  const int kmax = mixed ? nc + p->max_iter + 1 : ((nc > cap_iter + 1) ? nc : cap_iter + 1);
+  const int kmax = (mixed || proj) ? nc + p->max_iter + 1 : ((nc > cap_iter + 1) ? nc : cap_iter + 1);
   ss->kmax = kmax;
   KRS_CUDA(apcg_prepare_attributes(kmax, prec));
   int bps = 0;
@@ -934,6 +948,7 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   } else if (proj) {
     a.vals = s->vals_use; a.minv = s->minv; a.C = s->C32; a.AC = s->AC32; a.Ci = s->C; a.ACi = s->AC;
     a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.x = s->x; a.r = s->r; a.u = s->u; a.q = s->q64;
+    a.stall_win = 16; a.rrh = s->rrh;
   } else {
     a.vals = s->vals_use; a.minv = s->minv; a.C = s->C; a.AC = s->AC;
     a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.x = s->x; a.r = s->r; a.u = s->u;
@@ -944,7 +959,7 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
 
 krs_status krs::seq_begin(krs_seq* s, const krs_bsr* A, const double* b, double tol, const krs_policy* p,
                           int cap_iter, SolveState* ss) {
-  if (p->precision == KRS_MIXED_IR) return fail(KRS_ERR_INVALID_ARG, "internal: seq_begin runs one APCG solve");
+  if (p->precision != KRS_FP64) return fail(KRS_ERR_INVALID_ARG, "internal: seq_begin is the FP64 path");
   ss->tol = tol;
   KRS_TRY(seq_setup(s, A, b, p, cap_iter, ss));
   KRS_TRY(run_init(s, ss->a, s->b, tol, &ss->bb, &ss->rr0, &ss->launches));
@@ -978,7 +993,8 @@ krs_status krs::seq_grow_directions(krs_seq* s, int cap_iter, int keep, int prec
 }
 
 krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x, const krs_policy* p) {
-  const bool mixed = p->precision == KRS_MIXED_IR;
+  // both refinement precisions did their recycling step inside the refinement loop
+  const bool mixed = p->precision == KRS_MIXED_IR || p->precision == KRS_MIXED_PROJ;
   const int nc = ss->nc;
   int64_t& launches = ss->launches;
   krs_solve_stats st{};
@@ -987,23 +1003,7 @@ krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x
     s->last_m = m;
     KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
     ss->add = 0;
-    const bool proj = p->precision == KRS_MIXED_PROJ;
-    if (status == KRS_OK && proj) {
-      // FP32 directions: TRKS appends them as FP64 columns (A C of the new columns is
-      // formed by the next set-up); SRKS forms the Ritz vectors from the FP32 z's
-      if (p->recycle == KRS_RECYCLE_TRKS && m > 0) {
-        const int add = m < ss->room ? m : ss->room;
-        if (add > 0) {
-          KRS_TRY(ensure_cap_c(s, nc + add));
-          k_f2d_cols<<<1216, 256, 0, s->stream>>>(s->W32, s->C + (size_t)nc * s->ld, (int64_t)add * s->ld);
-          KRS_CUDA(cudaGetLastError());
-          launches++;
-        }
-        ss->add = add;
-      } else if (p->recycle == KRS_RECYCLE_SRKS && m >= 2) {
-        KRS_TRY(srks_extract(s, m, nc, ss->room, p, nullptr, s->Z32, &ss->add, &launches, true));
-      }
-    } else if (status == KRS_OK) {
+    if (status == KRS_OK) {
       if (p->recycle == KRS_RECYCLE_TRKS && m > 0) {
         const int add = m < ss->room ? m : ss->room;
         if (add > 0) {
@@ -1100,11 +1100,18 @@ static krs_status mixed_refine(krs_seq* s, const krs_policy* p, double tol, Solv
   const int room = ss->room;
   int64_t& launches = ss->launches;
   int status = KRS_OK, m = 0, outer = 0, m_first = 0, add = 0;
-  const double inner_tol = p->inner_tol > 0.0 ? p->inner_tol : 0.1;
+  // KRS_MIXED_IR: FP32 passes on r32, x accumulated in s->x.  KRS_MIXED_PROJ: FP64-recurrence
+  // passes on the FP64 residual rres, each pass's correction in s->x, the sum in s->xacc.
+  const bool pp = p->precision == KRS_MIXED_PROJ;
+  double* xtot = pp ? s->xacc : s->x;
+  double* rout = pp ? s->rres : s->r;
+  float* r32out = pp ? nullptr : s->b32;
+  const void* rhs_in = pp ? (const void*)s->rres : (const void*)s->b32;
+  const double inner_tol = pp ? 0.0 : (p->inner_tol > 0.0 ? p->inner_tol : 0.1);
   const int max_outer = p->max_outer > 0 ? p->max_outer : 30;
-  KRS_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * s->ld, s->stream));
+  KRS_CUDA(cudaMemsetAsync(xtot, 0, sizeof(double) * s->ld, s->stream));
   // r = b - A*0 = b (FP64), r32 = (float) b, rr = ||b||^2
-  KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->r, s->b32,
+  KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, xtot, s->b, s->tmp, rout, r32out,
                                s->part, s->scal + 4, s->stream));
   launches += 3;
   KRS_CUDA(cudaMemcpyAsync(s->h_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -1127,10 +1134,11 @@ static krs_status mixed_refine(krs_seq* s, const krs_policy* p, double tol, Solv
     a.max_iter = p->max_iter - m;
     int st_in = KRS_OK, m_in = 0;
     double bb_in = 0.0;
-    KRS_TRY(run_apcg(s, a, s->b32, tin, p->exec, &st_in, &m_in, &bb_in, &ss->t_iter, &launches));
-    // An FP32 breakdown ((w, Aw) <= 0 or (r, z) <= 0) after some progress only ends this
-    // inner solve: its iterate and directions up to there are valid, and the FP64 outer
-    // residual decides whether refinement still advances.
+    KRS_TRY(run_apcg(s, a, rhs_in, tin, p->exec, &st_in, &m_in, &bb_in, &ss->t_iter, &launches));
+    // An FP32 breakdown ((w, Aw) <= 0 or (r, z) <= 0) after some progress, or a stalled
+    // residual, only ends this pass: its iterate and directions up to there are valid, and
+    // the FP64 outer residual decides whether refinement still advances.
+    if (st_in == KRS_STALLED) st_in = KRS_OK;
     if (st_in != KRS_OK && st_in != KRS_ERR_NO_CONVERGENCE && !(st_in == KRS_ERR_NOT_SPD && m_in > 0)) {
       status = st_in;
       break;
@@ -1164,10 +1172,16 @@ static krs_status mixed_refine(krs_seq* s, const krs_policy* p, double tol, Solv
       KRS_CUDA(cudaGetLastError());
       launches++;
       a.nc = nct + m_in;
+      if (pp) {  // the earlier passes' directions exist in FP32 only: later inits read C32, AC32
+        a.init32 = true;
+        a.Ci = nullptr;
+        a.ACi = nullptr;
+      }
     }
-    // x += d (FP64), r = b - A x (FP64), next inner right-hand side r32 = (float) r
-    KRS_CUDA(launch_add_f2d(s->x, s->x32, s->n, s->stream));
-    KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->r, s->b32,
+    // x += d (FP64), r = b - A x (FP64), next pass's right-hand side (r32 = (float) r)
+    if (pp) KRS_CUDA(launch_add_d(xtot, s->x, s->n, s->stream));
+    else KRS_CUDA(launch_add_f2d(xtot, s->x32, s->n, s->stream));
+    KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, xtot, s->b, s->tmp, rout, r32out,
                                  s->part, s->scal + 4, s->stream));
     launches += 4;
     KRS_CUDA(cudaMemcpyAsync(s->h_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -1181,6 +1195,8 @@ static krs_status mixed_refine(krs_seq* s, const krs_policy* p, double tol, Solv
     }
     rr = rr_new;
   }
+  if (pp)  // the result and the true residual are taken from s->x
+    KRS_CUDA(cudaMemcpyAsync(s->x, xtot, sizeof(double) * s->ld, cudaMemcpyDeviceToDevice, s->stream));
   KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
   ss->add = add;
   ss->outer = outer;
@@ -1195,7 +1211,7 @@ static krs_status solve_impl(krs_seq* s, const krs_bsr* A, const double* b, doub
   SolveState ss;
   ss.tol = tol;
   int status = KRS_OK, m = 0;
-  if (p->precision == KRS_MIXED_IR) {
+  if (p->precision == KRS_MIXED_IR || p->precision == KRS_MIXED_PROJ) {
     KRS_TRY(seq_setup(s, A, b, p, p->max_iter, &ss));
     KRS_TRY(mixed_refine(s, p, tol, &ss, &status, &m));
   } else {

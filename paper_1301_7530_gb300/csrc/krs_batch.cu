@@ -579,8 +579,7 @@ krs_status krs_batch_submit(krs_batch_t b, krs_seq_t s, const krs_bsr* A, const 
   if (s->busy) return failf(KRS_ERR_INVALID_ARG, "the sequence already has a solve in flight");
   if (s->device != b->device) return failf(KRS_ERR_INVALID_ARG, "sequence and batch are on different devices");
   KRS_TRY(validate_policy(p));
-  if (p->precision == KRS_MIXED_IR)
-    return failf(KRS_ERR_INVALID_ARG, "batched solves run one APCG solve each (KRS_FP64 or KRS_MIXED_PROJ)");
+  if (p->precision != KRS_FP64) return failf(KRS_ERR_INVALID_ARG, "batched solves run in FP64 (precision KRS_FP64)");
   if (p->max_iter < 1 || p->max_iter > 16000) return failf(KRS_ERR_INVALID_ARG, "max_iter %d outside [1, 16000]", p->max_iter);
   Entry* e = new (std::nothrow) Entry();
   if (!e) return failf(KRS_ERR_OOM, "host allocation failed");

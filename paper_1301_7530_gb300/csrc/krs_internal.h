@@ -7,6 +7,9 @@
 
 namespace krs {
 
+// internal solve status (never returned through the ABI): the residual stopped decreasing
+constexpr int KRS_STALLED = 7;
+
 // Records msg as the calling thread's krs_last_error() and returns st.
 krs_status set_error(krs_status st, const char* msg);
 
@@ -38,6 +41,10 @@ struct IterArgs {
   const double* Ginv;
   void *W, *AW, *Z, *x, *r, *u;
   void* q;          // prec 2: FP64 product A w_j
+  bool init32;      // prec 2: the init stage reads the FP32 C and AC (restarted passes)
+  int stall_win;    // > 0: end the solve when ||r||^2 fell by less than 4x over this many
+                    //      iterations (status KRS_STALLED)
+  double* rrh;      // ||r_j||^2 history (stall_win > 0)
   double *alpha, *gamma, *rho;
   double *tfull, *sfull, *gfull;
   double* part;
@@ -119,9 +126,11 @@ cudaError_t launch_axpy2_dot(int64_t n, const double* alpha, const double* w, co
                              double* r, double* rr, double* part, cudaStream_t st);
 cudaError_t launch_fill_zero(double* p, int64_t count, cudaStream_t st);
 // mixed-precision refinement: dst = (float) src; x += (double) d; r = b - A x (FP64),
-// r32 = (float) r, out = ||r||^2 (ax: n-vector scratch, part: >= 128 doubles)
+// r32 = (float) r (skipped when r32 is NULL), out = ||r||^2 (ax: n-vector scratch, part:
+// >= 128 doubles)
 cudaError_t launch_d2f(const double* src, float* dst, int64_t count, cudaStream_t st);
 cudaError_t launch_add_f2d(double* x, const float* d, int64_t n, cudaStream_t st);
+cudaError_t launch_add_d(double* x, const double* d, int64_t n, cudaStream_t st);  // x += d
 cudaError_t launch_resid_update(int nbr, const int* rp, const int* ci, const double* vals, const double* x,
                                 const double* b, double* ax, double* r, float* r32, double* part, double* out,
                                 cudaStream_t st);

@@ -508,7 +508,7 @@ __global__ void k_resid_update(int64_t n, const double* b, const double* ax, dou
   for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB) {
     const double d = b[i] - ax[i];
     r[i] = d;
-    r32[i] = (float)d;
+    if (r32) r32[i] = (float)d;
     s += d * d;
   }
   s = block_sum(s, red);
@@ -524,6 +524,17 @@ cudaError_t launch_resid_update(int nbr, const int* rp, const int* ci, const dou
   const int blocks = 128;
   k_resid_update<<<blocks, TPB, 0, st>>>(n, b, ax, r, r32, part);
   k_sum_parts<<<1, 32, 0, st>>>(part, blocks, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_add_d(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += d[i];
+}
+
+cudaError_t launch_add_d(double* x, const double* d, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_add_d<<<1216, 256, 0, st>>>(x, d, n);
   return cudaGetLastError();
 }
 

@@ -106,6 +106,10 @@ struct krs_seq {
   float *W32 = nullptr, *AW32 = nullptr, *Z32 = nullptr;
   float *x32 = nullptr, *r32 = nullptr, *u32 = nullptr, *b32 = nullptr;
   double* q64 = nullptr;   // FP32-projection precision: the FP64 product A w_j
+  double* xacc = nullptr;  //   sum of the passes' corrections
+  double* rres = nullptr;  //   FP64 residual b - A xacc (the next pass's right-hand side)
+  double* rrh = nullptr;   //   ||r_j||^2 history of the stall test
+  int rrh_cap = 0;
   int last_prec = 0;       // precision of the last solve (what its stored directions are)
   double* dinv = nullptr;  // 1/(w, Aw) of the inner directions appended within one system
   int64_t vals32_cap = 0;
