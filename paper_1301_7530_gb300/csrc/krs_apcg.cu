@@ -93,6 +93,7 @@ struct ApcgCtx {
   const int* idle;     // batched: groups that found their queue empty
   int drain_at;        // batched: drain once this many groups are idle (0: never)
   int stall_win;       // > 0: end with status 7 when ||r||^2 fell < 4x over stall_win iterations
+  double stall_rr;     //   once ||r||^2 is below this (the test is off on the way down)
   double* rrh;         // ||r_j||^2 history for the stall test
   unsigned long long* bar;
 };
@@ -250,7 +251,7 @@ __device__ __forceinline__ int phase3(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm)
     // the history entry stall_win iterations back was written before many grid barriers,
     // so every CTA reads the same value and takes the same decision
     if (c.lb == 0 && threadIdx.x == 0) c.rrh[j] = rr;
-    if (j >= c.stall_win && rr > 0.25 * c.rrh[j - c.stall_win]) {
+    if (j >= c.stall_win && rr < c.stall_rr && rr > 0.25 * c.rrh[j - c.stall_win]) {
       finish(c, 7 /* KRS_STALLED */, j + 1);
       return PH_STOP;
     }
@@ -680,6 +681,7 @@ static ApcgCtx<Pr> make_ctx(const IterArgs& a) {
   c.idle = nullptr;
   c.drain_at = 0;
   c.stall_win = a.stall_win;
+  c.stall_rr = a.stall_rr;
   c.rrh = a.rrh;
   return c;
 }

@@ -738,6 +738,9 @@ static krs_status run_apcg(krs_seq* s, IterArgs& a, const void* b_in, double tol
   *m = 0;
   KRS_TRY(run_init(s, a, b_in, tol, bb, &rr0, launches));
   if (rr0 <= a.tol2) return KRS_OK;
+  // the stall test watches only the last stretch: below 1e-3 of the pass's first residual
+  // (earlier plateaus of the CG residual are normal)
+  a.stall_rr = 1e-6 * rr0;
   return run_loop(s, a, exec, status, m, t_iter_ms, launches);
 }
 
@@ -948,7 +951,7 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   } else if (proj) {
     a.vals = s->vals_use; a.minv = s->minv; a.C = s->C32; a.AC = s->AC32; a.Ci = s->C; a.ACi = s->AC;
     a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.x = s->x; a.r = s->r; a.u = s->u; a.q = s->q64;
-    a.stall_win = 16; a.rrh = s->rrh;
+    a.stall_win = 32; a.rrh = s->rrh;
   } else {
     a.vals = s->vals_use; a.minv = s->minv; a.C = s->C; a.AC = s->AC;
     a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.x = s->x; a.r = s->r; a.u = s->u;

@@ -43,7 +43,8 @@ struct IterArgs {
   void* q;          // prec 2: FP64 product A w_j
   bool init32;      // prec 2: the init stage reads the FP32 C and AC (restarted passes)
   int stall_win;    // > 0: end the solve when ||r||^2 fell by less than 4x over this many
-                    //      iterations (status KRS_STALLED)
+                    //      iterations (status KRS_STALLED), once it is below stall_rr
+  double stall_rr;
   double* rrh;      // ||r_j||^2 history (stall_win > 0)
   double *alpha, *gamma, *rho;
   double *tfull, *sfull, *gfull;
