@@ -65,6 +65,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "mixed_ir", "mixed_proj"], default="fp64",
+                    help="sequence workload: FP64, FP32 refinement passes, or FP32 projection passes")
+    ap.add_argument("--reselect", choices=["none", "cluster"], default="none",
+                    help="SRKS cluster reselection (Section 4.4, end)")
     ap.add_argument("--workload", choices=["sequence", "batched", "served"], default="sequence",
                     help="sequence: one 32^3 damage sequence (default); batched: many sequences of "
                          "uneven size through the batched engine; served: Poisson requests of many clients")
@@ -261,7 +265,8 @@ def run_krs(args, rank, world, local):
     b_d = torch.as_tensor(b, device=dev)
     x_d = torch.zeros(n, dtype=torch.float64, device=dev)
     pol = B.make_policy("srks", "block_jacobi3", ritz_eps=args.ritz_eps, theta_frac=args.theta_frac,
-                        max_aug=args.max_aug, max_iter=args.max_iter, exec=args.exec)
+                        max_aug=args.max_aug, max_iter=args.max_iter, exec=args.exec, precision=args.precision,
+                        reselect=args.reselect)
     seq = B.Sequence(n, device=local, stream=stream)
 
     def one_step(record=None, lat=None):
@@ -315,7 +320,7 @@ def run_krs(args, rank, world, local):
     achieved_tflops = flops / (t_iter / 1e3) / 1e12
     achieved_gbs = byts / (t_iter / 1e3) / 1e9
     hbm_peak, hbm_kind = measured_peaks()
-    traffic, traffic_alg = profiled_traffic()
+    traffic, traffic_alg = profiled_traffic() if args.precision == "fp64" else (None, None)
     iter_share = t_iter / ms
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -363,9 +368,10 @@ def run_krs(args, rank, world, local):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
             "config": {
                 "workload": f"{args.N}^3 Q1 elasticity damage sequence, {args.systems} systems per step, SRKS",
+                "precision": args.precision, "reselect": args.reselect,
                 "n": n, "nnzb": mats[0].nnzb, "systems_per_step": args.systems, "precond": "block_jacobi3",
                 "recycle": "srks", "ritz_eps": args.ritz_eps, "theta_frac": args.theta_frac,
                 "max_aug": args.max_aug, "tol": TOL, "exec": args.exec, "reorth": "full",
@@ -381,6 +387,8 @@ def run_krs(args, rank, world, local):
                        "t_iter_ms_mean": float(np.mean([s["t_iter_ms"] for s in stats])),
                        "t_recycle_ms_mean": float(np.mean([s["t_recycle_ms"] for s in stats]))},
             "roofline": {"kernel": "k_apcg_persistent", "bound": "alu", "achieved": achieved_tflops,
+                         "flops": "FP64 algorithmic flops of the iterations" if args.precision == "fp64" else
+                                  "FP64-equivalent flops of the iterations (mixed-precision passes)",
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                          "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                          "traffic": traffic, "traffic_alg_bytes": traffic_alg,
