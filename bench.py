@@ -69,6 +69,8 @@ def parse_args():
                     help="sequence workload: FP64, FP32 refinement passes, or FP32 projection passes")
     ap.add_argument("--reselect", choices=["none", "cluster"], default="none",
                     help="SRKS cluster reselection (Section 4.4, end)")
+    ap.add_argument("--problem", choices=["damage", "inclusions"], default="damage",
+                    help="sequence workload: damage sequence (default) or the stiff-inclusion cube")
     ap.add_argument("--workload", choices=["sequence", "batched", "served"], default="sequence",
                     help="sequence: one 32^3 damage sequence (default); batched: many sequences of "
                          "uneven size through the batched engine; served: Poisson requests of many clients")
@@ -107,34 +109,44 @@ def barrier(world):
         dist.barrier()
 
 
-def all_max(v, world):
+def _reduce(v, world, op):
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([float(v)], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def all_max(v, world):
+    """Largest v over the ranks (the job's time is the slowest rank's)."""
+    import torch.distributed as dist
+    return _reduce(v, world, dist.ReduceOp.MAX if world > 1 else None)
 
 
 def all_sum(v, world):
-    if world == 1:
-        return v
-    import torch
+    """Sum of v over the ranks (the job's solves)."""
     import torch.distributed as dist
-    t = torch.tensor([float(v)], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(v, world, dist.ReduceOp.SUM if world > 1 else None)
 
 
 # ----------------------------------------------------------------------------------------
 # workload
 # ----------------------------------------------------------------------------------------
 
-def workload(N, systems, rank):
+def workload(N, systems, rank, problem="damage"):
+    """(matrices, right-hand sides) of the sequence: the damage sequence (one A^(k) per
+    system, fixed b), or the inclusion cube (fixed A with seeded stiff spheres, one traction
+    draw per system)."""
+    if problem == "inclusions":
+        A = P.elasticity_inclusions(N, 3000 + rank)
+        bs = [P.traction_rhs(N, P.random_traction(N, 3100 + 100 * rank + k)) for k in range(systems)]
+        return [A] * systems, bs
     mask, b, gen = P.elasticity_sequence_damage(N, systems, 2000, 2000 + rank)
     mats = [A for _, A in gen]
-    return mats, b
+    return mats, [b] * systems
 
 
 def alg_counts(N, precond_bytes_per_dof, m, nc):
@@ -254,7 +266,8 @@ def run_krs(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    mats, b = workload(args.N, args.systems, rank)
+    mats, bs = workload(args.N, args.systems, rank, args.problem)
+    b = bs[0]
     n = mats[0].n
     # device-resident inputs
     dmats = []
@@ -262,7 +275,7 @@ def run_krs(args, rank, world, local):
         dmats.append({"row_ptr": torch.as_tensor(A.row_ptr, device=dev),
                       "col_idx": torch.as_tensor(A.col_idx, device=dev),
                       "values": torch.as_tensor(A.vals, device=dev).reshape(-1)})
-    b_d = torch.as_tensor(b, device=dev)
+    b_ds = [torch.as_tensor(bk, device=dev) for bk in bs]
     x_d = torch.zeros(n, dtype=torch.float64, device=dev)
     pol = B.make_policy("srks", "block_jacobi3", ritz_eps=args.ritz_eps, theta_frac=args.theta_frac,
                         max_aug=args.max_aug, max_iter=args.max_iter, exec=args.exec, precision=args.precision,
@@ -273,7 +286,8 @@ def run_krs(args, rank, world, local):
         seq.import_space(np.zeros((n, 0)))
         for k, Ad in enumerate(dmats):
             t0 = time.perf_counter()
-            _, st = seq.solve(Ad, b_d, TOL, pol, x=x_d, version=k + 1)
+            ver = 1 if args.problem == "inclusions" else k + 1  # the inclusion cube keeps its A
+            _, st = seq.solve(Ad, b_ds[k], TOL, pol, x=x_d, version=ver)
             if lat is not None:
                 lat.append((time.perf_counter() - t0) * 1e3)
             if st["status"] != 0:
@@ -332,14 +346,15 @@ def run_krs(args, rank, world, local):
             ci = torch.as_tensor(A.col_idx).pin_memory()
             vv = torch.as_tensor(A.vals).pin_memory()
             pin.append(P.BSR3(rp.numpy(), ci.numpy(), vv.numpy()))
-        b_h = torch.as_tensor(b).pin_memory().numpy()
+        b_hs = [torch.as_tensor(bk).pin_memory().numpy() for bk in bs]
         x_h = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
         seq2 = B.Sequence(n, device=local, stream=stream)
 
         def host_step():
             seq2.import_space(np.zeros((n, 0)))
             for k, A in enumerate(pin):
-                _, st = seq2.solve(A, b_h, TOL, pol, x=x_h, version=k + 1)
+                ver = 1 if args.problem == "inclusions" else k + 1
+                _, st = seq2.solve(A, b_hs[k], TOL, pol, x=x_h, version=ver)
                 if st["status"] != 0:
                     raise RuntimeError(f"e2e solve {k} failed: {st}")
 
@@ -353,7 +368,10 @@ def run_krs(args, rank, world, local):
         e_ms = all_max((time.perf_counter() - t0) * 1e3, world)
         e_solves = all_sum(args.e2e_steps * args.systems, world)
         s0 = P.sizes(args.N)
-        h2d = sum(4 * (A.n_block_rows + 1) + 4 * A.nnzb + 72 * A.nnzb + 8 * n for A in mats)
+        if args.problem == "inclusions":  # one A for the whole sequence: uploaded before the timed region
+            h2d = 8 * n * len(mats)
+        else:
+            h2d = sum(4 * (A.n_block_rows + 1) + 4 * A.nnzb + 72 * A.nnzb + 8 * n for A in mats)
         d2h = 8 * n * len(mats)
         e2e = {"value": e_solves / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps, "n": s0["n"]}
@@ -370,7 +388,10 @@ def run_krs(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
             "config": {
-                "workload": f"{args.N}^3 Q1 elasticity damage sequence, {args.systems} systems per step, SRKS",
+                "workload": (f"{args.N}^3 Q1 elasticity damage sequence, {args.systems} systems per step, SRKS"
+                             if args.problem == "damage" else
+                             f"{args.N}^3 Q1 elasticity with stiff spherical inclusions (5 %, contrast 1e3), "
+                             f"{args.systems} traction systems per step, SRKS"),
                 "precision": args.precision, "reselect": args.reselect,
                 "n": n, "nnzb": mats[0].nnzb, "systems_per_step": args.systems, "precond": "block_jacobi3",
                 "recycle": "srks", "ritz_eps": args.ritz_eps, "theta_frac": args.theta_frac,
@@ -427,7 +448,8 @@ def cpu_baseline(mats, b):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    mats, b = workload(args.N, 1, 0)
+    mats, bs = workload(args.N, 1, 0, args.problem)
+    b = bs[0]
     for _ in range(args.warmup):
         oracle_one_solve(mats, b)
     t0 = time.perf_counter()
