@@ -36,23 +36,43 @@ cudaError_t launch_lanczos(int m, const double* alpha, const double* rho, double
   return cudaGetLastError();
 }
 
-// Number of eigenvalues of T (order m, diagonal d, squared off-diagonal e2) below x.
-// Pivots of T - x I = L D L^T; a pivot at or below pivmin counts as negative and is
-// replaced by -pivmin (standard safeguard).
+// Number of eigenvalues of T (order m, diagonal d, squared off-diagonal e2) below x: the
+// number of negative pivots q_i of T - x I = L D L^T.  The pivots are taken as ratios of
+// consecutive leading principal minors, p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2} (p_{-1} = 1),
+// which needs no division: after every step the pair (p_{i-1}, p_i) is rescaled by the power
+// of two that brings |p_i| into [1, 2) (exact), so the minors stay in range.  A pivot at or
+// below pivmin counts as negative, and one within pivmin of zero is replaced by -pivmin.
+// With pivmin >= 2^-900 max(1, max e2) the rescaled p_{i-1} stays below 2^901 / max(1, e2), so
+// no product overflows.  (A division per step made each count a chain of slow FP64
+// divisions on GB300; this chain is one fused multiply-add, one multiply and integer work.)
 __device__ __forceinline__ int sturm_count(int m, const double* d, const double* e2, double x,
                                            double pivmin) {
   int cnt = 0;
-  double q = d[0] - x;
-  if (q <= pivmin) {
+  double a = 1.0;       // p_{i-1}, rescaled
+  double b = d[0] - x;  // p_i, rescaled (p_{-1} = 1, so q_0 = p_0)
+  if (b <= pivmin) {
     cnt++;
-    q = fmin(q, -pivmin);
+    b = fmin(b, -pivmin);
   }
-  for (int i = 1; i < m; i++) {
-    q = (d[i] - x) - e2[i - 1] / q;
-    if (q <= pivmin) {
+  for (int i = 1; i <= m; i++) {
+    // rescale the pair so that |b| is in [1, 2): s = 2^(1023 - biased exponent of b)
+    const long long bits = __double_as_longlong(b);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    const double sc = __longlong_as_double((long long)(2046 - ex) << 52);
+    a *= sc;
+    b *= sc;
+    if (i == m) break;
+    double p = (d[i] - x) * b - e2[i - 1] * a;
+    // q_i = p / b <= pivmin  <=>  p sgn(b) <= pivmin |b|
+    const double ab = fabs(b);
+    const double ps = (b > 0.0) ? p : -p;
+    const double lim = pivmin * ab;
+    if (ps <= lim) {
       cnt++;
-      q = fmin(q, -pivmin);
+      if (ps > -lim) p = -pivmin * b;  // q_i := -pivmin
     }
+    a = b;
+    b = p;
   }
   return cnt;
 }
@@ -94,7 +114,7 @@ __global__ void __launch_bounds__(32) k_bisect(int m, int m1, int L, const doubl
     if (i < order - 1) emax = fmax(emax, e2[i]);
   }
   const double tnorm = fmax(fabs(lo), fabs(hi));
-  const double pivmin = DBL_MIN * fmax(1.0, emax);
+  const double pivmin = 0x1p-900 * fmax(1.0, emax);
   lo -= 2.0 * DBL_EPSILON * tnorm + pivmin;
   hi += 2.0 * DBL_EPSILON * tnorm + pivmin;
   const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (grp * L));
