@@ -45,54 +45,41 @@ cudaError_t launch_lanczos(int m, const double* alpha, const double* rho, double
 // With pivmin >= 2^-900 max(1, max e2) the rescaled p_{i-1} stays below 2^901 / max(1, e2), so
 // no product overflows.  (A division per step made each count a chain of slow FP64
 // divisions on GB300; this chain is one fused multiply-add, one multiply and integer work.)
-// Two such counts at once (points xa and xb): the two recurrences are independent, so
-// their dependent chains overlap in one thread.
-__device__ __forceinline__ void sturm_count2(int m, const double* d, const double* e2, double xa, double xb,
-                                             double pivmin, int& ca, int& cb) {
-  ca = 0;
-  cb = 0;
-  double aa = 1.0, ba = d[0] - xa;
-  double ab = 1.0, bb = d[0] - xb;
-  if (ba <= pivmin) {
-    ca++;
-    ba = fmin(ba, -pivmin);
-  }
-  if (bb <= pivmin) {
-    cb++;
-    bb = fmin(bb, -pivmin);
+__device__ __forceinline__ int sturm_count(int m, const double* d, const double* e2, double x,
+                                           double pivmin) {
+  int cnt = 0;
+  double a = 1.0;       // p_{i-1}, rescaled
+  double b = d[0] - x;  // p_i, rescaled (p_{-1} = 1, so q_0 = p_0)
+  if (b <= pivmin) {
+    cnt++;
+    b = fmin(b, -pivmin);
   }
   for (int i = 1; i <= m; i++) {
-    const double sa = __longlong_as_double((long long)(2046 - (int)((__double_as_longlong(ba) >> 52) & 0x7ff)) << 52);
-    const double sb = __longlong_as_double((long long)(2046 - (int)((__double_as_longlong(bb) >> 52) & 0x7ff)) << 52);
-    aa *= sa;
-    ba *= sa;
-    ab *= sb;
-    bb *= sb;
+    // rescale the pair so that |b| is in [1, 2): s = 2^(1023 - biased exponent of b)
+    const long long bits = __double_as_longlong(b);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    const double sc = __longlong_as_double((long long)(2046 - ex) << 52);
+    a *= sc;
+    b *= sc;
     if (i == m) break;
-    const double di = d[i], ei = e2[i - 1];
-    double pa = (di - xa) * ba - ei * aa;
-    double pb = (di - xb) * bb - ei * ab;
-    const double la = pivmin * fabs(ba), lb = pivmin * fabs(bb);
-    const double qa = (ba > 0.0) ? pa : -pa, qb = (bb > 0.0) ? pb : -pb;
-    if (qa <= la) {
-      ca++;
-      if (qa > -la) pa = -pivmin * ba;
+    double p = (d[i] - x) * b - e2[i - 1] * a;
+    // q_i = p / b <= pivmin  <=>  p sgn(b) <= pivmin |b|
+    const double ab = fabs(b);
+    const double ps = (b > 0.0) ? p : -p;
+    const double lim = pivmin * ab;
+    if (ps <= lim) {
+      cnt++;
+      if (ps > -lim) p = -pivmin * b;  // q_i := -pivmin
     }
-    if (qb <= lb) {
-      cb++;
-      if (qb > -lb) pb = -pivmin * bb;
-    }
-    aa = ba;
-    ba = pa;
-    ab = bb;
-    bb = pb;
+    a = b;
+    b = p;
   }
+  return cnt;
 }
 
 // Multisection over lane groups.  Each eigenvalue (a "job") gets a group of L lanes of a
-// one-warp CTA (L a power of two); every round the L lanes evaluate Sturm counts at 2L
-// interior points of the job's interval (two per lane, interleaved), which shrinks
-// (2L + 1)-fold.  GB300's FP64 pipe
+// one-warp CTA (L a power of two); every round the L lanes evaluate Sturm counts at L
+// interior points of the job's interval, which shrinks (L + 1)-fold.  GB300's FP64 pipe
 // costs the same per warp instruction whatever the number of active lanes, so the cost
 // of a job is rounds x m, and the number of jobs per warp is 32 / L: the launcher picks L
 // so that the warps about fill the SMs (one warp per SM keeps the FP64 pipe of every SM
@@ -132,33 +119,22 @@ __global__ void __launch_bounds__(32) k_bisect(int m, int m1, int L, const doubl
   hi += 2.0 * DBL_EPSILON * tnorm + pivmin;
   const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (grp * L));
   bool done = !active;
-  // invariant: count(lo) <= k < count(hi).  Each lane tests two points per round (points
-  // 2 sub and 2 sub + 1 of the group's 2L), so the interval shrinks (2L + 1)-fold.
-  const double denom = (double)(2 * L + 1);
+  // invariant: count(lo) <= k < count(hi)
   for (int round = 0; round < 400; round++) {
     if (!done) {
       const double width = hi - lo;
       if (width <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) done = true;
     }
     if (!__any_sync(0xffffffffu, !done)) break;
-    const double w = hi - lo;
-    const double xa = lo + w * ((double)(2 * sub + 1) / denom);
-    const double xb = lo + w * ((double)(2 * sub + 2) / denom);
-    int ca = 0, cb = 0;
-    if (!done) sturm_count2(order, d, e2, xa, xb, pivmin, ca, cb);
-    const bool a_up = !done && ca > k, b_up = !done && cb > k;
-    const unsigned above = __ballot_sync(0xffffffffu, a_up || b_up) & gmask;
-    const int fl = above ? (__ffs(above) - 1) - grp * L : L;  // first lane with a point above
-    const bool fl_a = __shfl_sync(0xffffffffu, a_up, grp * L + (fl < L ? fl : 0));
-    const int F = (fl < L) ? 2 * fl + (fl_a ? 0 : 1) : 2 * L;  // first point above (2L: none)
-    const int Fm = F > 0 ? F - 1 : 0;
-    const double xFa = __shfl_sync(0xffffffffu, xa, grp * L + ((F < 2 * L ? F : 0) >> 1));
-    const double xFb = __shfl_sync(0xffffffffu, xb, grp * L + ((F < 2 * L ? F : 0) >> 1));
-    const double xMa = __shfl_sync(0xffffffffu, xa, grp * L + (Fm >> 1));
-    const double xMb = __shfl_sync(0xffffffffu, xb, grp * L + (Fm >> 1));
+    const double x = lo + (hi - lo) * ((double)(sub + 1) / (double)(L + 1));
+    const int c = done ? 0 : sturm_count(order, d, e2, x, pivmin);
+    const unsigned above = __ballot_sync(0xffffffffu, !done && c > k) & gmask;
+    const int first = above ? (__ffs(above) - 1) - grp * L : L;  // first point above, in the group
+    const double xF = __shfl_sync(0xffffffffu, x, grp * L + (first < L ? first : 0));
+    const double xFm = __shfl_sync(0xffffffffu, x, grp * L + (first > 0 ? first - 1 : 0));
     if (!done) {
-      const double nhi = (F < 2 * L) ? ((F & 1) ? xFb : xFa) : hi;
-      const double nlo = (F > 0) ? ((Fm & 1) ? xMb : xMa) : lo;
+      const double nhi = (first < L) ? xF : hi;
+      const double nlo = (first > 0) ? xFm : lo;
       if (nhi == hi && nlo == lo) done = true;  // no representable progress
       lo = nlo;
       hi = nhi;
