@@ -78,16 +78,18 @@ __device__ __forceinline__ int sturm_count(int m, const double* d, const double*
 }
 
 // Multisection over lane groups.  Each eigenvalue (a "job") gets a group of L lanes of a
-// one-warp CTA (L a power of two); every round the L lanes evaluate Sturm counts at L
-// interior points of the job's interval, which shrinks (L + 1)-fold.  GB300's FP64 pipe
-// costs the same per warp instruction whatever the number of active lanes, so the cost
-// of a job is rounds x m, and the number of jobs per warp is 32 / L: the launcher picks L
-// so that the warps about fill the SMs (one warp per SM keeps the FP64 pipe of every SM
-// busy without contention, and a Sturm count is a dependent chain).
+// warp (L a power of two); every round the L lanes evaluate Sturm counts at L interior
+// points of the job's interval, which shrinks (L + 1)-fold.  GB300's FP64 units cost the
+// same per warp instruction whatever the number of active lanes, so the cost of a job is
+// rounds x m and a warp holds 32 / L jobs: the launcher picks L so that the warps about
+// fill one warp per SM sub-partition (four-warp CTAs).
 // Job index q in [0, m + m1): q < m is eigenvalue q (descending) of T_m, else eigenvalue
 // q - m of T_{m1} (leading block).  Output: theta_m[m], theta_m1[m1], descending.
-__global__ void __launch_bounds__(32) k_bisect(int m, int m1, int L, const double* __restrict__ delta,
-                                               const double* __restrict__ eta, double* theta_m, double* theta_m1) {
+constexpr int BISECT_WARPS = 4;  // one warp per SM sub-partition
+
+__global__ void __launch_bounds__(32 * BISECT_WARPS) k_bisect(int m, int m1, int L, const double* __restrict__ delta,
+                                                              const double* __restrict__ eta, double* theta_m,
+                                                              double* theta_m1) {
   extern __shared__ double sh[];
   double* d = sh;
   double* e2 = sh + m;
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(32) k_bisect(int m, int m1, int L, const doubl
   const int lane = threadIdx.x & 31;
   const int per_warp = 32 / L;
   const int grp = lane / L, sub = lane % L;
-  const int job = blockIdx.x * per_warp + grp;
+  const int job = (blockIdx.x * BISECT_WARPS + (int)(threadIdx.x >> 5)) * per_warp + grp;
   const bool active = job < m + m1;
   const int order = !active ? m : (job < m ? m : m1);
   const int idx_desc = !active ? 0 : (job < m ? job : job - m);
@@ -153,16 +155,19 @@ cudaError_t launch_tridiag_eigvals2(int m, int m1, const double* delta, const do
   const int jobs = m + m1;
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // lanes per job: the largest power of two whose warps (32 / L jobs each) still fit the SMs
+  // lanes per job: the largest power of two whose warps (32 / L jobs each) still fit one
+  // warp per SM sub-partition (an FP64 warp instruction occupies its sub-partition's FP64
+  // unit; a lone warp per SM leaves three of them idle)
   int L = 32;
-  while (L > 1 && (int64_t)jobs * L > 32 * (int64_t)sms) L >>= 1;
+  while (L > 1 && (int64_t)jobs * L > 32 * (int64_t)BISECT_WARPS * sms) L >>= 1;
   const int per_warp = 32 / L;
+  const int per_cta = per_warp * BISECT_WARPS;
   const size_t sm = sizeof(double) * (size_t)(2 * m + 1);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute((const void*)k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  k_bisect<<<(jobs + per_warp - 1) / per_warp, 32, sm, st>>>(m, m1, L, delta, eta, theta_m, theta_m1);
+  k_bisect<<<(jobs + per_cta - 1) / per_cta, 32 * BISECT_WARPS, sm, st>>>(m, m1, L, delta, eta, theta_m, theta_m1);
   return cudaGetLastError();
 }
 
