@@ -744,23 +744,27 @@ static krs_status run_apcg(krs_seq* s, IterArgs& a, const void* b_in, double tol
   return run_loop(s, a, exec, status, m, t_iter_ms, launches);
 }
 
-// SRKS extraction (Algorithm 3) from the coefficients of an m-iteration solve and its z's
-// (FP64 or FP32): selected Ritz vectors written to C[:, nc .. nc + *cnt) (not yet counted in
-// s->nc).  room: how many may be appended.
-static krs_status srks_extract(krs_seq* s, int m, int nc, int room, const krs_policy* p, const double* Z,
-                               const float* Z32, int* cnt, int64_t* launches, bool can_grow) {
-  *cnt = 0;
+// SRKS, first half: H_m from the coefficients, the eigenvalues of H_m and H_{m-1}, the
+// selection; the selected count goes to pinned host memory (h_ctrl[16]), valid once the
+// stream has been synchronised.
+static krs_status srks_begin(krs_seq* s, int m, int room, const krs_policy* p, int64_t* launches) {
   s->last_srks = 1;
   s->last_ritz_m = m;
   KRS_TRY(ensure_eig(s, m));
   KRS_CUDA(launch_lanczos(m, s->alpha, s->rho, s->delta, s->eta, s->stream));
   KRS_CUDA(launch_tridiag_eigvals2(m, m - 1, s->delta, s->eta, s->theta_m, s->theta_m1, s->stream));
   KRS_CUDA(launch_srks_select(m, s->theta_m, s->theta_m1, p->ritz_eps, p->theta_frac, p->reselect, room, s->sel,
-                              s->selcount,
-                              s->tsel, s->stream));
+                              s->selcount, s->tsel, s->stream));
   *launches += 3;
   KRS_CUDA(cudaMemcpyAsync(&s->h_ctrl[16], s->selcount, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  return KRS_OK;
+}
+
+// SRKS, second half (after the stream was synchronised): eigenvectors of the selected
+// values and the Ritz vectors, written to C[:, nc .. nc + *cnt) (not yet counted in s->nc).
+static krs_status srks_finish(krs_seq* s, int m, int nc, const double* Z, const float* Z32, int* cnt,
+                              int64_t* launches, bool can_grow) {
+  *cnt = 0;
   const int k = s->h_ctrl[16];
   s->last_nsel = k;
   if (k <= 0) return KRS_OK;
@@ -784,6 +788,17 @@ static krs_status srks_extract(krs_seq* s, int m, int nc, int room, const krs_po
   *launches += 3;
   *cnt = k;
   return KRS_OK;
+}
+
+// SRKS extraction (Algorithm 3) from the coefficients of an m-iteration solve and its z's
+// (FP64 or FP32): selected Ritz vectors written to C[:, nc .. nc + *cnt) (not yet counted in
+// s->nc).  room: how many may be appended.
+static krs_status srks_extract(krs_seq* s, int m, int nc, int room, const krs_policy* p, const double* Z,
+                               const float* Z32, int* cnt, int64_t* launches, bool can_grow) {
+  *cnt = 0;
+  KRS_TRY(srks_begin(s, m, room, p, launches));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  return srks_finish(s, m, nc, Z, Z32, cnt, launches, can_grow);
 }
 
 __global__ void k_recip(const double* __restrict__ src, double* __restrict__ dst, int count) {
@@ -995,18 +1010,25 @@ krs_status krs::seq_grow_directions(krs_seq* s, int cap_iter, int keep, int prec
   return KRS_OK;
 }
 
-krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x, const krs_policy* p) {
+krs_status krs::seq_end_stage(krs_seq* s, SolveState* ss, int status, int m, double* x, const krs_policy* p,
+                              int stage) {
   // both refinement precisions did their recycling step inside the refinement loop
   const bool mixed = p->precision == KRS_MIXED_IR || p->precision == KRS_MIXED_PROJ;
   const int nc = ss->nc;
   int64_t& launches = ss->launches;
-  krs_solve_stats st{};
-  if (!mixed) {
-    // ---- FP64: the recycling step on this solve's W / Z
-    s->last_m = m;
-    KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
-    ss->add = 0;
-    if (status == KRS_OK) {
+  const bool srks = !mixed && status == KRS_OK && p->recycle == KRS_RECYCLE_SRKS && m >= 2;
+  if (stage == 1) {
+    if (!mixed) {
+      s->last_m = m;
+      KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
+      ss->add = 0;
+      if (srks) KRS_TRY(srks_begin(s, m, ss->room, p, &launches));
+    }
+    return KRS_OK;
+  }
+  if (stage == 2) {
+    if (!mixed && status == KRS_OK) {
+      // ---- FP64: the recycling step on this solve's W / Z
       if (p->recycle == KRS_RECYCLE_TRKS && m > 0) {
         const int add = m < ss->room ? m : ss->room;
         if (add > 0) {
@@ -1021,28 +1043,28 @@ krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x
           }
         }
         ss->add = add;
-      } else if (p->recycle == KRS_RECYCLE_SRKS && m >= 2) {
-        KRS_TRY(srks_extract(s, m, nc, ss->room, p, s->Z, nullptr, &ss->add, &launches, true));
+      } else if (srks) {
+        KRS_TRY(srks_finish(s, m, nc, s->Z, nullptr, &ss->add, &launches, true));
       }
     }
+    // ---- result and true residual
+    const bool x_dev = is_device_ptr(x);
+    KRS_CUDA(cudaMemcpyAsync(x, s->x, sizeof(double) * s->n, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             s->stream));
+    KRS_CUDA(launch_true_residual(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->part, s->scal + 2,
+                                  s->stream));
+    launches += 3;
+    if (!mixed) {
+      KRS_CUDA(launch_norm2(s->n, s->r, s->part, s->scal + 3, s->stream));
+      launches += 2;
+    }
+    KRS_CUDA(cudaMemcpyAsync(s->h_scal, s->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    return KRS_OK;
   }
+  // stage 3 (the stream has been synchronised): statistics and the commit
+  krs_solve_stats st{};
   const int add = ss->add;
   const double bb = ss->bb;
-
-  // ---- result and true residual
-  const bool x_dev = is_device_ptr(x);
-  KRS_CUDA(cudaMemcpyAsync(x, s->x, sizeof(double) * s->n, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                           s->stream));
-  KRS_CUDA(launch_true_residual(s->nbr, s->rp_use, s->ci_use, s->vals_use, s->x, s->b, s->tmp, s->part, s->scal + 2,
-                                s->stream));
-  launches += 3;
-  if (!mixed) {
-    KRS_CUDA(launch_norm2(s->n, s->r, s->part, s->scal + 3, s->stream));
-    launches += 2;
-  }
-  KRS_CUDA(cudaMemcpyAsync(s->h_scal, s->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  KRS_CUDA(cudaStreamSynchronize(s->stream));
-
   st.status = status;
   st.m = m;
   st.n_c = nc;
@@ -1066,7 +1088,6 @@ krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x
                                                   : "solve did not complete";
     return fail((krs_status)status, "%s (m = %d)", what, m);
   }
-
   // ---- commit the recycled columns
   s->nc = nc + add;
   if (p->cap_mode == KRS_CAP_RESTART && p->max_aug > 0 && s->nc >= p->max_aug) {
@@ -1079,7 +1100,7 @@ krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x
     s->ginv_valid = false;
   }
   KRS_CUDA(cudaEventRecord(s->ev[3], s->stream));
-  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  KRS_CUDA(cudaEventSynchronize(s->ev[3]));
   float t1 = 0.f, t3 = 0.f, tt = 0.f;
   cudaEventElapsedTime(&t1, s->ev[0], s->ev[1]);
   cudaEventElapsedTime(&t3, s->ev[2], s->ev[3]);
@@ -1093,6 +1114,14 @@ krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x
   st.kernel_launches = launches;
   s->st = st;
   return KRS_OK;
+}
+
+krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x, const krs_policy* p) {
+  KRS_TRY(seq_end_stage(s, ss, status, m, x, p, 1));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  KRS_TRY(seq_end_stage(s, ss, status, m, x, p, 2));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  return seq_end_stage(s, ss, status, m, x, p, 3);
 }
 
 // mixed precision: FP64 refinement around FP32 inner APCG solves

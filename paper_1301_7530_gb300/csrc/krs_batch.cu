@@ -113,8 +113,11 @@ struct krs_batch {
   int h_cap = 0;
 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t post[4] = {nullptr, nullptr, nullptr, nullptr};  // finishing streams
   krs_batch_stats st{};
 };
+
+constexpr int kPostStreams = 4;
 
 // ------------------------------------------------------------------------------------
 // engine memory
@@ -472,19 +475,33 @@ static krs_status autotune(krs_batch* b, std::vector<Entry*>& run) {
   return KRS_OK;
 }
 
-// Finish ended entries: recycling, result, statistics; they leave the engine.
+// Finish ended entries: recycling, result, statistics; they leave the engine.  The stages
+// of every ended solve are enqueued together, round-robin over a few streams, with one
+// synchronisation per stage instead of two per solve, so the small between-solve kernels
+// of different solves run concurrently.
 static krs_status finish_ended(krs_batch* b) {
-  std::vector<Entry*> keep;
-  for (Entry* e : b->entries) {
-    if (!e->ended) {
-      keep.push_back(e);
-      continue;
+  std::vector<Entry*> keep, done;
+  for (Entry* e : b->entries) (e->ended ? done : keep).push_back(e);
+  if (done.empty()) return KRS_OK;
+  // the solves' last kernels ran on the engine's stream
+  KRS_CUDA(cudaStreamSynchronize(b->stream));
+  std::vector<krs_status> res(done.size(), KRS_OK);
+  for (size_t i = 0; i < done.size(); i++) done[i]->s->stream = b->post[i % kPostStreams];
+  for (int stage = 1; stage <= 3; stage++) {
+    for (size_t i = 0; i < done.size(); i++) {
+      Entry* e = done[i];
+      if (res[i] != KRS_OK) continue;
+      res[i] = seq_end_stage(e->s, &e->ss, e->status, e->m, e->x_out, &e->p, stage);
     }
-    krs_status st = seq_end(e->s, &e->ss, e->status, e->m, e->x_out, &e->p);
-    if (st != KRS_OK && e->s->st.status == 0) e->s->st.status = st;
+    if (stage < 3)
+      for (int k = 0; k < kPostStreams; k++) KRS_CUDA(cudaStreamSynchronize(b->post[k]));
+  }
+  for (size_t i = 0; i < done.size(); i++) {
+    Entry* e = done[i];
+    if (res[i] != KRS_OK && e->s->st.status == 0) e->s->st.status = res[i];
     restore_stream(e);
     b->done_tags.push_back(e->tag);
-    b->done_status.push_back((int32_t)st);
+    b->done_status.push_back((int32_t)res[i]);
     delete e;
   }
   b->entries.swap(keep);
@@ -548,6 +565,9 @@ krs_status krs_batch_create(const krs_device* dev, const krs_batch_config* cfg, 
   if (st) return bail(st);
   if (cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess)
     return bail(failf(KRS_ERR_CUDA, "cudaEventCreate failed"));
+  for (int k = 0; k < kPostStreams; k++)
+    if (cudaStreamCreateWithFlags(&b->post[k], cudaStreamNonBlocking) != cudaSuccess)
+      return bail(failf(KRS_ERR_CUDA, "cudaStreamCreate failed"));
   *out = b;
   return KRS_OK;
 }
@@ -568,6 +588,11 @@ krs_status krs_batch_destroy(krs_batch_t b) {
   if (b->h_gather) cudaFreeHost(b->h_gather);
   if (b->e0) cudaEventDestroy(b->e0);
   if (b->e1) cudaEventDestroy(b->e1);
+  for (int k = 0; k < kPostStreams; k++)
+    if (b->post[k]) {
+      cudaStreamSynchronize(b->post[k]);
+      cudaStreamDestroy(b->post[k]);
+    }
   delete b;
   return KRS_OK;
 }

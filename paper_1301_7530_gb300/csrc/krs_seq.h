@@ -180,5 +180,10 @@ inline int dir_cap(const krs_seq* s, int prec) { return prec == KRS_MIXED_PROJ ?
 // statistics and the commit of the new augmentation space.  `status` and `m` are the
 // iteration loop's outcome.
 krs_status seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x, const krs_policy* p);
+// seq_end in three stages, for callers that finish many solves at once: stage 1 enqueues the
+// first half of the recycling step (SRKS eigenvalues and selection), stage 2 -- after the
+// stream was synchronised -- the rest of it, the result copy and the true residual, stage 3
+// -- after another synchronisation -- the statistics and the commit.
+krs_status seq_end_stage(krs_seq* s, SolveState* ss, int status, int m, double* x, const krs_policy* p, int stage);
 
 }  // namespace krs
