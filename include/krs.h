@@ -107,8 +107,11 @@ typedef struct {
  *               combined in FP32 -- on GB300 those tall-skinny products are most of the FP64
  *               arithmetic of an iteration.  chol(C^T A C), x_0 / r_0 and H_m stay FP64; SRKS
  *               forms Ritz vectors from the FP32 z's; krs_last_vectors returns nothing.
- *   inner_tol:  KRS_MIXED_IR: relative residual each inner solve aims for (<= 0: 0.1);
- *               the last one is loosened to what the outer tolerance still needs.
+ *   inner_tol:  KRS_MIXED_IR: relative residual each inner solve aims for (<= 0: 1e-5,
+ *               the fastest on the damage sequences: a long first pass gives SRKS converged
+ *               Ritz values); the last one is loosened to what the outer tolerance still
+ *               needs.  An inner solve also ends when its residual stalls (fell less than 4x
+ *               over 32 iterations once below 1e-3 of its first value).
  *   max_outer:  KRS_MIXED_IR: limit of refinement steps (<= 0: 30).  max_iter bounds the
  *               total of inner iterations.
  *   reselect:   SRKS only.  KRS_RESELECT_NONE (0), or KRS_RESELECT_CLUSTER (1): after the

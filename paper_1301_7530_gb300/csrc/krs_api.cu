@@ -282,7 +282,7 @@ krs_status krs_policy_default(krs_policy* p) {
   p->cap_mode = KRS_CAP_TRUNCATE;
   p->max_iter = 2000;
   p->exec = KRS_EXEC_PERSISTENT;
-  p->inner_tol = 0.1;
+  p->inner_tol = 1e-5;
   p->max_outer = 30;
   return KRS_OK;
 }
@@ -634,6 +634,12 @@ static krs_status ensure_mixed(krs_seq* s, int max_iter, int64_t nnzb) {
     s->vals32_valid = false;
   }
   KRS_TRY(ensure_w32(s, max_iter + 1, 0));
+  if (s->rrh_cap < s->cap_w32) {
+    dev_free(s, s->rrh);
+    s->rrh = nullptr;
+    KRS_TRY(alloc_n(s, &s->rrh, (size_t)s->cap_w32));
+    s->rrh_cap = s->cap_w32;
+  }
   // C32 / AC32 hold C, then the directions of the earlier inner solves of the same system
   if (s->cap_c + s->cap_w32 > s->cap_c32) {
     const int cap = s->cap_c + s->cap_w32;
@@ -963,6 +969,7 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   if (mixed) {
     a.vals = s->vals32; a.minv = s->minv32; a.C = s->C32; a.AC = s->AC32;
     a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.x = s->x32; a.r = s->r32; a.u = s->u32;
+    a.stall_win = 32; a.rrh = s->rrh;
   } else if (proj) {
     a.vals = s->vals_use; a.minv = s->minv; a.C = s->C32; a.AC = s->AC32; a.Ci = s->C; a.ACi = s->AC;
     a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.x = s->x; a.r = s->r; a.u = s->u; a.q = s->q64;
@@ -1139,7 +1146,7 @@ static krs_status mixed_refine(krs_seq* s, const krs_policy* p, double tol, Solv
   double* rout = pp ? s->rres : s->r;
   float* r32out = pp ? nullptr : s->b32;
   const void* rhs_in = pp ? (const void*)s->rres : (const void*)s->b32;
-  const double inner_tol = pp ? 0.0 : (p->inner_tol > 0.0 ? p->inner_tol : 0.1);
+  const double inner_tol = pp ? 0.0 : (p->inner_tol > 0.0 ? p->inner_tol : 1e-5);
   const int max_outer = p->max_outer > 0 ? p->max_outer : 30;
   KRS_CUDA(cudaMemsetAsync(xtot, 0, sizeof(double) * s->ld, s->stream));
   // r = b - A*0 = b (FP64), r32 = (float) b, rr = ||b||^2
