@@ -196,7 +196,7 @@ const char* krs_last_error(void);
 
 /* Default policy: FP64, block-Jacobi, full reorthogonalisation, no recycling,
  * ritz_eps 1e-14, no theta filter, no cap, max_iter 2000, persistent execution,
- * inner_tol 0.1 and max_outer 30 (used by KRS_MIXED_IR only). */
+ * inner_tol 1e-5 and max_outer 30 (used by KRS_MIXED_IR only). */
 krs_status krs_policy_default(krs_policy* p);
 
 /* --- recycled space (checkpoint, eviction, lock-step comparison) ----------------------- */
