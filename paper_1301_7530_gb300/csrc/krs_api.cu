@@ -282,7 +282,7 @@ krs_status krs_policy_default(krs_policy* p) {
   p->cap_mode = KRS_CAP_TRUNCATE;
   p->max_iter = 2000;
   p->exec = KRS_EXEC_PERSISTENT;
-  p->inner_tol = 1e-5;
+  p->inner_tol = 0.1;
   p->max_outer = 30;
   return KRS_OK;
 }
@@ -1146,7 +1146,7 @@ static krs_status mixed_refine(krs_seq* s, const krs_policy* p, double tol, Solv
   double* rout = pp ? s->rres : s->r;
   float* r32out = pp ? nullptr : s->b32;
   const void* rhs_in = pp ? (const void*)s->rres : (const void*)s->b32;
-  const double inner_tol = pp ? 0.0 : (p->inner_tol > 0.0 ? p->inner_tol : 1e-5);
+  const double inner_tol = pp ? 0.0 : (p->inner_tol > 0.0 ? p->inner_tol : 0.1);
   const int max_outer = p->max_outer > 0 ? p->max_outer : 30;
   KRS_CUDA(cudaMemsetAsync(xtot, 0, sizeof(double) * s->ld, s->stream));
   // r = b - A*0 = b (FP64), r32 = (float) b, rr = ||b||^2
