@@ -1131,117 +1131,172 @@ krs_status krs::seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x
   return seq_end_stage(s, ss, status, m, x, p, 3);
 }
 
-// mixed precision: FP64 refinement around FP32 inner APCG solves
-static krs_status mixed_refine(krs_seq* s, const krs_policy* p, double tol, SolveState* ss, int* status_out,
-                               int* m_out) {
-  IterArgs& a = ss->a;
-  const int nc = ss->nc;
-  const int room = ss->room;
-  int64_t& launches = ss->launches;
-  int status = KRS_OK, m = 0, outer = 0, m_first = 0, add = 0;
-  // KRS_MIXED_IR: FP32 passes on r32, x accumulated in s->x.  KRS_MIXED_PROJ: FP64-recurrence
-  // passes on the FP64 residual rres, each pass's correction in s->x, the sum in s->xacc.
+// ------------------------------------------------------------------------------------
+// refinement: FP64 outer residual around inner APCG passes (KRS_MIXED_IR: FP32 passes on
+// r32 with x accumulated in s->x; KRS_MIXED_PROJ: FP32-projection passes on the FP64
+// residual rres, each pass's correction in s->x and their sum in s->xacc)
+// ------------------------------------------------------------------------------------
+krs_status krs::refine_setup(krs_seq* s, const krs_bsr* A, const double* b, const krs_policy* p, SolveState* ss) {
+  return seq_setup(s, A, b, p, p->max_iter, ss);
+}
+
+krs_status krs::refine_start(krs_seq* s, const krs_policy* p, double tol, SolveState* ss) {
   const bool pp = p->precision == KRS_MIXED_PROJ;
   double* xtot = pp ? s->xacc : s->x;
   double* rout = pp ? s->rres : s->r;
   float* r32out = pp ? nullptr : s->b32;
-  const void* rhs_in = pp ? (const void*)s->rres : (const void*)s->b32;
-  const double inner_tol = pp ? 0.0 : (p->inner_tol > 0.0 ? p->inner_tol : 0.1);
-  const int max_outer = p->max_outer > 0 ? p->max_outer : 30;
+  ss->tol = tol;
+  ss->first = true;
+  ss->status = KRS_OK;
+  ss->m = 0;
+  ss->outer = 0;
+  ss->m_first = 0;
+  ss->add = 0;
   KRS_CUDA(cudaMemsetAsync(xtot, 0, sizeof(double) * s->ld, s->stream));
   // r = b - A*0 = b (FP64), r32 = (float) b, rr = ||b||^2
   KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, xtot, s->b, s->tmp, rout, r32out,
                                s->part, s->scal + 4, s->stream));
-  launches += 3;
+  ss->launches += 3;
   KRS_CUDA(cudaMemcpyAsync(s->h_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   KRS_CUDA(cudaStreamSynchronize(s->stream));
-  const double bb = s->h_scal[4];
-  ss->bb = bb;
-  if (!isfinite(bb)) return fail(KRS_ERR_INVALID_ARG, "right-hand side is not finite");
-  double rr = bb;
-  bool first = true;
-  for (;;) {
-    if (rr <= tol * tol * bb) break;
-    if (outer >= max_outer || m >= p->max_iter) {
-      status = KRS_ERR_NO_CONVERGENCE;
-      break;
-    }
-    // aim at inner_tol, or less when the outer tolerance is closer than that
-    double tin = 0.5 * tol * sqrt(bb / rr);
-    if (tin < inner_tol) tin = inner_tol;
-    if (tin > 0.5) tin = 0.5;
-    a.max_iter = p->max_iter - m;
-    int st_in = KRS_OK, m_in = 0;
-    double bb_in = 0.0;
-    KRS_TRY(run_apcg(s, a, rhs_in, tin, p->exec, &st_in, &m_in, &bb_in, &ss->t_iter, &launches));
-    // An FP32 breakdown ((w, Aw) <= 0 or (r, z) <= 0) after some progress, or a stalled
-    // residual, only ends this pass: its iterate and directions up to there are valid, and
-    // the FP64 outer residual decides whether refinement still advances.
-    if (st_in == KRS_STALLED) st_in = KRS_OK;
-    if (st_in != KRS_OK && st_in != KRS_ERR_NO_CONVERGENCE && !(st_in == KRS_ERR_NOT_SPD && m_in > 0)) {
-      status = st_in;
-      break;
-    }
-    m += m_in;
-    s->last_m = m_in;
-    if (first) {
-      m_first = m_in;
-      // recycling from the first inner solve (staged beyond nc until the system converges)
-      if (p->recycle == KRS_RECYCLE_TRKS && m_in > 0) {
-        add = m_in < room ? m_in : room;
-        if (add > 0) {
-          k_f2d_cols<<<1216, 256, 0, s->stream>>>(s->W32, s->C + (size_t)nc * s->ld, (int64_t)add * s->ld);
-          KRS_CUDA(cudaGetLastError());
-          launches++;
-        }
-      } else if (p->recycle == KRS_RECYCLE_SRKS && m_in >= 2) {
-        KRS_TRY(srks_extract(s, m_in, nc, room, p, nullptr, s->Z32, &add, &launches, false));
-      }
-      first = false;
-    }
-    // The next inner solve (same operator) is augmented by this one's directions: they
-    // are A-conjugate to C and to each other, so their coarse block is diag(1/(w, Aw)).
-    if (m_in > 0) {
-      const int nct = a.nc;
-      KRS_CUDA(cudaMemcpyAsync(s->C32 + (size_t)nct * s->ld, s->W32, sizeof(float) * (size_t)m_in * s->ld,
-                               cudaMemcpyDeviceToDevice, s->stream));
-      KRS_CUDA(cudaMemcpyAsync(s->AC32 + (size_t)nct * s->ld, s->AW32, sizeof(float) * (size_t)m_in * s->ld,
-                               cudaMemcpyDeviceToDevice, s->stream));
-      k_recip<<<(m_in + 255) / 256, 256, 0, s->stream>>>(s->gamma, s->dinv + (nct - nc), m_in);
-      KRS_CUDA(cudaGetLastError());
-      launches++;
-      a.nc = nct + m_in;
-      if (pp) {  // the earlier passes' directions exist in FP32 only: later inits read C32, AC32
-        a.init32 = true;
-        a.Ci = nullptr;
-        a.ACi = nullptr;
-      }
-    }
-    // x += d (FP64), r = b - A x (FP64), next pass's right-hand side (r32 = (float) r)
-    if (pp) KRS_CUDA(launch_add_d(xtot, s->x, s->n, s->stream));
-    else KRS_CUDA(launch_add_f2d(xtot, s->x32, s->n, s->stream));
-    KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, xtot, s->b, s->tmp, rout, r32out,
-                                 s->part, s->scal + 4, s->stream));
-    launches += 4;
-    KRS_CUDA(cudaMemcpyAsync(s->h_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-    KRS_CUDA(cudaStreamSynchronize(s->stream));
-    const double rr_new = s->h_scal[4];
-    outer++;
-    if (!(rr_new < 0.81 * rr) && !(rr_new <= tol * tol * bb)) {  // stagnation: refinement no longer pays
-      rr = rr_new;
-      status = KRS_ERR_NO_CONVERGENCE;
-      break;
-    }
-    rr = rr_new;
+  ss->bb = s->h_scal[4];
+  ss->rr = ss->bb;
+  if (!isfinite(ss->bb)) return fail(KRS_ERR_INVALID_ARG, "right-hand side is not finite");
+  return KRS_OK;
+}
+
+krs_status krs::refine_pass_begin(krs_seq* s, const krs_policy* p, double tol, SolveState* ss, bool* need_loop,
+                                  bool* finished) {
+  const bool pp = p->precision == KRS_MIXED_PROJ;
+  const void* rhs_in = pp ? (const void*)s->rres : (const void*)s->b32;
+  const double inner_tol = pp ? 0.0 : (p->inner_tol > 0.0 ? p->inner_tol : 0.1);
+  const int max_outer = p->max_outer > 0 ? p->max_outer : 30;
+  IterArgs& a = ss->a;
+  *need_loop = false;
+  *finished = false;
+  const double bb = ss->bb;
+  if (ss->rr <= tol * tol * bb) {
+    *finished = true;
+    return KRS_OK;
   }
-  if (pp)  // the result and the true residual are taken from s->x
-    KRS_CUDA(cudaMemcpyAsync(s->x, xtot, sizeof(double) * s->ld, cudaMemcpyDeviceToDevice, s->stream));
+  if (ss->outer >= max_outer || ss->m >= p->max_iter) {
+    ss->status = KRS_ERR_NO_CONVERGENCE;
+    *finished = true;
+    return KRS_OK;
+  }
+  // aim at inner_tol, or less when the outer tolerance is closer than that
+  double tin = 0.5 * tol * sqrt(bb / ss->rr);
+  if (tin < inner_tol) tin = inner_tol;
+  if (tin > 0.5) tin = 0.5;
+  a.max_iter = p->max_iter - ss->m;
+  double bb_in = 0.0, rr0 = 0.0;
+  KRS_TRY(run_init(s, a, rhs_in, tin, &bb_in, &rr0, &ss->launches));
+  // the stall test watches only the last stretch: below 1e-3 of the pass's first residual
+  a.stall_rr = 1e-6 * rr0;
+  *need_loop = rr0 > a.tol2;
+  return KRS_OK;
+}
+
+krs_status krs::refine_pass_end(krs_seq* s, const krs_policy* p, double tol, SolveState* ss, int st_in, int m_in,
+                                bool* finished) {
+  const bool pp = p->precision == KRS_MIXED_PROJ;
+  double* xtot = pp ? s->xacc : s->x;
+  double* rout = pp ? s->rres : s->r;
+  float* r32out = pp ? nullptr : s->b32;
+  IterArgs& a = ss->a;
+  const int nc = ss->nc;
+  const int room = ss->room;
+  int64_t& launches = ss->launches;
+  *finished = false;
+  // An FP32 breakdown ((w, Aw) <= 0 or (r, z) <= 0) after some progress, or a stalled
+  // residual, only ends this pass: its iterate and directions up to there are valid, and
+  // the FP64 outer residual decides whether refinement still advances.
+  if (st_in == KRS_STALLED) st_in = KRS_OK;
+  if (st_in != KRS_OK && st_in != KRS_ERR_NO_CONVERGENCE && !(st_in == KRS_ERR_NOT_SPD && m_in > 0)) {
+    ss->status = st_in;
+    *finished = true;
+    return KRS_OK;
+  }
+  ss->m += m_in;
+  s->last_m = m_in;
+  if (ss->first) {
+    ss->m_first = m_in;
+    // recycling from the first inner solve (staged beyond nc until the system converges)
+    if (p->recycle == KRS_RECYCLE_TRKS && m_in > 0) {
+      const int add = m_in < room ? m_in : room;
+      if (add > 0) {
+        k_f2d_cols<<<1216, 256, 0, s->stream>>>(s->W32, s->C + (size_t)nc * s->ld, (int64_t)add * s->ld);
+        KRS_CUDA(cudaGetLastError());
+        launches++;
+      }
+      ss->add = add;
+    } else if (p->recycle == KRS_RECYCLE_SRKS && m_in >= 2) {
+      KRS_TRY(srks_extract(s, m_in, nc, room, p, nullptr, s->Z32, &ss->add, &launches, false));
+    }
+    ss->first = false;
+  }
+  // The next inner solve (same operator) is augmented by this one's directions: they
+  // are A-conjugate to C and to each other, so their coarse block is diag(1/(w, Aw)).
+  if (m_in > 0) {
+    const int nct = a.nc;
+    KRS_CUDA(cudaMemcpyAsync(s->C32 + (size_t)nct * s->ld, s->W32, sizeof(float) * (size_t)m_in * s->ld,
+                             cudaMemcpyDeviceToDevice, s->stream));
+    KRS_CUDA(cudaMemcpyAsync(s->AC32 + (size_t)nct * s->ld, s->AW32, sizeof(float) * (size_t)m_in * s->ld,
+                             cudaMemcpyDeviceToDevice, s->stream));
+    k_recip<<<(m_in + 255) / 256, 256, 0, s->stream>>>(s->gamma, s->dinv + (nct - nc), m_in);
+    KRS_CUDA(cudaGetLastError());
+    launches++;
+    a.nc = nct + m_in;
+    if (pp) {  // the earlier passes' directions exist in FP32 only: later inits read C32, AC32
+      a.init32 = true;
+      a.Ci = nullptr;
+      a.ACi = nullptr;
+    }
+  }
+  // x += d (FP64), r = b - A x (FP64), next pass's right-hand side (r32 = (float) r)
+  if (pp) KRS_CUDA(launch_add_d(xtot, s->x, s->n, s->stream));
+  else KRS_CUDA(launch_add_f2d(xtot, s->x32, s->n, s->stream));
+  KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, xtot, s->b, s->tmp, rout, r32out,
+                               s->part, s->scal + 4, s->stream));
+  launches += 4;
+  KRS_CUDA(cudaMemcpyAsync(s->h_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  const double rr_new = s->h_scal[4];
+  ss->outer++;
+  const double bb = ss->bb;
+  if (!(rr_new < 0.81 * ss->rr) && !(rr_new <= tol * tol * bb)) {  // stagnation: refinement no longer pays
+    ss->rr = rr_new;
+    ss->status = KRS_ERR_NO_CONVERGENCE;
+    *finished = true;
+    return KRS_OK;
+  }
+  ss->rr = rr_new;
+  return KRS_OK;
+}
+
+krs_status krs::refine_finish(krs_seq* s, const krs_policy* p, SolveState* ss) {
+  if (p->precision == KRS_MIXED_PROJ)  // the result and the true residual are taken from s->x
+    KRS_CUDA(cudaMemcpyAsync(s->x, s->xacc, sizeof(double) * s->ld, cudaMemcpyDeviceToDevice, s->stream));
   KRS_CUDA(cudaEventRecord(s->ev[2], s->stream));
-  ss->add = add;
-  ss->outer = outer;
-  ss->m_first = m_first;
-  *status_out = status;
-  *m_out = m;
+  return KRS_OK;
+}
+
+// the whole refinement loop of one system (krs_solve)
+static krs_status mixed_refine(krs_seq* s, const krs_policy* p, double tol, SolveState* ss, int* status_out,
+                               int* m_out) {
+  KRS_TRY(refine_start(s, p, tol, ss));
+  for (;;) {
+    bool need_loop = false, finished = false;
+    KRS_TRY(refine_pass_begin(s, p, tol, ss, &need_loop, &finished));
+    if (finished) break;
+    int st_in = KRS_OK, m_in = 0;
+    if (need_loop) KRS_TRY(run_loop(s, ss->a, p->exec, &st_in, &m_in, &ss->t_iter, &ss->launches));
+    KRS_TRY(refine_pass_end(s, p, tol, ss, st_in, m_in, &finished));
+    if (finished) break;
+  }
+  KRS_TRY(refine_finish(s, p, ss));
+  *status_out = ss->status;
+  *m_out = ss->m;
   return KRS_OK;
 }
 

@@ -239,12 +239,10 @@ static IterArgs group_args(const Entry* e, int64_t vld) {
   const int g = e->g;
   krs_seq* s = e->s;
   IterArgs a = e->ss.a;
-  if (e->p.precision == KRS_MIXED_PROJ) {
-    a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.q = s->q64;
-  } else {
+  if (e->p.precision == KRS_FP64) {  // FP64 storage may have grown since the set-up
     a.W = s->W; a.AW = s->AW; a.Z = s->Z;
+    a.alpha = s->alpha; a.gamma = s->gamma; a.rho = s->rho; a.gfull = s->gfull;
   }
-  a.alpha = s->alpha; a.gamma = s->gamma; a.rho = s->rho; a.gfull = s->gfull;
   a.tfull = s->tfull; a.sfull = s->sfull;
   a.P = g;
   int64_t per = (s->nbr + g - 1) / g;
@@ -258,6 +256,37 @@ static IterArgs group_args(const Entry* e, int64_t vld) {
 static krs_status restore_stream(Entry* e) {
   e->s->stream = e->saved_stream;
   e->s->busy = false;
+  return KRS_OK;
+}
+
+// Refinement solves (KRS_MIXED_IR): after a pass's iterations (have_pass: their outcome
+// st_in, m_in), update the FP64 iterate and residual, then start the next pass: the entry
+// is queued again with iteration 0 when the pass has iterations to run, or it ends.
+static krs_status advance_refinement(krs_batch* b, Entry* e, int st_in, int m_in, bool have_pass) {
+  krs_seq* s = e->s;
+  bool finished = false;
+  for (;;) {
+    if (have_pass) {
+      KRS_TRY(refine_pass_end(s, &e->p, e->tol, &e->ss, st_in, m_in, &finished));
+      if (finished) break;
+    }
+    bool need_loop = false;
+    KRS_TRY(refine_pass_begin(s, &e->p, e->tol, &e->ss, &need_loop, &finished));
+    if (finished) break;
+    if (need_loop) {
+      KRS_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, b->stream));
+      e->j = 0;
+      e->ended = false;
+      e->m_est = e->ss.m_first > 0 ? (double)e->ss.m_first : e->m_est;
+      return KRS_OK;
+    }
+    have_pass = true;  // a pass already within its tolerance: no iterations
+    st_in = KRS_OK;
+    m_in = 0;
+  }
+  e->ended = true;
+  e->status = e->ss.status;
+  e->m = e->ss.m;
   return KRS_OK;
 }
 
@@ -311,10 +340,11 @@ static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int quantu
   const int count = (int)queued.size();
   const int nact = (int)act.size();
   int kmax = 1;
-  for (Entry* e : queued) kmax = std::max(kmax, std::max(e->ss.nc, dir_cap(e->s, e->p.precision)));
+  for (Entry* e : queued)  // refinement passes project against C and the earlier passes' directions
+    kmax = std::max(kmax, std::max(std::max(e->ss.nc, e->ss.a.nc), dir_cap(e->s, e->p.precision)));
   const int64_t vld = round_up(kmax + 1, 32);
   int bps = 0;
-  const int prec = queued[0]->p.precision == KRS_MIXED_PROJ ? 2 : 0;
+  const int prec = queued[0]->p.precision == KRS_MIXED_IR ? 1 : 0;  // one precision per launch
   KRS_CUDA(apcg_batched_coresident(kmax, prec, &bps));
   if (bps < 1) return failf(KRS_ERR_CUDA, "batch: persistent kernel cannot be resident (kmax %d)", kmax);
   KRS_TRY(ensure_table(b, count));
@@ -401,7 +431,11 @@ static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int quantu
     const int* cw = b->h_gather + 4 * i;
     const int j_before = e->j;
     e->ss.t_iter += *ms;
-    if (cw[CTRL_DONE]) {
+    if (cw[CTRL_DONE] && e->p.precision == KRS_MIXED_IR) {
+      // one refinement pass ended: the next pass starts (or the refinement ends)
+      if (rows_iters) *rows_iters += (double)e->s->n * (cw[CTRL_M] - j_before);
+      KRS_TRY(advance_refinement(b, e, cw[CTRL_STATUS], cw[CTRL_M], true));
+    } else if (cw[CTRL_DONE]) {
       e->ended = true;
       e->status = cw[CTRL_STATUS];
       e->m = cw[CTRL_M];
@@ -446,7 +480,7 @@ static krs_status autotune(krs_batch* b, std::vector<Entry*>& run) {
     float ms = 0.f;
     double ri = 0.0;
     std::vector<Entry*> part[2];
-    for (Entry* e : run) part[e->p.precision == KRS_MIXED_PROJ ? 1 : 0].push_back(e);
+    for (Entry* e : run) part[e->p.precision == KRS_MIXED_IR ? 1 : 0].push_back(e);
     for (auto& pr : part) {
       if (pr.empty()) continue;
       float ms1 = 0.f;
@@ -487,6 +521,8 @@ static krs_status finish_ended(krs_batch* b) {
   KRS_CUDA(cudaStreamSynchronize(b->stream));
   std::vector<krs_status> res(done.size(), KRS_OK);
   for (size_t i = 0; i < done.size(); i++) done[i]->s->stream = b->post[i % kPostStreams];
+  for (size_t i = 0; i < done.size(); i++)
+    if (done[i]->p.precision == KRS_MIXED_IR) res[i] = refine_finish(done[i]->s, &done[i]->p, &done[i]->ss);
   for (int stage = 1; stage <= 3; stage++) {
     for (size_t i = 0; i < done.size(); i++) {
       Entry* e = done[i];
@@ -604,7 +640,8 @@ krs_status krs_batch_submit(krs_batch_t b, krs_seq_t s, const krs_bsr* A, const 
   if (s->busy) return failf(KRS_ERR_INVALID_ARG, "the sequence already has a solve in flight");
   if (s->device != b->device) return failf(KRS_ERR_INVALID_ARG, "sequence and batch are on different devices");
   KRS_TRY(validate_policy(p));
-  if (p->precision != KRS_FP64) return failf(KRS_ERR_INVALID_ARG, "batched solves run in FP64 (precision KRS_FP64)");
+  if (p->precision == KRS_MIXED_PROJ)
+    return failf(KRS_ERR_INVALID_ARG, "batched solves run in KRS_FP64 or KRS_MIXED_IR");
   if (p->max_iter < 1 || p->max_iter > 16000) return failf(KRS_ERR_INVALID_ARG, "max_iter %d outside [1, 16000]", p->max_iter);
   Entry* e = new (std::nothrow) Entry();
   if (!e) return failf(KRS_ERR_OOM, "host allocation failed");
@@ -617,10 +654,19 @@ krs_status krs_batch_submit(krs_batch_t b, krs_seq_t s, const krs_bsr* A, const 
   e->saved_stream = s->stream;
   s->stream = b->stream;
   s->busy = true;
-  krs_status st = seq_begin(s, A, rhs, tol, p, first_cap(e), &e->ss);
-  if (st == KRS_OK) {
-    cudaError_t ce = cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, b->stream);
-    if (ce != cudaSuccess) st = failf(KRS_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(ce));
+  krs_status st = KRS_OK;
+  if (p->precision == KRS_MIXED_IR) {
+    // FP64 refinement around FP32 passes: set-up, the first FP64 residual, the first pass's
+    // init (the pass's iterations run in the batched launches)
+    st = refine_setup(s, A, rhs, p, &e->ss);
+    if (st == KRS_OK) st = refine_start(s, p, tol, &e->ss);
+    if (st == KRS_OK) st = advance_refinement(b, e, KRS_OK, 0, false);
+  } else {
+    st = seq_begin(s, A, rhs, tol, p, first_cap(e), &e->ss);
+    if (st == KRS_OK) {
+      cudaError_t ce = cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, b->stream);
+      if (ce != cudaSuccess) st = failf(KRS_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(ce));
+    }
   }
   if (st != KRS_OK) {
     if (s->st.status == 0) s->st.status = st;
@@ -628,7 +674,7 @@ krs_status krs_batch_submit(krs_batch_t b, krs_seq_t s, const krs_bsr* A, const 
     delete e;
     return st;
   }
-  if (!e->ss.need_iter) e->ended = true;  // ||r_0|| already within tolerance: m = 0
+  if (p->precision == KRS_FP64 && !e->ss.need_iter) e->ended = true;  // ||r_0|| within tolerance: m = 0
   b->entries.push_back(e);
   return KRS_OK;
 }
@@ -644,14 +690,14 @@ krs_status krs_batch_step(krs_batch_t b, int32_t max_done, int64_t* done_tags, i
     if (!e->ended) run.push_back(e);
   if (!run.empty()) {
     if (b->cfg.group_ctas == 0 && b->scale == 0) {
-      bool fresh = true;
-      for (Entry* e : run) fresh = fresh && e->j == 0 && e->g == 0;
+      bool fresh = true;  // (refinement passes change state the probe could not restore)
+      for (Entry* e : run) fresh = fresh && e->j == 0 && e->g == 0 && e->p.precision == KRS_FP64;
       if (fresh) KRS_TRY(autotune(b, run));
       if (b->scale == 0) b->scale = 100;
     }
     // one launch per precision present (each launch runs one kernel instantiation)
     std::vector<Entry*> part[2];
-    for (Entry* e : run) part[e->p.precision == KRS_MIXED_PROJ ? 1 : 0].push_back(e);
+    for (Entry* e : run) part[e->p.precision == KRS_MIXED_IR ? 1 : 0].push_back(e);
     for (auto& pr : part) {
       if (pr.empty()) continue;
       float ms = 0.f;

@@ -163,6 +163,11 @@ struct SolveState {
   int m_first = 0;    // mixed precision: iterations of the first inner solve
   int64_t launches = 0;
   float t_iter = 0.f;
+  // refinement state (KRS_MIXED_IR, KRS_MIXED_PROJ) between passes
+  double rr = 0.0;     // ||b - A x||^2 of the current iterate
+  bool first = true;   // the next pass is the first one
+  int status = 0;      // outcome so far
+  int m = 0;           // inner iterations so far
 };
 
 // Stage 1: matrix, preconditioner, right-hand side, storage (direction capacity `cap_iter`
@@ -175,11 +180,24 @@ krs_status seq_begin(krs_seq* s, const krs_bsr* A, const double* b, double tol, 
 // the scalars of the first `keep` iterations (between launches).
 krs_status seq_grow_directions(krs_seq* s, int cap_iter, int keep, int prec);
 // columns of the direction storage a solve of precision `prec` uses
-inline int dir_cap(const krs_seq* s, int prec) { return prec == KRS_MIXED_PROJ ? s->cap_w32 : s->cap_w; }
+inline int dir_cap(const krs_seq* s, int prec) { return prec == KRS_FP64 ? s->cap_w : s->cap_w32; }
 // Stage 3: recycling step (TRKS / SRKS), result copy to x (host or device), true residual,
 // statistics and the commit of the new augmentation space.  `status` and `m` are the
 // iteration loop's outcome.
 krs_status seq_end(krs_seq* s, SolveState* ss, int status, int m, double* x, const krs_policy* p);
+// Refinement (KRS_MIXED_IR, KRS_MIXED_PROJ) as resumable steps, after seq_setup-like set-up
+// (refine_setup): refine_start forms the first FP64 residual; refine_pass_begin checks
+// convergence and limits (*finished) and otherwise runs the next pass's init stage
+// (*need_loop: the pass has iterations to run); the caller runs the pass's iteration loop
+// and gives its outcome to refine_pass_end, which updates x, the residual and the
+// augmentation; refine_finish ends the loop.
+krs_status refine_setup(krs_seq* s, const krs_bsr* A, const double* b, const krs_policy* p, SolveState* ss);
+krs_status refine_start(krs_seq* s, const krs_policy* p, double tol, SolveState* ss);
+krs_status refine_pass_begin(krs_seq* s, const krs_policy* p, double tol, SolveState* ss, bool* need_loop,
+                             bool* finished);
+krs_status refine_pass_end(krs_seq* s, const krs_policy* p, double tol, SolveState* ss, int st_in, int m_in,
+                           bool* finished);
+krs_status refine_finish(krs_seq* s, const krs_policy* p, SolveState* ss);
 // seq_end in three stages, for callers that finish many solves at once: stage 1 enqueues the
 // first half of the recycling step (SRKS eigenvalues and selection), stage 2 -- after the
 // stream was synchronised -- the rest of it, the result copy and the true residual, stage 3

@@ -105,7 +105,11 @@ class Server:
         m = c.m_prev if c.m_prev > 0 else 12.0 * c.n ** (1.0 / 3.0)
         cap = _round_up(int(1.25 * m) + 48, 32)
         room = self.policy.max_aug if self.policy.max_aug > 0 else cap
-        est = 8 * ld * (3 * cap + 2 * room) + 72 * c.nnzb
+        if self.policy.precision == 1:  # refinement: FP32 storage for max_iter inner iterations
+            wi = _round_up(self.policy.max_iter + 1, 32)
+            est = ld * (4 * 3 * wi + 4 * 2 * (room + wi) + 8 * 2 * room + 40) + (72 + 36) * c.nnzb
+        else:
+            est = 8 * ld * (3 * cap + 2 * room) + 72 * c.nnzb
         if c.evicted is not None:
             est += 16 * ld * c.evicted.shape[1]
         return est
