@@ -121,7 +121,8 @@ def test_autotuned_engine_matches_fixed_choice(gpu_lib):
 
 def test_submit_step_tags_and_statuses(gpu_lib):
     """Request-level interface: submissions return by tag; a zero right-hand side ends at
-    m = 0; a sequence with a solve in flight is refused; batched solves are FP64 only."""
+    m = 0; a sequence with a solve in flight is refused; the FP32-projection precision is
+    not batched."""
     probs = _damage_set([5, 6, 4], 1, seed0=130)
     seqs = [B.Sequence(_n(N)) for N, _, _ in probs]
     pol = B.make_policy("none", "block_jacobi3")
@@ -134,7 +135,7 @@ def test_submit_step_tags_and_statuses(gpu_lib):
     eng.submit(z, probs[2][2][0], np.zeros(_n(4)), 1e-8, pol, tag=200, version=1)
     with pytest.raises(B.KrsError):
         eng.submit(B.Sequence(_n(4)), probs[2][2][0], probs[2][1], 1e-8,
-                   B.make_policy("none", "block_jacobi3", precision="mixed_ir"), tag=8, version=1)
+                   B.make_policy("none", "block_jacobi3", precision="mixed_proj"), tag=8, version=1)
     done = {}
     for _ in range(500):
         for tag, st, x in eng.step():
