@@ -38,7 +38,14 @@ from paper_1301_7530_gb300 import problems as P  # noqa: E402
 METRIC = "solves/s and p50/p99 latency at rel. residual 1e-8; SpMV+proj HBM GB/s vs 8 TB/s"
 UNIT = "solves/s"
 TOL = 1e-8
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "apcg_persistent_32cube_damage_fp64.md")
+PROFILE_SUMMARY = {"fp64": os.path.join(ROOT, "profiles", "apcg_persistent_32cube_damage_fp64.md"),
+                   "double_float": os.path.join(ROOT, "profiles", "apcg_persistent_32cube_damage_dfloat.md")}
+
+
+def dtype_of(precision):
+    """Arithmetic type of the path: FP64; FP64 with double-float (two-FP32) directions; or
+    FP32 inner passes with FP64 refinement."""
+    return {"fp64": "f64", "double_float": "f64+df32x2"}.get(precision, "f32+f64")
 CSRC = os.path.join(ROOT, "paper_1301_7530_gb300", "csrc")
 
 # FP64 ALU roof of GB300: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz
@@ -65,7 +72,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--precision", choices=["fp64", "mixed_ir", "mixed_proj"], default="fp64",
+    ap.add_argument("--precision", choices=["fp64", "double_float", "mixed_ir", "mixed_proj"], default="fp64",
                     help="sequence workload: FP64, FP32 refinement passes, or FP32 projection passes")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="mixed_ir: relative residual of each FP32 pass (0: the library default 0.1)")
@@ -190,12 +197,13 @@ def csrc_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources (else None)."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def profiled_traffic(precision="fp64"):
+    """DRAM bytes per launch from the committed ncu summary of that precision's persistent
+    kernel, if it was taken on the current kernel sources (else None)."""
+    path = PROFILE_SUMMARY.get(precision)
+    if not path or not os.path.exists(path):
         return None, None
-    txt = open(PROFILE_SUMMARY).read()
+    txt = open(path).read()
     vals = {}
     for line in txt.splitlines():
         if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "algorithmic_bytes_per_launch",
@@ -336,7 +344,7 @@ def run_krs(args, rank, world, local):
     achieved_tflops = flops / (t_iter / 1e3) / 1e12
     achieved_gbs = byts / (t_iter / 1e3) / 1e9
     hbm_peak, hbm_kind = measured_peaks()
-    traffic, traffic_alg = profiled_traffic() if args.precision == "fp64" else (None, None)
+    traffic, traffic_alg = profiled_traffic(args.precision)
     iter_share = t_iter / ms
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -388,7 +396,7 @@ def run_krs(args, rank, world, local):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": dtype_of(args.precision), "data": "synthetic",
             "config": {
                 "workload": (f"{args.N}^3 Q1 elasticity damage sequence, {args.systems} systems per step, SRKS"
                              if args.problem == "damage" else
@@ -409,13 +417,22 @@ def run_krs(args, rank, world, local):
                        "t_setup_ms_mean": float(np.mean([s["t_setup_ms"] for s in stats])),
                        "t_iter_ms_mean": float(np.mean([s["t_iter_ms"] for s in stats])),
                        "t_recycle_ms_mean": float(np.mean([s["t_recycle_ms"] for s in stats]))},
-            "roofline": {"kernel": "k_apcg_persistent", "bound": "alu", "achieved": achieved_tflops,
-                         "flops": "FP64 algorithmic flops of the iterations" if args.precision == "fp64" else
-                                  "FP64-equivalent flops of the iterations (mixed-precision passes)",
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-                         "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
-                         "traffic": traffic, "traffic_alg_bytes": traffic_alg,
-                         "launches": launches, "share_of_step_time": iter_share},
+            "roofline": ({"kernel": "k_apcg_persistent", "bound": "alu", "achieved": achieved_tflops,
+                          "flops": "FP64 algorithmic flops of the iterations" if args.precision == "fp64" else
+                                   "FP64-equivalent flops of the iterations (mixed-precision passes)",
+                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                          "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                          "traffic": traffic, "traffic_alg_bytes": traffic_alg,
+                          "launches": launches, "share_of_step_time": iter_share}
+                         if args.precision != "double_float" else
+                         # the reorthogonalisation streams run on the FP32 pipes: memory-bound
+                         {"kernel": "k_apcg_persistent<PrecE>", "bound": "hbm", "achieved": achieved_gbs,
+                          "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                          "peak_kind": hbm_kind, "what": "algorithmic bytes of the iterations / iteration kernel time",
+                          "traffic": traffic, "traffic_alg_bytes": traffic_alg,
+                          "launches": launches, "share_of_step_time": iter_share,
+                          "fp64_view": {"achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                        "what": "FP64-equivalent algorithmic flops / time (part of them on FP32 pipes)"}}),
             "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
                     "peak_kind": hbm_kind, "what": "algorithmic bytes of the iteration kernel / its time"},
             "e2e": e2e,
@@ -517,7 +534,7 @@ def run_many(args, kind):
     Ns, systems, clients = _many(args, kind)
     B.lib()
     pol = B.make_policy("srks", "block_jacobi3", ritz_eps=args.ritz_eps, theta_frac=args.theta_frac,
-                        max_aug=100, max_iter=1000 if args.precision == "fp64" else 800,
+                        max_aug=100, max_iter=1000 if args.precision in ("fp64", "double_float") else 800,
                         precision=args.precision, inner_tol=args.inner_tol)
     quantum = args.quantum if args.quantum is not None else (0 if kind == "batched" else 32)
     budget = int(args.budget_gb * (1 << 30)) if kind == "served" else int(200 * (1 << 30))
@@ -567,7 +584,7 @@ def run_many(args, kind):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": systems, "warmup": 1,
         "ms_per_step": wall * 1e3 / systems, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic", "impl": "krs",
+        "dtype": dtype_of(args.precision), "data": "synthetic", "impl": "krs",
         "workload_kind": kind,
         "config": {
             "workload": (f"{len(clients)} damage sequences x {systems} systems, cubes N ~ U{{{min(Ns)}..{max(Ns)}}}"
@@ -591,6 +608,11 @@ def run_many(args, kind):
                       "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                       "kernel_ms": kern_ms, "share_of_wall": kern_ms / (wall * 1e3)}
                      if args.precision == "fp64" else
+                     {"kernel": "k_apcg_batched<PrecE>", "bound": "hbm", "achieved": 2.0 * gbs, "peak": hbm_peak,
+                      "unit": "GB/s", "frac": 2.0 * gbs / hbm_peak, "traffic": None,
+                      "what": "FP64 algorithmic bytes of all iterations (double-float directions: 8 bytes each) / "
+                              "batched kernel time", "kernel_ms": kern_ms, "share_of_wall": kern_ms / (wall * 1e3)}
+                     if args.precision == "double_float" else
                      {"kernel": "k_apcg_batched (FP32 passes)", "bound": "hbm", "achieved": gbs,
                       "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
                       "what": "half the FP64 algorithmic bytes of all inner iterations (FP32 storage) / "

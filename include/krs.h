@@ -49,7 +49,7 @@ typedef enum {
 enum { KRS_RECYCLE_NONE = 0, KRS_RECYCLE_TRKS = 1, KRS_RECYCLE_SRKS = 2 };
 enum { KRS_PRECOND_JACOBI = 0, KRS_PRECOND_BLOCK_JACOBI3 = 1, KRS_PRECOND_IDENTITY = 2 };
 enum { KRS_REORTH_FULL = 0, KRS_REORTH_NONE = 1 };
-enum { KRS_FP64 = 0, KRS_MIXED_IR = 1, KRS_MIXED_PROJ = 2 };
+enum { KRS_FP64 = 0, KRS_MIXED_IR = 1, KRS_MIXED_PROJ = 2, KRS_DOUBLE_FLOAT = 3 };
 enum { KRS_CAP_TRUNCATE = 0, KRS_CAP_RESTART = 1 };
 enum { KRS_EXEC_PERSISTENT = 0, KRS_EXEC_KERNELS = 1 };
 enum { KRS_RESELECT_NONE = 0, KRS_RESELECT_CLUSTER = 1 };
@@ -107,6 +107,19 @@ typedef struct {
  *               combined in FP32 -- on GB300 those tall-skinny products are most of the FP64
  *               arithmetic of an iteration.  chol(C^T A C), x_0 / r_0 and H_m stay FP64; SRKS
  *               forms Ritz vectors from the FP32 z's; krs_last_vectors returns nothing.
+ *               KRS_DOUBLE_FLOAT: the FP64 solve (operator product, preconditioner, x / r
+ *               recurrences, projection with the FP64 C and AC, coarse set-up, H_m) with the
+ *               search directions W, AW, Z stored as double-float pairs (hi + lo, two FP32
+ *               numbers in 8 bytes: a 48-bit significand) and the reorthogonalisation's
+ *               tall-skinny products taken on the FP32 pipes with error-free products and
+ *               compensated sums (about 2^-46 relative per product against 2^-53 in FP64).
+ *               On GB300 the FP64 pipe retires 1/64 of the FP32 rate, so these products
+ *               become bound by memory instead of by FP64 arithmetic.  There is no
+ *               refinement loop: the iteration converges on its FP64 residual as KRS_FP64
+ *               does.  The directions must stay within the FP32 exponent range (about
+ *               1e-30 .. 1e38 in magnitude keep the full significand); TRKS appends them to C
+ *               in FP64, SRKS forms Ritz vectors from them in FP64, krs_last_vectors returns
+ *               them as doubles.
  *   inner_tol:  KRS_MIXED_IR: relative residual each inner solve aims for (<= 0: 0.1);
  *               the last one is loosened to what the outer tolerance still needs.  An inner
  *               solve also ends when its residual stalls (fell less than 4x over 32
@@ -259,7 +272,8 @@ krs_status krs_release(krs_seq_t s, int32_t what);
  * partition) it differs by rounding only.
  * Direction storage starts at 1.25x the sequence's previous iteration count (12 n^(1/3)
  * for its first solve) and grows between launches when a solve fills it.
- * Only KRS_FP64 policies are accepted; `exec` is ignored (the batched persistent kernel
+ * KRS_FP64, KRS_DOUBLE_FLOAT and KRS_MIXED_IR policies are accepted (one launch per precision
+ * present); `exec` is ignored (the batched persistent kernel
  * runs every solve).  The engine must not be used from two threads at once, and a
  * sequence with a solve in flight must not be used elsewhere until it is returned. */
 typedef struct krs_batch* krs_batch_t;

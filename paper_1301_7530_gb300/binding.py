@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "NO_CONVERGENCE", 4:
 RECYCLE = {"none": 0, "trks": 1, "srks": 2}
 PRECOND = {"jacobi": 0, "block_jacobi3": 1, "identity": 2}
 REORTH = {"full": 0, "none": 1}
-PRECISION = {"fp64": 0, "mixed_ir": 1, "mixed_proj": 2}
+PRECISION = {"fp64": 0, "mixed_ir": 1, "mixed_proj": 2, "double_float": 3}
 CAP = {"truncate": 0, "restart": 1}
 EXEC = {"persistent": 0, "kernels": 1}
 RESELECT = {"none": 0, "cluster": 1}

@@ -35,21 +35,28 @@
 
 namespace krs {
 
-// Precision of a solve: V = vectors x, r, u (and q in PrecP), M = multi-vectors C, AC, W,
-// AW, Z, A = matrix values and M^-1.  Partial sums that cross CTAs and every scalar are
-// doubles in all three.
+// Precision of a solve: V = vectors x, r, u (and q in PrecP / PrecE), M = the search
+// directions W, AW, Z, MC = the augmentation space C, AC, A = matrix values and M^-1.
+// Partial sums that cross CTAs and every scalar are doubles in all four.
 //   PrecD  FP64 throughout;
 //   PrecF  FP32 throughout (inner solves of the mixed-precision refinement);
 //   PrecP  FP64 operator product, preconditioner, x and r recurrences; FP32 projection and
-//          reorthogonalisation (C, AC, W, AW, Z stored and combined in FP32).
-struct PrecD { using V = double; using M = double; using A = double; static constexpr int id = 0; };
-struct PrecF { using V = float;  using M = float;  using A = float;  static constexpr int id = 1; };
-struct PrecP { using V = double; using M = float;  using A = double; static constexpr int id = 2; };
+//          reorthogonalisation (C, AC, W, AW, Z stored and combined in FP32);
+//   PrecE  FP64 operator product, preconditioner, recurrences and projection (C, AC);
+//          double-float search directions W, AW, Z (48-bit significand), so that the
+//          reorthogonalisation's tall-skinny products run on the FP32 pipes.  The operator
+//          product reads the FP64 copy wv of w_j and writes q in FP64 (its double-float copy
+//          goes to AW).
+struct PrecD { using V = double; using M = double; using MC = double; using A = double; static constexpr int id = 0; };
+struct PrecF { using V = float;  using M = float;  using MC = float;  using A = float;  static constexpr int id = 1; };
+struct PrecP { using V = double; using M = float;  using MC = float;  using A = double; static constexpr int id = 2; };
+struct PrecE { using V = double; using M = dfl;    using MC = double; using A = double; static constexpr int id = 3; };
 
 template <typename Pr>
 struct ApcgCtx {
   using V = typename Pr::V;
   using M = typename Pr::M;
+  using MC = typename Pr::MC;
   using A = typename Pr::A;
   int64_t n, ld;       // order, leading dimension of multi-vectors and vector padding
   int nbr, npc, P;     // block rows, nodes per CTA, CTAs of this problem's group
@@ -67,8 +74,8 @@ struct ApcgCtx {
   const int* ci;
   const A* vals;
   const A* minv;
-  const M* C;
-  const M* AC;
+  const MC* C;
+  const MC* AC;
   const double* Ginv;
   M* W;
   M* AW;
@@ -76,7 +83,8 @@ struct ApcgCtx {
   V* x;
   V* r;
   V* u;
-  V* q;                // PrecP: the FP64 operator product A w_j (AW keeps its FP32 copy)
+  V* q;                // PrecP, PrecE: the FP64 operator product A w_j (AW keeps its copy)
+  V* wv;               // PrecE: the FP64 search direction w_j (W keeps its double-float copy)
   double* alpha;
   double* gamma;
   double* rho;
@@ -99,20 +107,25 @@ struct ApcgCtx {
 };
 
 // shared-memory layout (in doubles): su[ROW_CHUNK] | red[4*TPB] | sv[kmax]
-// (su and sv hold values of the multi-vector type M)
+// (su and sv hold values of the direction type M; svc is sv seen as the type MC of the
+// augmentation space, for the coarse coefficients s)
 template <typename Pr>
 struct Smem {
   typename Pr::M* su;
   double* red;
   typename Pr::M* sv;
+  typename Pr::MC* svc;
 };
 
 template <typename Pr>
 __device__ __forceinline__ Smem<Pr> smem_layout(double* base) {
+  static_assert(sizeof(typename Pr::M) <= sizeof(double) && sizeof(typename Pr::MC) <= sizeof(double),
+                "shared-memory slots hold one double");
   Smem<Pr> s;
   s.su = reinterpret_cast<typename Pr::M*>(base);
   s.red = base + ROW_CHUNK;
   s.sv = reinterpret_cast<typename Pr::M*>(base + ROW_CHUNK + 4 * TPB);
+  s.svc = reinterpret_cast<typename Pr::MC*>(base + ROW_CHUNK + 4 * TPB);
   return s;
 }
 
@@ -183,6 +196,8 @@ __device__ __forceinline__ void phase1(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm
   double wq = 0.0, rw = 0.0;
   if constexpr (Pr::id == 2)  // q in FP64 for the recurrences, its FP32 copy into AW
     cta_spmv<A, M, V, V>(c.rp, c.ci, c.vals, w, c.q, c.r, r0, r1, wq, rw, aw);
+  else if constexpr (Pr::id == 3)  // FP64 w_j and q; the double-float copy of q into AW
+    cta_spmv<A, V, V, V, M>(c.rp, c.ci, c.vals, c.wv, c.q, c.r, r0, r1, wq, rw, aw);
   else
     cta_spmv<A, M, M, V>(c.rp, c.ci, c.vals, w, aw, c.r, r0, r1, wq, rw);
   block_sum2(wq, rw, sm.red);
@@ -211,9 +226,12 @@ __device__ __forceinline__ int phase2(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm)
   const V alT = (V)al;
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, c.lb, r0, r1);
-  const M* w = c.W + (int64_t)j * c.ld;
+  using WT = typename std::conditional<Pr::id == 3, V, M>::type;
+  const WT* w;
+  if constexpr (Pr::id == 3) w = c.wv;
+  else w = c.W + (int64_t)j * c.ld;
   const V* q;
-  if constexpr (Pr::id == 2) q = c.q;
+  if constexpr (Pr::id == 2 || Pr::id == 3) q = c.q;
   else q = c.AW + (int64_t)j * c.ld;
   double rr = 0.0;
   for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
@@ -228,7 +246,8 @@ __device__ __forceinline__ int phase2(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm)
   rr = block_sum(rr, sm.red);
   if (threadIdx.x == 0) c.part[c.lb * PS_STRIDE + PS_RR] = rr;
   if (c.nc > 0)
-    cta_gemv_t<true, M, V>(c.AC, c.ld, c.nc, c.u, r0, r1, c.vpart + c.lb * c.vld, sm.su, sm.red);
+    cta_gemv_t<true, typename Pr::MC, V>(c.AC, c.ld, c.nc, c.u, r0, r1, c.vpart + c.lb * c.vld,
+                                         reinterpret_cast<typename Pr::MC*>(sm.su), sm.red);
   return PH_CONTINUE;
 }
 
@@ -241,7 +260,7 @@ __device__ __forceinline__ void col_slice(int k, int P, int b, int& a, int& e) {
 
 template <typename Pr>
 __device__ __forceinline__ int phase3(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm) {
-  using M = typename Pr::M;
+  using MC = typename Pr::MC;
   const double rr = grid_scalar(c.part, c.P, PS_RR, sm.red);
   if (rr <= c.tol2) {
     finish(c, 0, j + 1);
@@ -279,7 +298,7 @@ __device__ __forceinline__ int phase3(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm)
     for (int col = warp; col < c.nc; col += TPB / 32) {
       const double sacc = coarse_coef(c.Ginv, c.ldg, c.nc_dense, c.dinv, col, sm.red);
       if (lane == 0) {
-        sm.sv[col] = (M)sacc;
+        sm.svc[col] = (MC)sacc;
         if (c.lb == 0) c.sfull[col] = sacc;  // for the per-phase kernel mode
       }
     }
@@ -305,15 +324,16 @@ template <typename Pr>
 __device__ __forceinline__ void phase5(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm, bool s_in_smem) {
   using V = typename Pr::V;
   using M = typename Pr::M;
+  using MC = typename Pr::MC;
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, c.lb, r0, r1);
   M* z = c.Z + (int64_t)(j + 1) * c.ld;
   if (c.nc > 0) {
     if (!s_in_smem) {
-      for (int k = threadIdx.x; k < c.nc; k += TPB) sm.sv[k] = (M)c.sfull[k];
+      for (int k = threadIdx.x; k < c.nc; k += TPB) sm.svc[k] = (MC)c.sfull[k];
     }
     __syncthreads();
-    cta_gemv_n<true, M, V, M>(c.C, c.ld, c.nc, sm.sv, M(-1), c.u, z, r0, r1, sm.red);
+    cta_gemv_n<true, MC, V, M>(c.C, c.ld, c.nc, sm.svc, MC(-1), c.u, z, r0, r1, sm.red);
   } else {
     for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) z[row] = (M)c.u[row];
     __syncthreads();
@@ -359,7 +379,9 @@ __device__ __forceinline__ void phase7(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm
   __syncthreads();
   const M* z = c.Z + (int64_t)(j + 1) * c.ld;
   M* wn = c.W + (int64_t)(j + 1) * c.ld;
-  cta_gemv_n<false, M, M, M>(c.W + (int64_t)base * c.ld, c.ld, kk, sm.sv, M(-1), z, wn, r0, r1, sm.red);
+  double* wv = nullptr;
+  if constexpr (Pr::id == 3) wv = c.wv;  // the FP64 copy of w_{j+1} for the next operator product
+  cta_gemv_n<false, M, M, M>(c.W + (int64_t)base * c.ld, c.ld, kk, sm.sv, M(-1.0), z, wn, r0, r1, sm.red, wv);
 }
 
 // ------------------------------------------------------------------------------------
@@ -610,10 +632,12 @@ __global__ void k_precond_rows(int kind, const TA* minv, const TV* r, TV* u, int
   if (row < n) u[row] = precond_row<TA, TV>(kind, minv, r, row);
 }
 
-// z0 = u - C s (or u), stored as TZ: W[:,0] = Z[:,0] = z0, partial (r, z0) of the stored z0
+// z0 = u - C s (or u), stored as TZ: W[:,0] = Z[:,0] = z0, partial (r, z0) of the stored z0;
+// wv (optional): z0 = w0 also as a double
 template <typename TC, typename TV, typename TZ>
 __global__ void __launch_bounds__(TPB, 1) k_init_z(const TC* C, int64_t ld, int k, const double* s, const TV* u,
-                                                   const TV* r, TZ* Z, TZ* W, int nbr, int npc, double* part) {
+                                                   const TV* r, TZ* Z, TZ* W, int nbr, int npc, double* part,
+                                                   double* wv) {
   extern __shared__ double4_32a smem_raw4[];
   double* base = reinterpret_cast<double*>(smem_raw4);
   double* red = base + ROW_CHUNK;
@@ -623,9 +647,12 @@ __global__ void __launch_bounds__(TPB, 1) k_init_z(const TC* C, int64_t ld, int 
   if (k > 0) {
     for (int i = threadIdx.x; i < k; i += TPB) sv[i] = (TC)s[i];
     __syncthreads();
-    cta_gemv_n<false, TC, TV, TZ>(C, ld, k, sv, TC(-1), u, Z, r0, r1, red);
+    cta_gemv_n<false, TC, TV, TZ>(C, ld, k, sv, TC(-1), u, Z, r0, r1, red, wv);
   } else {
-    for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) Z[row] = (TZ)u[row];
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += TPB) {
+      Z[row] = (TZ)u[row];
+      if (wv) wv[row] = (double)u[row];
+    }
     __syncthreads();
   }
   double rz = 0.0;
@@ -669,10 +696,12 @@ static ApcgCtx<Pr> make_ctx(const IterArgs& a) {
   c.precond = a.precond; c.tol2 = a.tol2; c.spin_limit = a.spin_limit;
   c.rp = a.rp; c.ci = a.ci;
   c.vals = static_cast<const A*>(a.vals); c.minv = static_cast<const A*>(a.minv);
-  c.C = static_cast<const M*>(a.C); c.AC = static_cast<const M*>(a.AC); c.Ginv = a.Ginv;
+  c.C = static_cast<const typename Pr::MC*>(a.C); c.AC = static_cast<const typename Pr::MC*>(a.AC);
+  c.Ginv = a.Ginv;
   c.W = static_cast<M*>(a.W); c.AW = static_cast<M*>(a.AW); c.Z = static_cast<M*>(a.Z);
   c.x = static_cast<V*>(a.x); c.r = static_cast<V*>(a.r); c.u = static_cast<V*>(a.u);
   c.q = static_cast<V*>(a.q);
+  c.wv = static_cast<V*>(a.wv);
   c.alpha = a.alpha; c.gamma = a.gamma; c.rho = a.rho;
   c.tfull = a.tfull; c.sfull = a.sfull; c.gfull = a.gfull;
   c.part = a.part; c.vpart = a.vpart; c.gpart = a.gpart; c.vld = a.vld; c.ctrl = a.ctrl; c.bar = a.bar;
@@ -687,10 +716,11 @@ static ApcgCtx<Pr> make_ctx(const IterArgs& a) {
 }
 
 // init element types: the init stage of PrecP works from the FP64 C and AC (x_0 and r_0 in
-// FP64, consistent with the FP64 recurrences) and stores z_0 in FP32
+// FP64, consistent with the FP64 recurrences) and stores z_0 in FP32; PrecE's C and AC are
+// FP64 and it stores z_0 in double-float
 template <typename Pr>
 struct InitTypes {
-  using TC = typename std::conditional<Pr::id == 2, double, typename Pr::M>::type;
+  using TC = typename std::conditional<Pr::id == 2, double, typename Pr::MC>::type;
 };
 
 template <typename Pr>
@@ -698,11 +728,13 @@ static cudaError_t prepare_attributes_t(size_t sm) {
   using V = typename Pr::V;
   using M = typename Pr::M;
   using TC = typename InitTypes<Pr>::TC;
+  // the init kernels over C and AC of type TC, and (PrecP's restarted passes, PrecF) of type M
+  using TM = typename std::conditional<Pr::id == 3, double, M>::type;
   const void* fns[] = {(const void*)k_apcg_persistent<Pr>, (const void*)k_phase1<Pr>, (const void*)k_phase2<Pr>,
                        (const void*)k_phase3<Pr>, (const void*)k_phase4<Pr>, (const void*)k_phase5<Pr>,
                        (const void*)k_phase6<Pr>, (const void*)k_phase7<Pr>, (const void*)k_gemv_t_part<TC, V>,
                        (const void*)k_init_xr<TC, V>, (const void*)k_init_z<TC, V, M>,
-                       (const void*)k_gemv_t_part<M, V>, (const void*)k_init_xr<M, V>, (const void*)k_init_z<M, V, M>};
+                       (const void*)k_gemv_t_part<TM, V>, (const void*)k_init_xr<TM, V>, (const void*)k_init_z<TM, V, M>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -710,7 +742,7 @@ static cudaError_t prepare_attributes_t(size_t sm) {
   return cudaSuccess;
 }
 
-// Dispatch on the precision id of IterArgs (0 PrecD, 1 PrecF, 2 PrecP).
+// Dispatch on the precision id of IterArgs (0 PrecD, 1 PrecF, 2 PrecP, 3 PrecE).
 #define KRS_DISPATCH(prec, CALL)           \
   do {                                     \
     if ((prec) == 1) {                     \
@@ -718,6 +750,9 @@ static cudaError_t prepare_attributes_t(size_t sm) {
       CALL;                                \
     } else if ((prec) == 2) {              \
       using PR = PrecP;                    \
+      CALL;                                \
+    } else if ((prec) == 3) {              \
+      using PR = PrecE;                    \
       CALL;                                \
     } else {                               \
       using PR = PrecD;                    \
@@ -730,11 +765,11 @@ static cudaError_t prepare_attributes_t(size_t sm) {
 // smaller kmax) prepared the same kernels.
 cudaError_t apcg_prepare_attributes(int kmax, int prec) {
   static std::mutex mu;
-  static size_t set_bytes[64][3] = {};
+  static size_t set_bytes[64][4] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || prec < 0 || prec > 2) return cudaErrorInvalidValue;
+  if (dev < 0 || dev >= 64 || prec < 0 || prec > 3) return cudaErrorInvalidValue;
   const size_t sm = apcg_smem_bytes(kmax);
   std::lock_guard<std::mutex> lock(mu);
   size_t& cur = set_bytes[dev][prec];
@@ -782,7 +817,7 @@ static cudaError_t launch_init_t(const IterArgs& a, const void* bv, double* scal
     *launches += 3;
   }
   k_init_z<TC, V, M><<<a.P, TPB, sm, st>>>(C, a.ld, k, a.sfull, u, r, static_cast<M*>(a.Z), static_cast<M*>(a.W),
-                                           a.nbr, a.npc, a.part);
+                                           a.nbr, a.npc, a.part, Pr::id == 3 ? static_cast<double*>(a.wv) : nullptr);
   k_init_finish<<<1, 96, 0, st>>>(a.part, a.P, scal, a.rho);
   *launches += 2;
   return cudaGetLastError();
@@ -797,6 +832,7 @@ cudaError_t apcg_launch_init(const IterArgs& a, const void* b, double* scal, cud
     return a.init32 ? launch_init_t<PrecP, float>(a, b, scal, st, launches)
                     : launch_init_t<PrecP, double>(a, b, scal, st, launches);
   if (a.prec == 1) return launch_init_t<PrecF, float>(a, b, scal, st, launches);
+  if (a.prec == 3) return launch_init_t<PrecE, double>(a, b, scal, st, launches);
   return launch_init_t<PrecD, double>(a, b, scal, st, launches);
 }
 
@@ -816,7 +852,8 @@ cudaError_t apcg_launch_persistent(const IterArgs& a, cudaStream_t st, int64_t* 
 }
 
 size_t apcg_ctx_bytes() {
-  static_assert(sizeof(ApcgCtx<PrecD>) == sizeof(ApcgCtx<PrecP>) && sizeof(ApcgCtx<PrecD>) == sizeof(ApcgCtx<PrecF>),
+  static_assert(sizeof(ApcgCtx<PrecD>) == sizeof(ApcgCtx<PrecP>) && sizeof(ApcgCtx<PrecD>) == sizeof(ApcgCtx<PrecF>) &&
+                    sizeof(ApcgCtx<PrecD>) == sizeof(ApcgCtx<PrecE>),
                 "one context size for every precision");
   return sizeof(ApcgCtx<PrecD>);
 }
@@ -847,7 +884,8 @@ __global__ void k_gather_ctrl(const ApcgCtx<PrecD>* __restrict__ ctxs, int count
 
 cudaError_t apcg_gather_ctrl(const void* ctxs, int count, int* out, cudaStream_t st) {
   static_assert(offsetof(ApcgCtx<PrecD>, ctrl) == offsetof(ApcgCtx<PrecP>, ctrl) &&
-                    offsetof(ApcgCtx<PrecD>, ctrl) == offsetof(ApcgCtx<PrecF>, ctrl),
+                    offsetof(ApcgCtx<PrecD>, ctrl) == offsetof(ApcgCtx<PrecF>, ctrl) &&
+                    offsetof(ApcgCtx<PrecD>, ctrl) == offsetof(ApcgCtx<PrecE>, ctrl),
                 "control pointer at one offset");
   if (count <= 0) return cudaSuccess;
   k_gather_ctrl<<<(4 * count + 255) / 256, 256, 0, st>>>(static_cast<const ApcgCtx<PrecD>*>(ctxs), count, out);

@@ -27,6 +27,7 @@ namespace krs {
 cudaError_t launch_tridiag_eigvals2(int m, int m1, const double* delta, const double* eta, double* theta_m,
                                     double* theta_m1, cudaStream_t st);
 }
+static cudaError_t launch_df2d(const dfl* src, double* dst, int64_t count, cudaStream_t st);
 
 static thread_local std::string g_last_error;
 
@@ -446,7 +447,7 @@ krs_status krs_release(krs_seq_t s, int32_t what) {
     drop(s->alpha); drop(s->gamma); drop(s->rho); drop(s->gfull);
     s->cap_w = 0;
     s->cap_sc = 0;
-    drop(s->q64); drop(s->xacc); drop(s->rres); drop(s->rrh);
+    drop(s->q64); drop(s->wv); drop(s->xacc); drop(s->rres); drop(s->rrh);
     s->rrh_cap = 0;
     drop(s->vpart); drop(s->gpart); drop(s->part); drop(s->tfull); drop(s->sfull);
     s->vpart_P = 0;
@@ -530,12 +531,20 @@ krs_status krs_last_vectors(krs_seq_t s, int32_t which, double* out) {
   if (!out) return fail(KRS_ERR_INVALID_ARG, "NULL output");
   KRS_CUDA(cudaSetDevice(s->device));
   const double* src = which == 0 ? s->W : (which == 1 ? s->AW : s->Z);
-  if (!src || s->last_prec != KRS_FP64)
+  if (!src || !single_pass(s->last_prec))
     return fail(KRS_ERR_INVALID_ARG, "the last solve stored no FP64 vectors (mixed precision)");
+  double* tmp = nullptr;
+  if (s->last_prec == KRS_DOUBLE_FLOAT) {  // double-float pairs -> doubles
+    KRS_TRY(alloc_n(s, &tmp, (size_t)m * s->ld));
+    KRS_CUDA(launch_df2d(reinterpret_cast<const dfl*>(src), tmp, (int64_t)m * s->ld, s->stream));
+    src = tmp;
+  }
   const bool dv = is_device_ptr(out);
-  KRS_CUDA(cudaMemcpy2DAsync(out, sizeof(double) * s->n, src, sizeof(double) * s->ld, sizeof(double) * s->n, m,
-                             dv ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
-  KRS_CUDA(cudaStreamSynchronize(s->stream));
+  cudaError_t e = cudaMemcpy2DAsync(out, sizeof(double) * s->n, src, sizeof(double) * s->ld, sizeof(double) * s->n, m,
+                                    dv ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  dev_free(s, tmp);
+  KRS_CUDA(e);
   return KRS_OK;
 }
 
@@ -549,7 +558,8 @@ krs_status krs::validate_policy(const krs_policy* p) {
   if (p->recycle < 0 || p->recycle > 2) return fail(KRS_ERR_INVALID_ARG, "bad recycle %d", p->recycle);
   if (p->precond < 0 || p->precond > 2) return fail(KRS_ERR_INVALID_ARG, "bad precond %d", p->precond);
   if (p->reorth < 0 || p->reorth > 1) return fail(KRS_ERR_INVALID_ARG, "bad reorth %d", p->reorth);
-  if (p->precision != KRS_FP64 && p->precision != KRS_MIXED_IR && p->precision != KRS_MIXED_PROJ)
+  if (p->precision != KRS_FP64 && p->precision != KRS_MIXED_IR && p->precision != KRS_MIXED_PROJ &&
+      p->precision != KRS_DOUBLE_FLOAT)
     return fail(KRS_ERR_INVALID_ARG, "bad precision %d", p->precision);
   if (!(p->inner_tol == p->inner_tol) || p->inner_tol >= 1.0) return fail(KRS_ERR_INVALID_ARG, "inner_tol must be < 1");
   if (p->cap_mode < 0 || p->cap_mode > 1) return fail(KRS_ERR_INVALID_ARG, "bad cap_mode %d", p->cap_mode);
@@ -768,8 +778,9 @@ static krs_status srks_begin(krs_seq* s, int m, int room, const krs_policy* p, i
 
 // SRKS, second half (after the stream was synchronised): eigenvectors of the selected
 // values and the Ritz vectors, written to C[:, nc .. nc + *cnt) (not yet counted in s->nc).
+// The z's: Z32 (FP32) when given, else Z -- FP64, or double-float pairs when z_df.
 static krs_status srks_finish(krs_seq* s, int m, int nc, const double* Z, const float* Z32, int* cnt,
-                              int64_t* launches, bool can_grow) {
+                              int64_t* launches, bool can_grow, bool z_df = false) {
   *cnt = 0;
   const int k = s->h_ctrl[16];
   s->last_nsel = k;
@@ -789,6 +800,9 @@ static krs_status srks_finish(krs_seq* s, int m, int nc, const double* Z, const 
   if (Z32)
     KRS_CUDA(launch_ritz_vectors_f(s->n, s->ld, m, k, Z32, s->rho, Q, s->tsel, Fm, s->C + (size_t)nc * s->ld,
                                    s->stream));
+  else if (z_df)
+    KRS_CUDA(launch_ritz_vectors_df(s->n, s->ld, m, k, reinterpret_cast<const dfl*>(Z), s->rho, Q, s->tsel, Fm,
+                                    s->C + (size_t)nc * s->ld, s->stream));
   else
     KRS_CUDA(launch_ritz_vectors(s->n, s->ld, m, k, Z, s->rho, Q, s->tsel, Fm, s->C + (size_t)nc * s->ld, s->stream));
   *launches += 3;
@@ -817,6 +831,19 @@ __global__ void k_f2d_cols(const float* __restrict__ src, double* __restrict__ d
     dst[i] = (double)src[i];
 }
 
+__global__ void k_df2d(const dfl* __restrict__ src, double* __restrict__ dst, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+// dst = src as doubles (count double-float pairs; dst may not overlap src)
+static cudaError_t launch_df2d(const dfl* src, double* dst, int64_t count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const int64_t blocks = (count + 255) / 256;
+  k_df2d<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
 // Set-up shared by both precisions: matrix, preconditioner, right-hand side, storage,
 // partition, coarse set-up (FP64), the FP32 copies (mixed), and the iteration arguments.
 // cap_iter: direction columns reserved (FP64 path).
@@ -832,7 +859,8 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   int64_t& launches = ss->launches;
   const bool mixed = p->precision == KRS_MIXED_IR;
   const bool proj = p->precision == KRS_MIXED_PROJ;
-  const int prec = mixed ? 1 : (proj ? 2 : 0);
+  const bool dfk = p->precision == KRS_DOUBLE_FLOAT;
+  const int prec = prec_id(p->precision);
   s->last_prec = p->precision;
   KRS_CUDA(cudaSetDevice(s->device));
   KRS_CUDA(cudaEventRecord(s->ev[0], s->stream));
@@ -880,6 +908,10 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   } else {
     KRS_TRY(ensure_cap_c(s, nc));
     KRS_TRY(ensure_cap_w(s, cap_iter));
+    if (dfk) {  // the FP64 copies of w_j and A w_j beside the double-float directions
+      if (!s->q64) KRS_TRY(alloc_n(s, &s->q64, s->ld));
+      if (!s->wv) KRS_TRY(alloc_n(s, &s->wv, s->ld));
+    }
   }
   // largest column count a tall-skinny phase sees (mixed: C plus earlier inner directions)
   const int kmax = (mixed || proj) ? nc + p->max_iter + 1 : ((nc > cap_iter + 1) ? nc : cap_iter + 1);
@@ -975,8 +1007,13 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
     a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.x = s->x; a.r = s->r; a.u = s->u; a.q = s->q64;
     a.stall_win = 32; a.rrh = s->rrh;
   } else {
+    // KRS_DOUBLE_FLOAT: W, AW, Z hold double-float pairs (8 bytes, like the FP64 directions)
     a.vals = s->vals_use; a.minv = s->minv; a.C = s->C; a.AC = s->AC;
     a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.x = s->x; a.r = s->r; a.u = s->u;
+    if (dfk) {
+      a.q = s->q64;
+      a.wv = s->wv;
+    }
   }
   KRS_CUDA(cudaEventRecord(s->ev[1], s->stream));
   return KRS_OK;
@@ -984,7 +1021,7 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
 
 krs_status krs::seq_begin(krs_seq* s, const krs_bsr* A, const double* b, double tol, const krs_policy* p,
                           int cap_iter, SolveState* ss) {
-  if (p->precision != KRS_FP64) return fail(KRS_ERR_INVALID_ARG, "internal: seq_begin is the FP64 path");
+  if (!single_pass(p->precision)) return fail(KRS_ERR_INVALID_ARG, "internal: seq_begin is the single-pass path");
   ss->tol = tol;
   KRS_TRY(seq_setup(s, A, b, p, cap_iter, ss));
   KRS_TRY(run_init(s, ss->a, s->b, tol, &ss->bb, &ss->rr0, &ss->launches));
@@ -1036,22 +1073,35 @@ krs_status krs::seq_end_stage(krs_seq* s, SolveState* ss, int status, int m, dou
   if (stage == 2) {
     if (!mixed && status == KRS_OK) {
       // ---- FP64: the recycling step on this solve's W / Z
+      const bool dfk = p->precision == KRS_DOUBLE_FLOAT;  // W, AW, Z hold double-float pairs
       if (p->recycle == KRS_RECYCLE_TRKS && m > 0) {
         const int add = m < ss->room ? m : ss->room;
         if (add > 0) {
           KRS_TRY(ensure_cap_c(s, nc + add));
-          KRS_CUDA(cudaMemcpyAsync(s->C + (size_t)nc * s->ld, s->W, sizeof(double) * (size_t)add * s->ld,
-                                   cudaMemcpyDeviceToDevice, s->stream));
+          if (dfk) {
+            KRS_CUDA(launch_df2d(reinterpret_cast<const dfl*>(s->W), s->C + (size_t)nc * s->ld, (int64_t)add * s->ld,
+                                 s->stream));
+            launches++;
+          } else {
+            KRS_CUDA(cudaMemcpyAsync(s->C + (size_t)nc * s->ld, s->W, sizeof(double) * (size_t)add * s->ld,
+                                     cudaMemcpyDeviceToDevice, s->stream));
+          }
           if (s->ac_valid == nc) {
             // A is unchanged since the directions' products were formed: A W is A C's new block
-            KRS_CUDA(cudaMemcpyAsync(s->AC + (size_t)nc * s->ld, s->AW, sizeof(double) * (size_t)add * s->ld,
-                                     cudaMemcpyDeviceToDevice, s->stream));
+            if (dfk) {
+              KRS_CUDA(launch_df2d(reinterpret_cast<const dfl*>(s->AW), s->AC + (size_t)nc * s->ld,
+                                   (int64_t)add * s->ld, s->stream));
+              launches++;
+            } else {
+              KRS_CUDA(cudaMemcpyAsync(s->AC + (size_t)nc * s->ld, s->AW, sizeof(double) * (size_t)add * s->ld,
+                                       cudaMemcpyDeviceToDevice, s->stream));
+            }
             s->ac_valid = nc + add;
           }
         }
         ss->add = add;
       } else if (srks) {
-        KRS_TRY(srks_finish(s, m, nc, s->Z, nullptr, &ss->add, &launches, true));
+        KRS_TRY(srks_finish(s, m, nc, s->Z, nullptr, &ss->add, &launches, true, dfk));
       }
     }
     // ---- result and true residual

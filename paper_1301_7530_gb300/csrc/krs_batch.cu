@@ -239,7 +239,7 @@ static IterArgs group_args(const Entry* e, int64_t vld) {
   const int g = e->g;
   krs_seq* s = e->s;
   IterArgs a = e->ss.a;
-  if (e->p.precision == KRS_FP64) {  // FP64 storage may have grown since the set-up
+  if (single_pass(e->p.precision)) {  // FP64 / double-float storage may have grown since the set-up
     a.W = s->W; a.AW = s->AW; a.Z = s->Z;
     a.alpha = s->alpha; a.gamma = s->gamma; a.rho = s->rho; a.gfull = s->gfull;
   }
@@ -344,7 +344,7 @@ static krs_status launch_once(krs_batch* b, std::vector<Entry*>& run, int quantu
     kmax = std::max(kmax, std::max(std::max(e->ss.nc, e->ss.a.nc), dir_cap(e->s, e->p.precision)));
   const int64_t vld = round_up(kmax + 1, 32);
   int bps = 0;
-  const int prec = queued[0]->p.precision == KRS_MIXED_IR ? 1 : 0;  // one precision per launch
+  const int prec = prec_id(queued[0]->p.precision);  // one precision per launch
   KRS_CUDA(apcg_batched_coresident(kmax, prec, &bps));
   if (bps < 1) return failf(KRS_ERR_CUDA, "batch: persistent kernel cannot be resident (kmax %d)", kmax);
   KRS_TRY(ensure_table(b, count));
@@ -479,8 +479,8 @@ static krs_status autotune(krs_batch* b, std::vector<Entry*>& run) {
     b->scale = r;
     float ms = 0.f;
     double ri = 0.0;
-    std::vector<Entry*> part[2];
-    for (Entry* e : run) part[e->p.precision == KRS_MIXED_IR ? 1 : 0].push_back(e);
+    std::vector<Entry*> part[4];
+    for (Entry* e : run) part[prec_id(e->p.precision)].push_back(e);
     for (auto& pr : part) {
       if (pr.empty()) continue;
       float ms1 = 0.f;
@@ -641,7 +641,7 @@ krs_status krs_batch_submit(krs_batch_t b, krs_seq_t s, const krs_bsr* A, const 
   if (s->device != b->device) return failf(KRS_ERR_INVALID_ARG, "sequence and batch are on different devices");
   KRS_TRY(validate_policy(p));
   if (p->precision == KRS_MIXED_PROJ)
-    return failf(KRS_ERR_INVALID_ARG, "batched solves run in KRS_FP64 or KRS_MIXED_IR");
+    return failf(KRS_ERR_INVALID_ARG, "batched solves run in KRS_FP64, KRS_DOUBLE_FLOAT or KRS_MIXED_IR");
   if (p->max_iter < 1 || p->max_iter > 16000) return failf(KRS_ERR_INVALID_ARG, "max_iter %d outside [1, 16000]", p->max_iter);
   Entry* e = new (std::nothrow) Entry();
   if (!e) return failf(KRS_ERR_OOM, "host allocation failed");
@@ -674,7 +674,7 @@ krs_status krs_batch_submit(krs_batch_t b, krs_seq_t s, const krs_bsr* A, const 
     delete e;
     return st;
   }
-  if (p->precision == KRS_FP64 && !e->ss.need_iter) e->ended = true;  // ||r_0|| within tolerance: m = 0
+  if (single_pass(p->precision) && !e->ss.need_iter) e->ended = true;  // ||r_0|| within tolerance: m = 0
   b->entries.push_back(e);
   return KRS_OK;
 }
@@ -691,13 +691,13 @@ krs_status krs_batch_step(krs_batch_t b, int32_t max_done, int64_t* done_tags, i
   if (!run.empty()) {
     if (b->cfg.group_ctas == 0 && b->scale == 0) {
       bool fresh = true;  // (refinement passes change state the probe could not restore)
-      for (Entry* e : run) fresh = fresh && e->j == 0 && e->g == 0 && e->p.precision == KRS_FP64;
+      for (Entry* e : run) fresh = fresh && e->j == 0 && e->g == 0 && single_pass(e->p.precision);
       if (fresh) KRS_TRY(autotune(b, run));
       if (b->scale == 0) b->scale = 100;
     }
     // one launch per precision present (each launch runs one kernel instantiation)
-    std::vector<Entry*> part[2];
-    for (Entry* e : run) part[e->p.precision == KRS_MIXED_IR ? 1 : 0].push_back(e);
+    std::vector<Entry*> part[4];
+    for (Entry* e : run) part[prec_id(e->p.precision)].push_back(e);
     for (auto& pr : part) {
       if (pr.empty()) continue;
       float ms = 0.f;

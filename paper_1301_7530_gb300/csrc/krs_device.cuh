@@ -154,9 +154,75 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* counter, unsign
 }
 
 // ------------------------------------------------------------------------------------
+// Double-float numbers (Dekker 1971; Knuth, TAOCP vol. 2, 4.2.2): a value hi + lo held as
+// two FP32 numbers with |lo| <= ulp(hi) / 2, i.e. a 48-bit significand in 8 bytes.  On
+// GB300 an FP64 instruction retires 2 lanes per clock per SM against 128 for FP32, so a
+// tall-skinny product over double-float storage runs on the FP32 pipes (about 12 FP32
+// operations per element) and is bound by memory, not by the FP64 pipe.  Conversions
+// to and from double use FP64 arithmetic and appear only O(n) times per iteration.
+// Range: FP32 exponents (|values| within about 1e-30 .. 1e38 keep the full significand).
+// ------------------------------------------------------------------------------------
+struct __align__(8) dfl {
+  float hi, lo;
+  dfl() = default;
+  __host__ __device__ __forceinline__ explicit dfl(double d) {
+    hi = (float)d;
+    lo = (float)(d - (double)hi);  // d - hi is exact in double
+  }
+  __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+struct __align__(16) dfl4 { dfl x, y, z, w; };
+struct __align__(16) dfl2 { dfl x, y; };
+
+// Running sum of products in double-float form: s + c, with every product x * y taken
+// exactly to 2^-48 relative (error-free FP32 product of the high parts by FMA, plus the
+// two cross terms) and added to s by an error-free two-sum whose error goes to c.
+struct dacc {
+  float s, c;
+};
+__device__ __forceinline__ void dacc_add(dacc& a, float p, float e) {
+  const float s = __fadd_rn(a.s, p);
+  const float bp = __fsub_rn(s, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  a.c = __fadd_rn(a.c, __fadd_rn(err, e));
+  a.s = s;
+}
+
+// Accumulator of a product stream over values of type T: T itself for double and float
+// (a += x * y, one FMA), dacc for double-float.  out(): the accumulated value as the type
+// the per-thread results are combined in (T, or double for double-float).
+template <typename T>
+struct Acc {
+  using type = T;
+  using out_t = T;
+  __device__ static __forceinline__ T zero() { return T(0); }
+  __device__ static __forceinline__ void mac(T& a, T x, T y) { a += x * y; }
+  __device__ static __forceinline__ T out(T a) { return a; }
+  __device__ static __forceinline__ double fold4(T a0, T a1, T a2, T a3) { return (double)((a0 + a1) + (a2 + a3)); }
+};
+template <>
+struct Acc<dfl> {
+  using type = dacc;
+  using out_t = double;
+  __device__ static __forceinline__ dacc zero() { return dacc{0.f, 0.f}; }
+  __device__ static __forceinline__ void mac(dacc& a, dfl x, dfl y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    dacc_add(a, p, e);
+  }
+  __device__ static __forceinline__ double out(dacc a) { return (double)a.s + (double)a.c; }
+  __device__ static __forceinline__ double fold4(dacc a0, dacc a1, dacc a2, dacc a3) {
+    return (out(a0) + out(a1)) + (out(a2) + out(a3));
+  }
+};
+
+// ------------------------------------------------------------------------------------
 // Value types.  The FP64 path instantiates everything with T = double; the inner solve of
 // the mixed-precision refinement with T = float (storage and arithmetic), while every
-// partial sum that crosses CTAs is a double.
+// partial sum that crosses CTAs is a double.  Double-float storage (T = dfl) holds the
+// search directions of the double-float precision.
 // ------------------------------------------------------------------------------------
 template <typename T>
 struct VT;
@@ -173,6 +239,12 @@ struct VT<float> {
   using V4 = float4;  // four rows, 16 bytes
   using V2 = float2;  // 8 bytes
   __device__ static __forceinline__ V4 make4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+template <>
+struct VT<dfl> {
+  using V4 = dfl4;  // four rows, 32 bytes
+  using V2 = dfl2;
+  __device__ static __forceinline__ V4 make4(dfl a, dfl b, dfl c, dfl d) { return dfl4{a, b, c, d}; }
 };
 
 // Load of four consecutive rows of data that is read-only for the whole kernel (NC = true:
@@ -198,6 +270,24 @@ __device__ __forceinline__ float4 ld4<true, float>(const float* p) {
 template <>
 __device__ __forceinline__ float4 ld4<false, float>(const float* p) {
   return *reinterpret_cast<const float4*>(p);
+}
+template <>
+__device__ __forceinline__ dfl4 ld4<true, dfl>(const dfl* p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(p + 2));
+  dfl4 v;
+  v.x.hi = a.x; v.x.lo = a.y; v.y.hi = a.z; v.y.lo = a.w;
+  v.z.hi = b.x; v.z.lo = b.y; v.w.hi = b.z; v.w.lo = b.w;
+  return v;
+}
+template <>
+__device__ __forceinline__ dfl4 ld4<false, dfl>(const dfl* p) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 2);
+  dfl4 v;
+  v.x.hi = a.x; v.x.lo = a.y; v.y.hi = a.z; v.y.lo = a.w;
+  v.z.hi = b.x; v.z.lo = b.y; v.w.hi = b.z; v.w.lo = b.w;
+  return v;
 }
 
 // Four consecutive rows of a vector of type TU, as the four-row vector of type T.
@@ -230,13 +320,14 @@ __device__ __forceinline__ void cta_gemv_t_few(const T* __restrict__ V, int64_t 
     const int qa = (int)((int64_t)q4 * g / Gw), qb = (int)((int64_t)q4 * (g + 1) / Gw);
     const T* col = V + (int64_t)c * ld + r0;
     const TU* uu = u + r0;
-    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    using AC = Acc<T>;
+    typename AC::type a0 = AC::zero(), a1 = AC::zero(), a2 = AC::zero(), a3 = AC::zero();
     for (int q = qa + lane; q < qb; q += 32) {
       const V4 x = ld4<NC, T>(col + 4 * q);
       const V4 y = load4_as<T, TU>(uu + 4 * q);
-      a0 += x.x * y.x; a1 += x.y * y.y; a2 += x.z * y.z; a3 += x.w * y.w;
+      AC::mac(a0, x.x, y.x); AC::mac(a1, x.y, y.y); AC::mac(a2, x.z, y.z); AC::mac(a3, x.w, y.w);
     }
-    double v = (double)((a0 + a1) + (a2 + a3));
+    double v = AC::fold4(a0, a1, a2, a3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[warp] = v;
@@ -281,7 +372,8 @@ __device__ __forceinline__ void cta_gemv_t(const T* __restrict__ V, int64_t ld, 
     const int kc = min(rem, TPB / G);
     const int c = t % kc;
     const int g = t / kc;
-    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    using AC = Acc<T>;
+    typename AC::type a0 = AC::zero(), a1 = AC::zero(), a2 = AC::zero(), a3 = AC::zero();
     for (int64_t ch = 0; ch < rows4; ch += ROW_CHUNK) {
       const int len = (int)kmin64(ROW_CHUNK, rows4 - ch);
       if (!one_chunk) {
@@ -299,19 +391,19 @@ __device__ __forceinline__ void cta_gemv_t(const T* __restrict__ V, int64_t ld, 
           const V4 x0 = ld4<NC, T>(col + 4 * q), x1 = ld4<NC, T>(col + 4 * q + 4);
           const V4 x2 = ld4<NC, T>(col + 4 * q + 8), x3 = ld4<NC, T>(col + 4 * q + 12);
           const V4 y0 = s4[q], y1 = s4[q + 1], y2 = s4[q + 2], y3 = s4[q + 3];
-          a0 += x0.x * y0.x; a1 += x0.y * y0.y; a2 += x0.z * y0.z; a3 += x0.w * y0.w;
-          a0 += x1.x * y1.x; a1 += x1.y * y1.y; a2 += x1.z * y1.z; a3 += x1.w * y1.w;
-          a0 += x2.x * y2.x; a1 += x2.y * y2.y; a2 += x2.z * y2.z; a3 += x2.w * y2.w;
-          a0 += x3.x * y3.x; a1 += x3.y * y3.y; a2 += x3.z * y3.z; a3 += x3.w * y3.w;
+          AC::mac(a0, x0.x, y0.x); AC::mac(a1, x0.y, y0.y); AC::mac(a2, x0.z, y0.z); AC::mac(a3, x0.w, y0.w);
+          AC::mac(a0, x1.x, y1.x); AC::mac(a1, x1.y, y1.y); AC::mac(a2, x1.z, y1.z); AC::mac(a3, x1.w, y1.w);
+          AC::mac(a0, x2.x, y2.x); AC::mac(a1, x2.y, y2.y); AC::mac(a2, x2.z, y2.z); AC::mac(a3, x2.w, y2.w);
+          AC::mac(a0, x3.x, y3.x); AC::mac(a1, x3.y, y3.y); AC::mac(a2, x3.z, y3.z); AC::mac(a3, x3.w, y3.w);
         }
         for (; q < qb; q++) {
           const V4 x0 = ld4<NC, T>(col + 4 * q), y0 = s4[q];
-          a0 += x0.x * y0.x; a1 += x0.y * y0.y; a2 += x0.z * y0.z; a3 += x0.w * y0.w;
+          AC::mac(a0, x0.x, y0.x); AC::mac(a1, x0.y, y0.y); AC::mac(a2, x0.z, y0.z); AC::mac(a3, x0.w, y0.w);
         }
       }
     }
     __syncthreads();
-    if (g < G) red[g * kc + c] = (double)((a0 + a1) + (a2 + a3));
+    if (g < G) red[g * kc + c] = AC::fold4(a0, a1, a2, a3);
     __syncthreads();
     // combine the G row groups: pairwise tree (fixed order), log2(G) parallel rounds
     for (int st = 1; st < G; st <<= 1) {
@@ -328,11 +420,17 @@ __device__ __forceinline__ void cta_gemv_t(const T* __restrict__ V, int64_t ld, 
 // Thread per 4 rows (four independent accumulators), four-column unroll; quads are taken
 // in blocks of qc with G = ceil(TPB / remaining quads) column groups each (qc = TPB / G),
 // combined by a pairwise tree in a fixed order.  s: shared (k values of T).  red: shared
-// scratch of TPB four-row vectors of T.
+// scratch of TPB four-row vectors of T (32 bytes each for double-float).  Double-float
+// V: the column sums are formed in double-float and combined in double.  z2 (optional):
+// the same result also stored as a double.
 template <bool NC, typename T, typename TU = T, typename TZ = T>
 __device__ __forceinline__ void cta_gemv_n(const T* __restrict__ V, int64_t ld, int k, const T* s, T sgn,
-                                           const TU* u, TZ* z, int64_t r0, int64_t r1, void* red) {
+                                           const TU* u, TZ* z, int64_t r0, int64_t r1, void* red,
+                                           double* z2 = nullptr) {
   using V4 = typename VT<T>::V4;
+  using AC = Acc<T>;
+  using FT = typename AC::out_t;          // type the column groups are combined in
+  using F4 = typename VT<FT>::V4;
   const int t = threadIdx.x;
   const int64_t L = r1 - r0;
   const int64_t q4 = (L + 3) >> 2;
@@ -344,7 +442,7 @@ __device__ __forceinline__ void cta_gemv_n(const T* __restrict__ V, int64_t ld, 
     const int nq = (int)kmin64(remq, TPB / G);
     const int q = t % nq;
     const int g = t / nq;
-    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    typename AC::type a0 = AC::zero(), a1 = AC::zero(), a2 = AC::zero(), a3 = AC::zero();
     if (g < G && k > 0) {
       const int ca = (int)((int64_t)k * g / G), cbnd = (int)((int64_t)k * (g + 1) / G);
       const int64_t row = r0 + 4 * (qb0 + q);
@@ -355,43 +453,49 @@ __device__ __forceinline__ void cta_gemv_n(const T* __restrict__ V, int64_t ld, 
         const V4 v2 = ld4<NC, T>(V + (int64_t)(c + 2) * ld + row);
         const V4 v3 = ld4<NC, T>(V + (int64_t)(c + 3) * ld + row);
         const T s0 = s[c], s1 = s[c + 1], s2 = s[c + 2], s3 = s[c + 3];
-        a0 += v0.x * s0; a1 += v0.y * s0; a2 += v0.z * s0; a3 += v0.w * s0;
-        a0 += v1.x * s1; a1 += v1.y * s1; a2 += v1.z * s1; a3 += v1.w * s1;
-        a0 += v2.x * s2; a1 += v2.y * s2; a2 += v2.z * s2; a3 += v2.w * s2;
-        a0 += v3.x * s3; a1 += v3.y * s3; a2 += v3.z * s3; a3 += v3.w * s3;
+        AC::mac(a0, v0.x, s0); AC::mac(a1, v0.y, s0); AC::mac(a2, v0.z, s0); AC::mac(a3, v0.w, s0);
+        AC::mac(a0, v1.x, s1); AC::mac(a1, v1.y, s1); AC::mac(a2, v1.z, s1); AC::mac(a3, v1.w, s1);
+        AC::mac(a0, v2.x, s2); AC::mac(a1, v2.y, s2); AC::mac(a2, v2.z, s2); AC::mac(a3, v2.w, s2);
+        AC::mac(a0, v3.x, s3); AC::mac(a1, v3.y, s3); AC::mac(a2, v3.z, s3); AC::mac(a3, v3.w, s3);
       }
       for (; c < cbnd; c++) {
         const V4 v0 = ld4<NC, T>(V + (int64_t)c * ld + row);
         const T s0 = s[c];
-        a0 += v0.x * s0; a1 += v0.y * s0; a2 += v0.z * s0; a3 += v0.w * s0;
+        AC::mac(a0, v0.x, s0); AC::mac(a1, v0.y, s0); AC::mac(a2, v0.z, s0); AC::mac(a3, v0.w, s0);
       }
     }
+    FT f0 = AC::out(a0), f1 = AC::out(a1), f2 = AC::out(a2), f3 = AC::out(a3);
     if (G > 1) {
       __syncthreads();
-      V4* r4 = reinterpret_cast<V4*>(red);
-      if (g < G) r4[g * nq + q] = VT<T>::make4(a0, a1, a2, a3);
+      F4* r4 = reinterpret_cast<F4*>(red);
+      if (g < G) r4[g * nq + q] = VT<FT>::make4(f0, f1, f2, f3);
       __syncthreads();
       // pairwise tree over the G column groups (fixed order), log2(G) parallel rounds
       for (int st = 1; st < G; st <<= 1) {
         if (g < G && (g % (2 * st)) == 0 && g + st < G) {
-          const V4 v = r4[(g + st) * nq + q];
-          V4 acc = r4[g * nq + q];
+          const F4 v = r4[(g + st) * nq + q];
+          F4 acc = r4[g * nq + q];
           acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
           r4[g * nq + q] = acc;
         }
         __syncthreads();
       }
       if (t < nq) {
-        const V4 acc = r4[t];
-        a0 = acc.x; a1 = acc.y; a2 = acc.z; a3 = acc.w;
+        const F4 acc = r4[t];
+        f0 = acc.x; f1 = acc.y; f2 = acc.z; f3 = acc.w;
       }
     }
     if (t < nq) {
       const int64_t row = r0 + 4 * (qb0 + t);
-      const T aa[4] = {a0, a1, a2, a3};
+      const FT ff[4] = {f0, f1, f2, f3};
+      const FT sg = (FT)sgn;
 #pragma unroll
       for (int e = 0; e < 4; e++) {
-        if (row + e < r1) z[row + e] = (TZ)((u ? (T)u[row + e] : T(0)) + sgn * aa[e]);
+        if (row + e < r1) {
+          const FT v = (u ? (FT)u[row + e] : FT(0)) + sg * ff[e];
+          z[row + e] = (TZ)v;
+          if (z2) z2[row + e] = (double)v;
+        }
       }
     }
     qb0 += nq;
@@ -407,12 +511,12 @@ __device__ __forceinline__ void cta_gemv_n(const T* __restrict__ V, int64_t ld, 
 // Blocks are read in pairs starting at an even block index, 18 values as nine two-value
 // loads (16-byte loads for FP64 values: 16-byte aligned values and 8-byte aligned col_idx
 // required).  The matrix goes through the non-coherent path; w (written by other CTAs of a
-// persistent kernel) does not.
-template <typename T, typename TW = T, typename TQ = T, typename TR = T>
+// persistent kernel) does not.  qw (optional): a second copy of q, of type TQW.
+template <typename T, typename TW = T, typename TQ = T, typename TR = T, typename TQW = TW>
 __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* __restrict__ ci,
                                          const T* __restrict__ vals, const TW* __restrict__ w,
                                          TQ* __restrict__ q, const TR* __restrict__ r, int64_t r0, int64_t r1,
-                                         double& wq, double& rw, TW* __restrict__ qw = nullptr) {
+                                         double& wq, double& rw, TQW* __restrict__ qw = nullptr) {
   using V2 = typename VT<T>::V2;
   const int64_t n0 = r0 / 3;
   const int64_t items = 2 * ((r1 - r0) / 3);
@@ -486,9 +590,9 @@ __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* 
       q[row + 1] = (TQ)q1;
       q[row + 2] = (TQ)q2;
       if (qw) {
-        qw[row] = (TW)q0;
-        qw[row + 1] = (TW)q1;
-        qw[row + 2] = (TW)q2;
+        qw[row] = (TQW)q0;
+        qw[row + 1] = (TQW)q1;
+        qw[row + 2] = (TQW)q2;
       }
       const T w0 = (T)w[row], w1 = (T)w[row + 1], w2 = (T)w[row + 2];
       wq += (double)w0 * (double)q0;

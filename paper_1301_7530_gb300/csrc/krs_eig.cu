@@ -555,4 +555,11 @@ cudaError_t launch_ritz_vectors_f(int64_t n, int64_t ld, int m, int k, const flo
   return ritz_vectors_t<float>(n, ld, m, k, Z, rho, Q, tsel, F, Y, st);
 }
 
+// Ritz vectors from double-float z_j (the double-float precision); accumulated and stored
+// in FP64.
+cudaError_t launch_ritz_vectors_df(int64_t n, int64_t ld, int m, int k, const dfl* Z, const double* rho,
+                                   const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st) {
+  return ritz_vectors_t<dfl>(n, ld, m, k, Z, rho, Q, tsel, F, Y, st);
+}
+
 }  // namespace krs

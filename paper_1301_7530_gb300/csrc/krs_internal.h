@@ -15,8 +15,9 @@ krs_status set_error(krs_status st, const char* msg);
 
 // Everything the iteration kernels need (device pointers, sizes, partition).  The element
 // types of the arrays follow `prec` (matrix values, M^-1, x, r, u: FP32 for prec 1, FP64
-// otherwise; C, AC, W, AW, Z: FP64 for prec 0, FP32 otherwise); scalars, partial sums and
-// G^-1 are doubles in all.
+// otherwise; C, AC: FP64 for prec 0 and 3, FP32 otherwise; W, AW, Z: FP64 for prec 0,
+// double-float pairs for prec 3, FP32 otherwise); scalars, partial sums and G^-1 are
+// doubles in all.
 struct IterArgs {
   int64_t n, ld;
   int nbr, npc, P;
@@ -27,7 +28,8 @@ struct IterArgs {
   int jcap;  // iterations j >= jcap do not start in one launch (0: no limit)
   int kmax;  // largest k a tall-skinny phase sees: max(nc, max_iter)
   int prec;  // 0: FP64; 1: FP32 (mixed-precision inner solves); 2: FP64 recurrences with FP32
-             // projection / reorthogonalisation (C, AC, W, AW, Z in FP32, q in FP64)
+             // projection / reorthogonalisation (C, AC, W, AW, Z in FP32, q in FP64);
+             // 3: FP64 with double-float W, AW, Z (q and wv in FP64)
   double tol2;
   long long spin_limit;
   const int* rp;
@@ -40,7 +42,8 @@ struct IterArgs {
   const void* ACi;
   const double* Ginv;
   void *W, *AW, *Z, *x, *r, *u;
-  void* q;          // prec 2: FP64 product A w_j
+  void* q;          // prec 2, 3: FP64 product A w_j
+  void* wv;         // prec 3: FP64 search direction w_j (n + padding doubles)
   bool init32;      // prec 2: the init stage reads the FP32 C and AC (restarted passes)
   int stall_win;    // > 0: end the solve when ||r||^2 fell by less than 4x over this many
                     //      iterations (status KRS_STALLED), once it is below stall_rr
@@ -156,5 +159,8 @@ cudaError_t launch_ritz_vectors(int64_t n, int64_t ld, int m, int k, const doubl
                                 cudaStream_t st);
 cudaError_t launch_ritz_vectors_f(int64_t n, int64_t ld, int m, int k, const float* Z, const double* rho,
                                   const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st);
+struct dfl;
+cudaError_t launch_ritz_vectors_df(int64_t n, int64_t ld, int m, int k, const dfl* Z, const double* rho,
+                                   const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st);
 
 }  // namespace krs

@@ -105,7 +105,8 @@ struct krs_seq {
   float *vals32 = nullptr, *minv32 = nullptr, *C32 = nullptr, *AC32 = nullptr;
   float *W32 = nullptr, *AW32 = nullptr, *Z32 = nullptr;
   float *x32 = nullptr, *r32 = nullptr, *u32 = nullptr, *b32 = nullptr;
-  double* q64 = nullptr;   // FP32-projection precision: the FP64 product A w_j
+  double* q64 = nullptr;   // FP32-projection and double-float precisions: the FP64 product A w_j
+  double* wv = nullptr;    // double-float precision: the FP64 search direction w_j
   double* xacc = nullptr;  //   sum of the passes' corrections
   double* rres = nullptr;  //   FP64 residual b - A xacc (the next pass's right-hand side)
   double* rrh = nullptr;   //   ||r_j||^2 history of the stall test
@@ -179,8 +180,17 @@ krs_status seq_begin(krs_seq* s, const krs_bsr* A, const double* b, double tol, 
 // for KRS_MIXED_PROJ) to at least cap_iter + 1 columns keeping the first `keep` columns and
 // the scalars of the first `keep` iterations (between launches).
 krs_status seq_grow_directions(krs_seq* s, int cap_iter, int keep, int prec);
-// columns of the direction storage a solve of precision `prec` uses
-inline int dir_cap(const krs_seq* s, int prec) { return prec == KRS_FP64 ? s->cap_w : s->cap_w32; }
+// columns of the direction storage a solve of precision `prec` uses (KRS_DOUBLE_FLOAT keeps
+// its double-float directions in the 8-byte W, AW, Z of the FP64 path)
+inline int dir_cap(const krs_seq* s, int prec) {
+  return (prec == KRS_FP64 || prec == KRS_DOUBLE_FLOAT) ? s->cap_w : s->cap_w32;
+}
+// internal precision id of the iteration kernels (IterArgs::prec)
+inline int prec_id(int precision) {
+  return precision == KRS_MIXED_IR ? 1 : precision == KRS_MIXED_PROJ ? 2 : precision == KRS_DOUBLE_FLOAT ? 3 : 0;
+}
+// one APCG solve per system with an FP64 residual (no refinement loop)
+inline bool single_pass(int precision) { return precision == KRS_FP64 || precision == KRS_DOUBLE_FLOAT; }
 // Stage 3: recycling step (TRKS / SRKS), result copy to x (host or device), true residual,
 // statistics and the commit of the new augmentation space.  `status` and `m` are the
 // iteration loop's outcome.
