@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #ifndef KRS_TPB
 #define KRS_TPB 512
 #endif
@@ -341,6 +343,175 @@ __device__ __forceinline__ void cta_gemv_t_few(const T* __restrict__ V, int64_t 
   __syncthreads();
 }
 
+// ------------------------------------------------------------------------------------
+// Double-float tall-skinny products.  With the arithmetic on the FP32 pipes these are
+// bound by memory, so their layouts favour long contiguous runs per column:
+//   cta_gemv_t_df: a warp takes a block of 8 columns over a range of row pairs; lane l
+//     reads row pairs l, l + 32, ... of all 8 columns (512 contiguous bytes of each column
+//     per warp load), accumulates per column, and the 8 x 32 lane sums are folded by a
+//     transposed shuffle reduction (4 + 2 + 1 + 1 + 1 compensated adds per lane for 8
+//     columns).  Units (column block, row range) are spread over the 16 warps; row ranges
+//     are split only when there are fewer than 16 column blocks.
+//   cta_gemv_n_df: thread per row quad; G = floor(TPB / quads) column groups so that one
+//     pass covers every quad; 8-column unroll (256 bytes in flight per thread).
+// Row pairs / quads past r1 read the zero padding of the columns (r0 is a multiple of 4;
+// a column holds ld >= n + 1 values when n is odd).
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ dacc dacc_sum(dacc a, dacc b) {
+  dacc_add(a, b.s, b.c);
+  return a;
+}
+__device__ __forceinline__ dacc dacc_shfl(dacc a, int m) {
+  return dacc{__shfl_xor_sync(0xffffffffu, a.s, m), __shfl_xor_sync(0xffffffffu, a.c, m)};
+}
+
+// out[c] = sum_{i in [r0, r1)} V[c*ld + i] u[i] (c < k), double-float V and u.  red: shared,
+// >= 240 doubles (row-range partials when k < 128).
+template <bool NC>
+__device__ __forceinline__ void cta_gemv_t_df(const dfl* __restrict__ V, int64_t ld, int k, const dfl* __restrict__ u,
+                                              int64_t r0, int64_t r1, double* __restrict__ out, double* red) {
+  constexpr int CB = 8;
+  constexpr int NW = TPB / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t pairs = ((r1 - r0) + 1) >> 1;
+  const int nblk = (k + CB - 1) / CB;
+  const int Rg = nblk >= NW ? 1 : (NW + nblk - 1) / nblk;  // row ranges per column block
+  const int units = nblk * Rg;
+  const dfl2* u2 = reinterpret_cast<const dfl2*>(u + r0);
+  for (int un = warp; un < units; un += NW) {
+    const int blk = un / Rg, rg = un - blk * Rg;
+    const int c0 = blk * CB;
+    const int nc = min(CB, k - c0);
+    const int64_t pa = pairs * rg / Rg, pb = pairs * (rg + 1) / Rg;
+    dacc acc[CB];
+#pragma unroll
+    for (int c = 0; c < CB; c++) acc[c] = dacc{0.f, 0.f};
+    const dfl* col0 = V + (int64_t)c0 * ld + r0;
+    for (int64_t p = pa + lane; p < pb; p += 32) {
+      dfl2 x[CB];
+#pragma unroll
+      for (int c = 0; c < CB; c++) {
+        if (c < nc) {
+          const float4 v = NC ? __ldg(reinterpret_cast<const float4*>(col0 + (int64_t)c * ld + 2 * p))
+                              : *reinterpret_cast<const float4*>(col0 + (int64_t)c * ld + 2 * p);
+          x[c].x.hi = v.x; x[c].x.lo = v.y; x[c].y.hi = v.z; x[c].y.lo = v.w;
+        } else {
+          x[c].x.hi = x[c].x.lo = x[c].y.hi = x[c].y.lo = 0.f;
+        }
+      }
+      const float4 uv = *reinterpret_cast<const float4*>(u2 + p);
+      dfl y0, y1;
+      y0.hi = uv.x; y0.lo = uv.y; y1.hi = uv.z; y1.lo = uv.w;
+#pragma unroll
+      for (int c = 0; c < CB; c++) {
+        Acc<dfl>::mac(acc[c], x[c].x, y0);
+        Acc<dfl>::mac(acc[c], x[c].y, y1);
+      }
+    }
+    // transposed reduction: after it, lane 4c holds column c0 + c (sum over all 32 lanes)
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    dacc v4[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+      v4[i] = dacc_sum(b4 ? acc[4 + i] : acc[i], dacc_shfl(b4 ? acc[i] : acc[4 + i], 16));
+    dacc v2[2];
+#pragma unroll
+    for (int i = 0; i < 2; i++) v2[i] = dacc_sum(b3 ? v4[2 + i] : v4[i], dacc_shfl(b3 ? v4[i] : v4[2 + i], 8));
+    dacc v1 = dacc_sum(b2 ? v2[1] : v2[0], dacc_shfl(b2 ? v2[0] : v2[1], 4));
+    v1 = dacc_sum(v1, dacc_shfl(v1, 1));
+    v1 = dacc_sum(v1, dacc_shfl(v1, 2));
+    if ((lane & 3) == 0 && (lane >> 2) < nc) {
+      const double r = Acc<dfl>::out(v1);
+      if (Rg == 1) out[c0 + (lane >> 2)] = r;
+      else red[rg * k + c0 + (lane >> 2)] = r;
+    }
+  }
+  if (Rg > 1) {  // fixed-order sum of the row ranges
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += TPB) {
+      double s = red[c];
+      for (int g = 1; g < Rg; g++) s += red[g * k + c];
+      out[c] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// z[i] = u[i] + sgn * sum_{c<k} V[c*ld + i] * s[c] for i in [r0, r1), double-float V and s
+// (shared); u of type TU (nullptr: 0); z of type TZ; z2 (optional): the result as a double.
+// red: shared, TPB four-row double vectors.
+template <bool NC, typename TU, typename TZ>
+__device__ __forceinline__ void cta_gemv_n_df(const dfl* __restrict__ V, int64_t ld, int k, const dfl* s, double sgn,
+                                              const TU* u, TZ* z, int64_t r0, int64_t r1, void* red, double* z2) {
+  constexpr int CU = 8;
+  const int t = threadIdx.x;
+  const int64_t q4 = ((r1 - r0) + 3) >> 2;
+  for (int64_t qb0 = 0; qb0 < q4; ) {
+    const int64_t remq = q4 - qb0;
+    int G = remq >= TPB ? 1 : (int)(TPB / remq);  // column groups (one pass over the quads)
+    if (G > k) G = k > 0 ? k : 1;
+    const int nq = (int)kmin64(remq, TPB / G);
+    const int q = t % nq, g = t / nq;
+    dacc a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+    if (g < G && k > 0) {
+      const int ca = (int)((int64_t)k * g / G), cb = (int)((int64_t)k * (g + 1) / G);
+      const int64_t row = r0 + 4 * (qb0 + q);
+      int c = ca;
+      for (; c + CU <= cb; c += CU) {
+        dfl4 v[CU];
+#pragma unroll
+        for (int e = 0; e < CU; e++) v[e] = ld4<NC, dfl>(V + (int64_t)(c + e) * ld + row);
+#pragma unroll
+        for (int e = 0; e < CU; e++) {
+          const dfl se = s[c + e];
+          Acc<dfl>::mac(a0, v[e].x, se); Acc<dfl>::mac(a1, v[e].y, se);
+          Acc<dfl>::mac(a2, v[e].z, se); Acc<dfl>::mac(a3, v[e].w, se);
+        }
+      }
+      for (; c < cb; c++) {
+        const dfl4 v0 = ld4<NC, dfl>(V + (int64_t)c * ld + row);
+        const dfl se = s[c];
+        Acc<dfl>::mac(a0, v0.x, se); Acc<dfl>::mac(a1, v0.y, se);
+        Acc<dfl>::mac(a2, v0.z, se); Acc<dfl>::mac(a3, v0.w, se);
+      }
+    }
+    double f0 = Acc<dfl>::out(a0), f1 = Acc<dfl>::out(a1), f2 = Acc<dfl>::out(a2), f3 = Acc<dfl>::out(a3);
+    if (G > 1) {
+      __syncthreads();
+      double4_32a* r4 = reinterpret_cast<double4_32a*>(red);
+      if (g < G) r4[g * nq + q] = make_double4_32a(f0, f1, f2, f3);
+      __syncthreads();
+      for (int st = 1; st < G; st <<= 1) {  // pairwise tree over the column groups (fixed order)
+        if (g < G && (g % (2 * st)) == 0 && g + st < G) {
+          const double4_32a v = r4[(g + st) * nq + q];
+          double4_32a acc = r4[g * nq + q];
+          acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+          r4[g * nq + q] = acc;
+        }
+        __syncthreads();
+      }
+      if (t < nq) {
+        const double4_32a acc = r4[t];
+        f0 = acc.x; f1 = acc.y; f2 = acc.z; f3 = acc.w;
+      }
+    }
+    if (t < nq) {
+      const int64_t row = r0 + 4 * (qb0 + t);
+      const double ff[4] = {f0, f1, f2, f3};
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        if (row + e < r1) {
+          const double v = (u ? (double)u[row + e] : 0.0) + sgn * ff[e];
+          z[row + e] = (TZ)v;
+          if (z2) z2[row + e] = v;
+        }
+      }
+    }
+    qb0 += nq;
+  }
+  __syncthreads();
+}
+
 // out[c] = sum_{i in [r0, r1)} V[c*ld + i] * u[i], c in [0, k), as doubles.  Thread per
 // column: each thread streams its column with four-row vector loads into four independent
 // accumulators (no dependent FMA chain).  Columns are taken in blocks of kc with
@@ -353,6 +524,11 @@ __device__ __forceinline__ void cta_gemv_t(const T* __restrict__ V, int64_t ld, 
                                            const TU* __restrict__ u, int64_t r0, int64_t r1,
                                            double* __restrict__ out, T* su, double* red) {
   using V4 = typename VT<T>::V4;
+  if constexpr (std::is_same<T, dfl>::value) {
+    static_assert(std::is_same<TU, dfl>::value, "double-float V^T u takes a double-float u");
+    cta_gemv_t_df<NC>(V, ld, k, u, r0, r1, out, red);
+    return;
+  }
   if (k <= TPB / 32) {
     cta_gemv_t_few<NC, T, TU>(V, ld, k, u, r0, r1, out, red);
     return;
@@ -427,6 +603,10 @@ template <bool NC, typename T, typename TU = T, typename TZ = T>
 __device__ __forceinline__ void cta_gemv_n(const T* __restrict__ V, int64_t ld, int k, const T* s, T sgn,
                                            const TU* u, TZ* z, int64_t r0, int64_t r1, void* red,
                                            double* z2 = nullptr) {
+  if constexpr (std::is_same<T, dfl>::value) {
+    cta_gemv_n_df<NC, TU, TZ>(V, ld, k, s, (double)sgn, u, z, r0, r1, red, z2);
+    return;
+  }
   using V4 = typename VT<T>::V4;
   using AC = Acc<T>;
   using FT = typename AC::out_t;          // type the column groups are combined in
