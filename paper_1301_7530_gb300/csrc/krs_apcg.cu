@@ -42,11 +42,11 @@ namespace krs {
 //   PrecF  FP32 throughout (inner solves of the mixed-precision refinement);
 //   PrecP  FP64 operator product, preconditioner, x and r recurrences; FP32 projection and
 //          reorthogonalisation (C, AC, W, AW, Z stored and combined in FP32);
-//   PrecE  FP64 operator product, preconditioner, recurrences and projection (C, AC);
-//          double-float search directions W, AW, Z (48-bit significand), so that the
-//          reorthogonalisation's tall-skinny products run on the FP32 pipes.  The operator
-//          product reads the FP64 copy wv of w_j and writes q in FP64 (its double-float copy
-//          goes to AW).
+//   PrecE  FP64 preconditioner, recurrences and projection (C, AC); double-float search
+//          directions W, AW, Z and matrix values (48-bit significand), so that the operator
+//          product and the reorthogonalisation run on the FP32 pipes.  The operator product
+//          writes q in FP64 (its double-float copy goes to AW); x, (w, q) and (r, w) use the
+//          FP64 copy wv of w_j.
 struct PrecD { using V = double; using M = double; using MC = double; using A = double; static constexpr int id = 0; };
 struct PrecF { using V = float;  using M = float;  using MC = float;  using A = float;  static constexpr int id = 1; };
 struct PrecP { using V = double; using M = float;  using MC = float;  using A = double; static constexpr int id = 2; };
@@ -85,6 +85,7 @@ struct ApcgCtx {
   V* u;
   V* q;                // PrecP, PrecE: the FP64 operator product A w_j (AW keeps its copy)
   V* wv;               // PrecE: the FP64 search direction w_j (W keeps its double-float copy)
+  const dfl* valsd;    // PrecE: the matrix values as double-float (the operator product)
   double* alpha;
   double* gamma;
   double* rho;
@@ -196,8 +197,8 @@ __device__ __forceinline__ void phase1(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm
   double wq = 0.0, rw = 0.0;
   if constexpr (Pr::id == 2)  // q in FP64 for the recurrences, its FP32 copy into AW
     cta_spmv<A, M, V, V>(c.rp, c.ci, c.vals, w, c.q, c.r, r0, r1, wq, rw, aw);
-  else if constexpr (Pr::id == 3)  // FP64 w_j and q; the double-float copy of q into AW
-    cta_spmv<A, V, V, V, M>(c.rp, c.ci, c.vals, c.wv, c.q, c.r, r0, r1, wq, rw, aw);
+  else if constexpr (Pr::id == 3)  // double-float A and w_j on the FP32 pipes; q in FP64 and into AW
+    cta_spmv_df(c.rp, c.ci, c.valsd, w, c.wv, c.q, aw, c.r, r0, r1, wq, rw);
   else
     cta_spmv<A, M, M, V>(c.rp, c.ci, c.vals, w, aw, c.r, r0, r1, wq, rw);
   block_sum2(wq, rw, sm.red);
@@ -702,6 +703,7 @@ static ApcgCtx<Pr> make_ctx(const IterArgs& a) {
   c.x = static_cast<V*>(a.x); c.r = static_cast<V*>(a.r); c.u = static_cast<V*>(a.u);
   c.q = static_cast<V*>(a.q);
   c.wv = static_cast<V*>(a.wv);
+  c.valsd = static_cast<const dfl*>(a.vals_df);
   c.alpha = a.alpha; c.gamma = a.gamma; c.rho = a.rho;
   c.tfull = a.tfull; c.sfull = a.sfull; c.gfull = a.gfull;
   c.part = a.part; c.vpart = a.vpart; c.gpart = a.gpart; c.vld = a.vld; c.ctrl = a.ctrl; c.bar = a.bar;

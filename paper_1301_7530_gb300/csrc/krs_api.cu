@@ -448,6 +448,9 @@ krs_status krs_release(krs_seq_t s, int32_t what) {
     s->cap_w = 0;
     s->cap_sc = 0;
     drop(s->q64); drop(s->wv); drop(s->xacc); drop(s->rres); drop(s->rrh);
+    drop(s->vals_df);
+    s->vals_df_cap = 0;
+    s->vals_df_valid = false;
     s->rrh_cap = 0;
     drop(s->vpart); drop(s->gpart); drop(s->part); drop(s->tfull); drop(s->sfull);
     s->vpart_P = 0;
@@ -493,6 +496,9 @@ krs_status krs_release(krs_seq_t s, int32_t what) {
     drop(s->vals32);
     s->vals32_cap = 0;
     s->vals32_valid = false;
+    drop(s->vals_df);
+    s->vals_df_cap = 0;
+    s->vals_df_valid = false;
   }
   return KRS_OK;
 }
@@ -868,7 +874,10 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   // ---- matrix, preconditioner
   bool changed = false;
   KRS_TRY(upload_matrix(s, A, &changed));
-  if (changed) s->vals32_valid = false;
+  if (changed) {
+    s->vals32_valid = false;
+    s->vals_df_valid = false;
+  }
   if (s->precond_built != p->precond) {
     KRS_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(int) * CTRL_WORDS, s->stream));
     KRS_CUDA(launch_precond_setup(p->precond, s->nbr, s->rp_use, s->ci_use, s->vals_use, s->minv, s->ctrl + CTRL_STATUS,
@@ -911,6 +920,18 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
     if (dfk) {  // the FP64 copies of w_j and A w_j beside the double-float directions
       if (!s->q64) KRS_TRY(alloc_n(s, &s->q64, s->ld));
       if (!s->wv) KRS_TRY(alloc_n(s, &s->wv, s->ld));
+      if (A->nnzb > s->vals_df_cap) {  // double-float matrix values for the operator product
+        dev_free(s, s->vals_df);
+        s->vals_df = nullptr;
+        KRS_TRY(alloc_n(s, &s->vals_df, (size_t)A->nnzb * 9));
+        s->vals_df_cap = A->nnzb;
+        s->vals_df_valid = false;
+      }
+      if (!s->vals_df_valid) {
+        KRS_CUDA(launch_d2df(s->vals_use, s->vals_df, 9 * A->nnzb, s->stream));
+        s->vals_df_valid = true;
+        launches++;
+      }
     }
   }
   // largest column count a tall-skinny phase sees (mixed: C plus earlier inner directions)
@@ -1013,6 +1034,7 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
     if (dfk) {
       a.q = s->q64;
       a.wv = s->wv;
+      a.vals_df = s->vals_df;
     }
   }
   KRS_CUDA(cudaEventRecord(s->ev[1], s->stream));

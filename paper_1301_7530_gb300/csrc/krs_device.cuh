@@ -787,6 +787,114 @@ __device__ __forceinline__ void cta_spmv(const int* __restrict__ rp, const int* 
   }
 }
 
+// q = A w on one CTA's nodes with double-float matrix values and w: the layout of cta_spmv
+// (two threads per node, block pairs as nine 16-byte loads, two-stage software pipeline)
+// with each row accumulated in double-float on the FP32 pipes.  q is written as a double
+// (qd) and as double-float (qw); (w, q) and (r, w) are formed in FP64 from wv, the FP64
+// copy of w.
+__device__ __forceinline__ dfl dfl_of(float hi, float lo) {
+  dfl v;
+  v.hi = hi;
+  v.lo = lo;
+  return v;
+}
+__device__ __forceinline__ void spmv_df_block(const dfl* __restrict__ v, dfl w0, dfl w1, dfl w2, dacc& a0, dacc& a1,
+                                              dacc& a2) {
+  const float2* f = reinterpret_cast<const float2*>(v);
+  dfl m[9];
+#pragma unroll
+  for (int e = 0; e < 9; e++) {
+    const float2 t = __ldg(f + e);
+    m[e] = dfl_of(t.x, t.y);
+  }
+  using AC = Acc<dfl>;
+  AC::mac(a0, m[0], w0); AC::mac(a1, m[3], w0); AC::mac(a2, m[6], w0);
+  AC::mac(a0, m[1], w1); AC::mac(a1, m[4], w1); AC::mac(a2, m[7], w1);
+  AC::mac(a0, m[2], w2); AC::mac(a1, m[5], w2); AC::mac(a2, m[8], w2);
+}
+__device__ __forceinline__ void cta_spmv_df(const int* __restrict__ rp, const int* __restrict__ ci,
+                                            const dfl* __restrict__ vals, const dfl* __restrict__ w,
+                                            const double* __restrict__ wv, double* __restrict__ qd,
+                                            dfl* __restrict__ qw, const double* __restrict__ r, int64_t r0,
+                                            int64_t r1, double& wq, double& rw) {
+  using AC = Acc<dfl>;
+  const int64_t n0 = r0 / 3;
+  const int64_t items = 2 * ((r1 - r0) / 3);
+  for (int64_t base = 0; base < items; base += TPB) {
+    const int64_t it = base + threadIdx.x;
+    dacc a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f};
+    const bool active = it < items;
+    int64_t node = 0;
+    if (active) {
+      node = n0 + (it >> 1);
+      const int ka = __ldg(rp + node), kb = __ldg(rp + node + 1);
+      const int mid = ka + ((kb - ka) >> 1);
+      const int kbeg = (it & 1) ? mid : ka, kend = (it & 1) ? kb : mid;
+      int k = kbeg;
+      if ((k & 1) && k < kend) {  // a leading odd block alone (not aligned for pair loads)
+        const int64_t cc = 3 * (int64_t)__ldg(ci + k);
+        spmv_df_block(vals + 9 * (int64_t)k, w[cc], w[cc + 1], w[cc + 2], a0, a1, a2);
+        k++;
+      }
+      if (k + 2 <= kend) {
+        int2 cp = __ldg(reinterpret_cast<const int2*>(ci + k));
+        const float4* v4 = reinterpret_cast<const float4*>(vals + 9 * (int64_t)k);
+        float4 p[9];
+#pragma unroll
+        for (int e = 0; e < 9; e++) p[e] = __ldg(v4 + e);
+#pragma unroll 1
+        for (; k + 2 <= kend; k += 2) {
+          const int64_t c0 = 3 * (int64_t)cp.x, c1 = 3 * (int64_t)cp.y;
+          const dfl x0 = w[c0], x1 = w[c0 + 1], x2 = w[c0 + 2];
+          const dfl y0 = w[c1], y1 = w[c1 + 1], y2 = w[c1 + 2];
+          float4 q[9];
+#pragma unroll
+          for (int e = 0; e < 9; e++) q[e] = p[e];
+          if (k + 4 <= kend) {
+            cp = __ldg(reinterpret_cast<const int2*>(ci + k + 2));
+            const float4* n4 = reinterpret_cast<const float4*>(vals + 9 * (int64_t)(k + 2));
+#pragma unroll
+            for (int e = 0; e < 9; e++) p[e] = __ldg(n4 + e);
+          }
+          // value e of the pair (0..17) is half (e & 1) of q[e >> 1]; block k: values 0..8,
+          // block k + 1: values 9..17, each row-major
+#define KRS_DFV(e) ((((e) & 1) == 0) ? dfl_of(q[(e) >> 1].x, q[(e) >> 1].y) : dfl_of(q[(e) >> 1].z, q[(e) >> 1].w))
+          AC::mac(a0, KRS_DFV(0), x0); AC::mac(a1, KRS_DFV(3), x0); AC::mac(a2, KRS_DFV(6), x0);
+          AC::mac(a0, KRS_DFV(1), x1); AC::mac(a1, KRS_DFV(4), x1); AC::mac(a2, KRS_DFV(7), x1);
+          AC::mac(a0, KRS_DFV(2), x2); AC::mac(a1, KRS_DFV(5), x2); AC::mac(a2, KRS_DFV(8), x2);
+          AC::mac(a0, KRS_DFV(9), y0); AC::mac(a1, KRS_DFV(12), y0); AC::mac(a2, KRS_DFV(15), y0);
+          AC::mac(a0, KRS_DFV(10), y1); AC::mac(a1, KRS_DFV(13), y1); AC::mac(a2, KRS_DFV(16), y1);
+          AC::mac(a0, KRS_DFV(11), y2); AC::mac(a1, KRS_DFV(14), y2); AC::mac(a2, KRS_DFV(17), y2);
+#undef KRS_DFV
+        }
+      }
+      if (k < kend) {  // a trailing single block
+        const int64_t cc = 3 * (int64_t)__ldg(ci + k);
+        spmv_df_block(vals + 9 * (int64_t)k, w[cc], w[cc + 1], w[cc + 2], a0, a1, a2);
+      }
+    }
+    // pairs (2i, 2i+1) share a warp (TPB and base are even); every lane takes part
+    const dacc b0 = dacc_shfl(a0, 1), b1 = dacc_shfl(a1, 1), b2 = dacc_shfl(a2, 1);
+    if (active && !(it & 1)) {
+      const double q0 = AC::out(dacc_sum(a0, b0)), q1 = AC::out(dacc_sum(a1, b1)), q2 = AC::out(dacc_sum(a2, b2));
+      const int64_t row = 3 * node;
+      qd[row] = q0;
+      qd[row + 1] = q1;
+      qd[row + 2] = q2;
+      qw[row] = dfl(q0);
+      qw[row + 1] = dfl(q1);
+      qw[row + 2] = dfl(q2);
+      const double w0 = wv[row], w1 = wv[row + 1], w2 = wv[row + 2];
+      wq += w0 * q0;
+      wq += w1 * q1;
+      wq += w2 * q2;
+      rw += r[row] * w0;
+      rw += r[row + 1] * w1;
+      rw += r[row + 2] * w2;
+    }
+  }
+}
+
 // u = M^-1 r for one row (Jacobi: minv[row]; block Jacobi: minv[9*node + 3*d + e];
 // identity: r).
 template <typename T, typename TV = T>

@@ -29,7 +29,8 @@ struct IterArgs {
   int kmax;  // largest k a tall-skinny phase sees: max(nc, max_iter)
   int prec;  // 0: FP64; 1: FP32 (mixed-precision inner solves); 2: FP64 recurrences with FP32
              // projection / reorthogonalisation (C, AC, W, AW, Z in FP32, q in FP64);
-             // 3: FP64 with double-float W, AW, Z (q and wv in FP64)
+             // 3: FP64 with double-float W, AW, Z and matrix values for the operator
+             //    product (q and wv in FP64)
   double tol2;
   long long spin_limit;
   const int* rp;
@@ -44,6 +45,7 @@ struct IterArgs {
   void *W, *AW, *Z, *x, *r, *u;
   void* q;          // prec 2, 3: FP64 product A w_j
   void* wv;         // prec 3: FP64 search direction w_j (n + padding doubles)
+  const void* vals_df;  // prec 3: matrix values as double-float pairs (9 nnzb)
   bool init32;      // prec 2: the init stage reads the FP32 C and AC (restarted passes)
   int stall_win;    // > 0: end the solve when ||r||^2 fell by less than 4x over this many
                     //      iterations (status KRS_STALLED), once it is below stall_rr
@@ -133,6 +135,8 @@ cudaError_t launch_fill_zero(double* p, int64_t count, cudaStream_t st);
 // r32 = (float) r (skipped when r32 is NULL), out = ||r||^2 (ax: n-vector scratch, part:
 // >= 128 doubles)
 cudaError_t launch_d2f(const double* src, float* dst, int64_t count, cudaStream_t st);
+struct dfl;
+cudaError_t launch_d2df(const double* src, dfl* dst, int64_t count, cudaStream_t st);  // dst = double-float src
 cudaError_t launch_add_f2d(double* x, const float* d, int64_t n, cudaStream_t st);
 cudaError_t launch_add_d(double* x, const double* d, int64_t n, cudaStream_t st);  // x += d
 cudaError_t launch_resid_update(int nbr, const int* rp, const int* ci, const double* vals, const double* x,

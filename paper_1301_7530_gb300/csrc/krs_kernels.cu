@@ -489,6 +489,18 @@ cudaError_t launch_d2f(const double* src, float* dst, int64_t count, cudaStream_
   return cudaGetLastError();
 }
 
+// double-float copy of FP64 values (the matrix of the double-float precision)
+__global__ void k_d2df(const double* __restrict__ src, dfl* __restrict__ dst, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = dfl(src[i]);
+}
+
+cudaError_t launch_d2df(const double* src, dfl* dst, int64_t count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_d2df<<<1216, 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
 // x += (double) d
 __global__ void k_add_f2d(double* __restrict__ x, const float* __restrict__ d, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

@@ -107,6 +107,9 @@ struct krs_seq {
   float *x32 = nullptr, *r32 = nullptr, *u32 = nullptr, *b32 = nullptr;
   double* q64 = nullptr;   // FP32-projection and double-float precisions: the FP64 product A w_j
   double* wv = nullptr;    // double-float precision: the FP64 search direction w_j
+  krs::dfl* vals_df = nullptr;  // double-float precision: the matrix values as double-float pairs
+  int64_t vals_df_cap = 0;
+  bool vals_df_valid = false;
   double* xacc = nullptr;  //   sum of the passes' corrections
   double* rres = nullptr;  //   FP64 residual b - A xacc (the next pass's right-hand side)
   double* rrh = nullptr;   //   ||r_j||^2 history of the stall test
