@@ -72,6 +72,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-variant", action="store_true",
+                    help="sequence workload in FP64: skip the double-float line of the same workload")
     ap.add_argument("--precision", choices=["fp64", "double_float", "mixed_ir", "mixed_proj"], default="fp64",
                     help="sequence workload: FP64, FP32 refinement passes, or FP32 projection passes")
     ap.add_argument("--inner-tol", type=float, default=0.0,
@@ -305,8 +307,24 @@ def run_krs(args, rank, world, local):
             if record is not None:
                 record.append(st)
 
-    for _ in range(args.warmup):
-        one_step()
+    def timed(steps, warmup, record, lat):
+        """warm-up steps, then `steps` steps bracketed by a barrier and synchronisation on both
+        sides, CUDA events on the library's stream; returns (ms, clocks)"""
+        for _ in range(warmup):
+            one_step()
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(gpu_index, enabled=not args.no_clocks)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            one_step(record, lat)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return ev0.elapsed_time(ev1), clocks.stop()
+
     gpu_index = local
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
     if cvd:
@@ -315,19 +333,7 @@ def run_krs(args, rank, world, local):
         except (ValueError, IndexError):
             gpu_index = local
     stats, lat = [], []
-    barrier(world)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(gpu_index, enabled=not args.no_clocks)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        one_step(stats, lat)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms, clk = timed(args.steps, args.warmup, stats, lat)
     ms_max = all_max(ms, world)
     solves = args.steps * args.systems
     total_solves = all_sum(solves, world)
@@ -387,6 +393,39 @@ def run_krs(args, rank, world, local):
                "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps, "n": s0["n"]}
         seq2.close()
 
+    # the same workload with double-float search directions and matrix values (FP32 pipes)
+    variant = None
+    if args.precision == "fp64" and not args.no_variant:
+        pol = B.make_policy("srks", "block_jacobi3", ritz_eps=args.ritz_eps, theta_frac=args.theta_frac,
+                            max_aug=args.max_aug, max_iter=args.max_iter, exec=args.exec,
+                            precision="double_float", reselect=args.reselect)
+        vstats, vlat = [], []
+        vms, vclk = timed(args.steps, args.warmup, vstats, vlat)
+        vms_max = all_max(vms, world)
+        vflops = vbyts = vt_iter = 0.0
+        for st in vstats:
+            f, bb = alg_counts(args.N, 24, st["m"], st["n_c"])
+            vflops += f
+            vbyts += bb
+            vt_iter += st["t_iter_ms"]
+        vgbs = vbyts / (vt_iter / 1e3) / 1e9
+        vtraffic, vtraffic_alg = profiled_traffic("double_float")
+        variant = {
+            "precision": "double_float", "dtype": dtype_of("double_float"),
+            "value": all_sum(args.steps * args.systems, world) / (vms_max / 1e3), "unit": UNIT,
+            "ms_per_step": vms_max / args.steps,
+            "latency_ms": {"p50": float(np.percentile(vlat, 50)), "p99": float(np.percentile(vlat, 99))},
+            "m_mean": float(np.mean([st["m"] for st in vstats])),
+            "true_rel_res_max": float(max(st["true_rel_res"] for st in vstats)),
+            "roofline": {"kernel": "k_apcg_persistent<PrecE>", "bound": "hbm", "achieved": vgbs, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": vgbs / hbm_peak, "peak_kind": hbm_kind,
+                         "traffic": vtraffic, "traffic_alg_bytes": vtraffic_alg,
+                         "share_of_step_time": vt_iter / vms},
+            "gpu_launches": int(sum(st["kernel_launches"] for st in vstats)),
+            "clocks": vclk,
+            "what": "the same 20-system sequence, same warm-up and timing, precision KRS_DOUBLE_FLOAT "
+                    "(FP64 recurrences, projection and coarse solve; double-float directions and matrix values)"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(mats, b)
@@ -440,6 +479,8 @@ def run_krs(args, rank, world, local):
             "clocks": clk,
             "cpu_baseline": cpu,
         }
+        if variant is not None:
+            out["double_float"] = variant
         print(json.dumps(out))
     seq.close()
 
