@@ -8,9 +8,9 @@
 //
 // FP64 cost model (GB300, sm_103a): the FP64 pipe retires about 2 lane-operations per
 // clock per SM, so one warp-wide FP64 instruction costs ~16 SM clocks whatever its
-// active mask.  Inner loops therefore accumulate in registers (thread per column for
-// V^T u, thread per row for V s) and only the per-CTA results are combined, once,
-// through shared memory; no FP64 warp-shuffle trees run inside the streaming loops.
+// active mask.  Inner loops therefore accumulate in registers (a warp per 8-column block
+// for V^T u, thread per row quad for V s) and partial sums are combined once per column
+// block or per CTA; no FP64 warp-shuffle trees run inside the streaming loops.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -344,16 +344,18 @@ __device__ __forceinline__ void cta_gemv_t_few(const T* __restrict__ V, int64_t 
 }
 
 // ------------------------------------------------------------------------------------
-// Double-float tall-skinny products.  With the arithmetic on the FP32 pipes these are
-// bound by memory, so their layouts favour long contiguous runs per column:
-//   cta_gemv_t_df: a warp takes a block of 8 columns over a range of row pairs; lane l
-//     reads row pairs l, l + 32, ... of all 8 columns (512 contiguous bytes of each column
-//     per warp load), accumulates per column, and the 8 x 32 lane sums are folded by a
-//     transposed shuffle reduction (4 + 2 + 1 + 1 + 1 compensated adds per lane for 8
-//     columns).  Units (column block, row range) are spread over the 16 warps; row ranges
-//     are split only when there are fewer than 16 column blocks.
-//   cta_gemv_n_df: thread per row quad; G = floor(TPB / quads) column groups so that one
-//     pass covers every quad; 8-column unroll (256 bytes in flight per thread).
+// Tall-skinny layouts that favour long contiguous runs per column:
+//   cta_gemv_t_wb (V^T u; double-float, and FP64 as cta_gemv_t selects): a warp takes
+//     a block of 8 columns over a range of row pairs; lane l reads row pairs l, l + 32, ...
+//     of all 8 columns (512 contiguous bytes of each column per warp load), accumulates per
+//     column, and the 8 x 32 lane sums are folded once per block by a transposed shuffle
+//     reduction (4 + 2 + 1 + 1 + 1 adds per lane for 8 columns).  Units (column block, row
+//     range) are spread over the 16 warps.  A thread per column (the older layout) reads
+//     32 separate 128-byte runs per warp load: it streamed 2.9-3.7 TB/s at 696 rows per CTA
+//     and 1.7 TB/s at 5,340 (the 64^3 cube), against 4.7-5.3 TB/s for this layout.
+//   cta_gemv_n_df (u - V s, double-float): thread per row quad; G = floor(TPB / quads)
+//     column groups so that one pass covers every quad; 8-column unroll (256 bytes in flight
+//     per thread).
 // Row pairs / quads past r1 read the zero padding of the columns (r0 is a multiple of 4;
 // a column holds ld >= n + 1 values when n is odd).
 // ------------------------------------------------------------------------------------
@@ -365,63 +367,105 @@ __device__ __forceinline__ dacc dacc_shfl(dacc a, int m) {
   return dacc{__shfl_xor_sync(0xffffffffu, a.s, m), __shfl_xor_sync(0xffffffffu, a.c, m)};
 }
 
-// out[c] = sum_{i in [r0, r1)} V[c*ld + i] u[i] (c < k), double-float V and u.  red: shared,
-// >= 240 doubles (row-range partials when k < 128).
-template <bool NC>
-__device__ __forceinline__ void cta_gemv_t_df(const dfl* __restrict__ V, int64_t ld, int k, const dfl* __restrict__ u,
+// Per-type pieces of the warp-block layout of V^T u: a row pair of a column (16 bytes), a
+// multiply-add of two row pairs into the accumulator, and the lane combination.
+template <typename T>
+struct WB;
+template <>
+struct WB<double> {
+  using acc = double;
+  using P2 = double2;
+  __device__ static __forceinline__ acc zero() { return 0.0; }
+  template <bool NC>
+  __device__ static __forceinline__ P2 load(const double* p) {
+    return NC ? __ldg(reinterpret_cast<const double2*>(p)) : *reinterpret_cast<const double2*>(p);
+  }
+  __device__ static __forceinline__ P2 none() { return make_double2(0.0, 0.0); }
+  __device__ static __forceinline__ void mac2(acc& a, P2 x, P2 y) {
+    a += x.x * y.x;
+    a += x.y * y.y;
+  }
+  __device__ static __forceinline__ acc add(acc a, acc b) { return a + b; }
+  __device__ static __forceinline__ acc shfl(acc a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+  __device__ static __forceinline__ double out(acc a) { return a; }
+};
+template <>
+struct WB<dfl> {
+  using acc = dacc;
+  using P2 = float4;  // (hi, lo) of two rows
+  __device__ static __forceinline__ acc zero() { return dacc{0.f, 0.f}; }
+  template <bool NC>
+  __device__ static __forceinline__ P2 load(const dfl* p) {
+    return NC ? __ldg(reinterpret_cast<const float4*>(p)) : *reinterpret_cast<const float4*>(p);
+  }
+  __device__ static __forceinline__ P2 none() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ static __forceinline__ void mac2(acc& a, P2 x, P2 y) {
+    dfl x0, x1, y0, y1;
+    x0.hi = x.x; x0.lo = x.y; x1.hi = x.z; x1.lo = x.w;
+    y0.hi = y.x; y0.lo = y.y; y1.hi = y.z; y1.lo = y.w;
+    Acc<dfl>::mac(a, x0, y0);
+    Acc<dfl>::mac(a, x1, y1);
+  }
+  __device__ static __forceinline__ acc add(acc a, acc b) { return dacc_sum(a, b); }
+  __device__ static __forceinline__ acc shfl(acc a, int m) { return dacc_shfl(a, m); }
+  __device__ static __forceinline__ double out(acc a) { return Acc<dfl>::out(a); }
+};
+
+// Row ranges per 8-column block: split only when there are fewer blocks than warps (every
+// warp then gets a unit).  Splitting further to fill a last, partial wave of units was
+// measured slower (shorter per-lane runs, more lane reductions).
+__device__ __forceinline__ int wb_row_ranges(int nblk) {
+  constexpr int NW = TPB / 32;
+  return nblk >= NW ? 1 : (NW + nblk - 1) / nblk;
+}
+
+// out[c] = sum_{i in [r0, r1)} V[c*ld + i] u[i] (c < k), V and u of type T (double or
+// double-float), as doubles: the warp-block layout above.  red: shared, >= 256 doubles
+// (row-range partials).  The summation order depends only on k and the rows.
+template <bool NC, typename T>
+__device__ __forceinline__ void cta_gemv_t_wb(const T* __restrict__ V, int64_t ld, int k, const T* __restrict__ u,
                                               int64_t r0, int64_t r1, double* __restrict__ out, double* red) {
+  using W = WB<T>;
+  using A = typename W::acc;
+  using P2 = typename W::P2;
   constexpr int CB = 8;
   constexpr int NW = TPB / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t pairs = ((r1 - r0) + 1) >> 1;
   const int nblk = (k + CB - 1) / CB;
-  const int Rg = nblk >= NW ? 1 : (NW + nblk - 1) / nblk;  // row ranges per column block
+  const int Rg = wb_row_ranges(nblk);  // when Rg > 1: Rg * k <= (16 / nblk + 1) * 8 nblk <= 248
   const int units = nblk * Rg;
-  const dfl2* u2 = reinterpret_cast<const dfl2*>(u + r0);
+  const T* u2 = u + r0;
   for (int un = warp; un < units; un += NW) {
     const int blk = un / Rg, rg = un - blk * Rg;
     const int c0 = blk * CB;
     const int nc = min(CB, k - c0);
     const int64_t pa = pairs * rg / Rg, pb = pairs * (rg + 1) / Rg;
-    dacc acc[CB];
+    A acc[CB];
 #pragma unroll
-    for (int c = 0; c < CB; c++) acc[c] = dacc{0.f, 0.f};
-    const dfl* col0 = V + (int64_t)c0 * ld + r0;
+    for (int c = 0; c < CB; c++) acc[c] = W::zero();
+    const T* col0 = V + (int64_t)c0 * ld + r0;
     for (int64_t p = pa + lane; p < pb; p += 32) {
-      dfl2 x[CB];
+      P2 x[CB];
 #pragma unroll
-      for (int c = 0; c < CB; c++) {
-        if (c < nc) {
-          const float4 v = NC ? __ldg(reinterpret_cast<const float4*>(col0 + (int64_t)c * ld + 2 * p))
-                              : *reinterpret_cast<const float4*>(col0 + (int64_t)c * ld + 2 * p);
-          x[c].x.hi = v.x; x[c].x.lo = v.y; x[c].y.hi = v.z; x[c].y.lo = v.w;
-        } else {
-          x[c].x.hi = x[c].x.lo = x[c].y.hi = x[c].y.lo = 0.f;
-        }
-      }
-      const float4 uv = *reinterpret_cast<const float4*>(u2 + p);
-      dfl y0, y1;
-      y0.hi = uv.x; y0.lo = uv.y; y1.hi = uv.z; y1.lo = uv.w;
+      for (int c = 0; c < CB; c++) x[c] = c < nc ? W::template load<NC>(col0 + (int64_t)c * ld + 2 * p) : W::none();
+      const P2 y = W::template load<false>(u2 + 2 * p);
 #pragma unroll
-      for (int c = 0; c < CB; c++) {
-        Acc<dfl>::mac(acc[c], x[c].x, y0);
-        Acc<dfl>::mac(acc[c], x[c].y, y1);
-      }
+      for (int c = 0; c < CB; c++) W::mac2(acc[c], x[c], y);
     }
     // transposed reduction: after it, lane 4c holds column c0 + c (sum over all 32 lanes)
     const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-    dacc v4[4];
+    A v4[4];
 #pragma unroll
-    for (int i = 0; i < 4; i++)
-      v4[i] = dacc_sum(b4 ? acc[4 + i] : acc[i], dacc_shfl(b4 ? acc[i] : acc[4 + i], 16));
-    dacc v2[2];
+    for (int i = 0; i < 4; i++) v4[i] = W::add(b4 ? acc[4 + i] : acc[i], W::shfl(b4 ? acc[i] : acc[4 + i], 16));
+    A v2[2];
 #pragma unroll
-    for (int i = 0; i < 2; i++) v2[i] = dacc_sum(b3 ? v4[2 + i] : v4[i], dacc_shfl(b3 ? v4[i] : v4[2 + i], 8));
-    dacc v1 = dacc_sum(b2 ? v2[1] : v2[0], dacc_shfl(b2 ? v2[0] : v2[1], 4));
-    v1 = dacc_sum(v1, dacc_shfl(v1, 1));
-    v1 = dacc_sum(v1, dacc_shfl(v1, 2));
+    for (int i = 0; i < 2; i++) v2[i] = W::add(b3 ? v4[2 + i] : v4[i], W::shfl(b3 ? v4[i] : v4[2 + i], 8));
+    A v1 = W::add(b2 ? v2[1] : v2[0], W::shfl(b2 ? v2[0] : v2[1], 4));
+    v1 = W::add(v1, W::shfl(v1, 1));
+    v1 = W::add(v1, W::shfl(v1, 2));
     if ((lane & 3) == 0 && (lane >> 2) < nc) {
-      const double r = Acc<dfl>::out(v1);
+      const double r = W::out(v1);
       if (Rg == 1) out[c0 + (lane >> 2)] = r;
       else red[rg * k + c0 + (lane >> 2)] = r;
     }
@@ -516,9 +560,11 @@ __device__ __forceinline__ void cta_gemv_n_df(const dfl* __restrict__ V, int64_t
 // column: each thread streams its column with four-row vector loads into four independent
 // accumulators (no dependent FMA chain).  Columns are taken in blocks of kc with
 // G = ceil(TPB / rem) row groups each (kc = TPB / G), so that all threads stay busy
-// whatever k is; the groups are combined by a pairwise tree in a fixed order.
+// whatever k is; the groups are combined by a pairwise tree in a fixed order.  Double-float,
+// and FP64 with 17..256 columns or more than ROW_CHUNK rows, take the warp-block layout
+// (cta_gemv_t_wb).
 // u: global vector (zero padded past n).  su: shared (ROW_CHUNK values of T); red: shared
-// (TPB doubles).
+// (4 * TPB doubles).
 template <bool NC, typename T, typename TU = T>
 __device__ __forceinline__ void cta_gemv_t(const T* __restrict__ V, int64_t ld, int k,
                                            const TU* __restrict__ u, int64_t r0, int64_t r1,
@@ -526,8 +572,17 @@ __device__ __forceinline__ void cta_gemv_t(const T* __restrict__ V, int64_t ld, 
   using V4 = typename VT<T>::V4;
   if constexpr (std::is_same<T, dfl>::value) {
     static_assert(std::is_same<TU, dfl>::value, "double-float V^T u takes a double-float u");
-    cta_gemv_t_df<NC>(V, ld, k, u, r0, r1, out, red);
+    cta_gemv_t_wb<NC, dfl>(V, ld, k, u, r0, r1, out, red);
     return;
+  }
+  if constexpr (std::is_same<T, double>::value && std::is_same<TU, double>::value) {
+    // FP64: the warp-block layout up to 256 columns, and at any width once a CTA owns more
+    // rows than one staging chunk; thread per column streamed faster at ~700 rows per CTA and
+    // 400 columns (3.7 against 3.4 TB/s), far slower at 5,340 rows (1.7 against 4.8 TB/s)
+    if (k > TPB / 32 && (k <= 256 || r1 - r0 > ROW_CHUNK)) {
+      cta_gemv_t_wb<NC, double>(V, ld, k, u, r0, r1, out, red);
+      return;
+    }
   }
   if (k <= TPB / 32) {
     cta_gemv_t_few<NC, T, TU>(V, ld, k, u, r0, r1, out, red);

@@ -106,7 +106,7 @@ extern "C" krs_status krs_gemv_t_noalloc(int64_t n, int32_t k, const double* V, 
   double* part = nullptr;
   if (scratch_address(&part) != cudaSuccess)
     return set_error(KRS_ERR_CUDA, "krs_gemv_t_noalloc: cudaGetSymbolAddress of the scratch array failed");
-  const size_t sm = sizeof(double) * (size_t)(ROW_CHUNK + TPB);
+  const size_t sm = sizeof(double) * (size_t)(ROW_CHUNK + 4 * TPB);  // cta_gemv_t's staging and partials
   if (cudaFuncSetAttribute((const void*)k_noalloc_gemv_t_part, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sm) != cudaSuccess)
     return set_error(KRS_ERR_CUDA, "krs_gemv_t_noalloc: cudaFuncSetAttribute failed");

@@ -1,15 +1,18 @@
-"""Double-float search directions (KRS_DOUBLE_FLOAT) against the FP64 oracle.
+"""Double-float precision (KRS_DOUBLE_FLOAT) against the FP64 oracle.
 
-The solve is the FP64 one (operator product, preconditioner, recurrences, projection with
-the FP64 C and AC, coarse set-up, H_m) except that W, AW, Z are stored as double-float
-pairs (48-bit significand) and the reorthogonalisation's products are taken on the FP32
-pipes with error-free products and compensated sums (about 2^-46 relative).  That is far
-below the solve tolerance, so the FP64 parity bar applies unchanged: lock-step with the
-oracle, iterations within +-2, relative solution difference <= 1e-9 at equal counts.
+The solve is the FP64 one (preconditioner, recurrences, projection with the FP64 C and AC,
+coarse set-up, H_m) except that W, AW, Z and the matrix values are stored as double-float
+pairs (48-bit significand) and the operator product and the reorthogonalisation's products
+are taken on the FP32 pipes with error-free products and compensated sums (about 2^-46
+relative).  That is far below the solve tolerance, so the FP64 parity bar applies to the
+solves unchanged: lock-step with the oracle, iterations within +-2, relative solution
+difference <= 1e-9 at equal counts.  Ritz values that have not converged are the one
+quantity held to a looser, derived bound (test_dfloat_srks_damage_sequence).
 """
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1301_7530_gb300 import binding as B
 from paper_1301_7530_gb300 import problems as P
 
@@ -45,7 +48,13 @@ def test_dfloat_trks_fixed_matrix_sequence(gpu_lib):
 
 @pytest.mark.parametrize("eps,frac", [(1e-6, 0.1), (1e-10, 0.0)])
 def test_dfloat_srks_damage_sequence(gpu_lib, eps, frac):
-    """6^3 damage sequence, block Jacobi, SRKS in lock-step; Ritz values as the oracle's."""
+    """6^3 damage sequence, block Jacobi, SRKS in lock-step.  The selection is Eq. 16 applied
+    to the GPU's own Ritz values; selected (converged) values match the oracle's to 1e-9
+    theta_max.  Ritz values that have not converged depend on the last iterations' alpha and
+    rho, which sit at the residual's rounding floor: the recursive residual carries the
+    operator products' rounding, ~m 2^-46 ||r_0|| in double-float, so relative to a residual
+    of tol ||b|| the last coefficients move by ~m 2^-46 / tol (1e-4 at m = 80, tol = 1e-8);
+    all values are held to 1e-3 theta_max."""
     N = 6
     mask, b, gen = P.elasticity_sequence_damage(N, 6, 11, 2000)
     seq = B.Sequence(3 * N * (N + 1) ** 2)
@@ -57,7 +66,11 @@ def test_dfloat_srks_damage_sequence(gpu_lib, eps, frac):
         tm, tm1, sel = seq.last_ritz()
         otm, otm1, osel, oY = ora.ritz()
         if st["m"] == so["m"] and st["m"] >= 2:
-            assert np.allclose(tm, otm, atol=1e-11 * otm[0])
+            assert np.max(np.abs(tm - otm)) <= 1e-3 * otm[0]
+            assert list(O.srks_select(tm, tm1, eps, frac, 60 - st["n_c"])) == list(sel)
+            if list(sel) == list(osel):
+                for i in sel:
+                    assert abs(tm[i] - otm[i]) <= 1e-9 * otm[0]
             if list(sel) == list(osel) and len(sel):
                 Yg = seq.export_space()[:, st["n_c"]:]
                 for c in range(len(sel)):
@@ -127,7 +140,6 @@ def test_dfloat_full_size_first_system(gpu_lib):
 def test_dfloat_batched_lockstep(gpu_lib):
     """Four damage sequences of uneven sizes in the batched engine in double-float, three
     systems each, each solve against the oracle from the same space."""
-    import oracle as O
     Ns = [4, 7, 5, 6]
     probs = []
     for i, N in enumerate(Ns):
