@@ -208,9 +208,10 @@ def profiled_traffic(precision="fp64"):
     txt = open(path).read()
     vals = {}
     for line in txt.splitlines():
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "algorithmic_bytes_per_launch",
-                                                    "csrc_sha256")):
-            k, v = line.strip().split(":", 1)
+        item = line.strip().lstrip("-* ").strip()  # markdown list items "- key: `value`"
+        if ":" in item and item.startswith(("traffic_bytes_per_launch", "algorithmic_bytes_per_launch",
+                                            "csrc_sha256")):
+            k, v = item.split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("csrc_sha256") != csrc_digest():
         return None, None
