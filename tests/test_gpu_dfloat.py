@@ -160,3 +160,38 @@ def test_dfloat_batched_lockstep(gpu_lib):
             ora.set_C(C)
             xo, so = ora.solve(mats[k], b, 1e-8, oracle_policy(pol))
             check_pair(mats[k], b, 1e-8, pol, x, st, xo, so, C)
+
+
+def test_dfloat_and_fp64_in_one_engine(gpu_lib):
+    """FP64 and double-float solves submitted to one engine (each step launches once per
+    precision present): every result against the oracle from the same space, two systems."""
+    Ns = [5, 6, 4, 7]
+    precs = ["fp64", DF, DF, "fp64"]
+    probs = []
+    for i, N in enumerate(Ns):
+        mask, b, gen = P.elasticity_sequence_damage(N, 2, 60 + i, 3100 + i)
+        probs.append((N, b, [Ak for _, Ak in gen]))
+    seqs = [B.Sequence(3 * N * (N + 1) ** 2) for N, _, _ in probs]
+    pols = [B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, theta_frac=0.1, max_aug=60, precision=p)
+            for p in precs]
+    eng = B.Batch(group_ctas=0)
+    for k in range(2):
+        Cs = [s.export_space() for s in seqs]
+        for i, (s, (N, b, mats)) in enumerate(zip(seqs, probs)):
+            eng.submit(s, mats[k], b, 1e-8, pols[i], tag=i, version=k + 1)
+        done = {}
+        for _ in range(1000):
+            for tag, status, x in eng.step():
+                done[tag] = (status, x)
+            if len(done) == len(seqs):
+                break
+        assert sorted(done) == list(range(len(seqs)))
+        for i, ((N, b, mats), s, C) in enumerate(zip(probs, seqs, Cs)):
+            status, x = done[i]
+            assert status == 0
+            st = s.stats()
+            ora = O.Sequence(3 * N * (N + 1) ** 2)
+            ora.set_C(C)
+            xo, so = ora.solve(mats[k], b, 1e-8, oracle_policy(pols[i]))
+            check_pair(mats[k], b, 1e-8, pols[i], np.asarray(x), st, xo, so, C)
+    eng.close()
