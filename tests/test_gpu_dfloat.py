@@ -195,3 +195,31 @@ def test_dfloat_and_fp64_in_one_engine(gpu_lib):
             xo, so = ora.solve(mats[k], b, 1e-8, oracle_policy(pols[i]))
             check_pair(mats[k], b, 1e-8, pols[i], np.asarray(x), st, xo, so, C)
     eng.close()
+
+
+def test_dfloat_trks_changing_matrix(gpu_lib):
+    """TRKS over a damage sequence (A changes every system): the appended double-float
+    directions are converted to FP64 and A C is recomputed by the FP64 product; lock-step."""
+    N = 5
+    mask, b, gen = P.elasticity_sequence_damage(N, 4, 17, 2003)
+    seq = B.Sequence(3 * N * (N + 1) ** 2)
+    pol = B.make_policy("trks", "block_jacobi3", max_aug=150, precision=DF)
+    for k, Ak in gen:
+        x, st, xo, so, ora, C = solve_pair(seq, Ak, b, 1e-8, pol, version=k + 1)
+        check_pair(Ak, b, 1e-8, pol, x, st, xo, so, C)
+        assert st["n_c_after"] == min(150, st["n_c"] + st["m"])
+
+
+def test_dfloat_after_release(gpu_lib):
+    """Releasing the scratch (directions, FP64 copies of w and q, the double-float matrix) and
+    the matrix between solves: the next double-float solve re-creates them and gives the same
+    bits."""
+    A, bs = P.elasticity_sequence_fixed(5, 1, 77)
+    seq = B.Sequence(A.n)
+    pol = B.make_policy("none", "block_jacobi3", precision=DF)
+    x1, st1 = seq.solve(A, bs[0], 1e-9, pol, version=1)
+    held = seq.device_bytes()
+    seq.release(B.RELEASE_SCRATCH | B.RELEASE_MATRIX)
+    assert seq.device_bytes() < held
+    x2, st2 = seq.solve(A, bs[0], 1e-9, pol, version=1)
+    assert st2["m"] == st1["m"] and np.array_equal(x1, x2)
