@@ -161,8 +161,11 @@ def workload(N, systems, rank, problem="damage"):
 
 
 def alg_counts(N, precond_bytes_per_dof, m, nc):
-    """Algorithmic FP64 flops and bytes of one launch of the iteration kernel
-    (m iterations, augmentation size nc); see the design doc for the derivation."""
+    """Algorithmic FP64 flops and bytes of one launch of the iteration kernel (m iterations,
+    augmentation size nc): every array counted once per phase that needs it -- the operator
+    product 76 bytes and 18 flops per block, the updates and the preconditioner O(n), the two
+    projection products 8 n nc bytes each, the reorthogonalisation 16 n (j + 1) bytes; the last
+    iteration stops after the convergence test."""
     s = P.sizes(N)
     n, nb, nodes = s["n"], s["nb"], s["free_nodes"]
     flops = 0.0
