@@ -386,7 +386,9 @@ krs_status krs_tridiag_eigvecs(int32_t m, const double* delta, const double* eta
  * the library holds until the process exits.  Limits: k <= 1024 (larger k returns
  * KRS_ERR_INVALID_ARG with a message); the row blocks follow krs_gemv_t's partition (at
  * most one per SM).  The first call on each device looks up the array's device address on
- * that device; make that first call before any stream capture.  All calls share the array
+ * that device (and a call made under a new context of that device, after cudaDeviceReset
+ * for instance, looks it up again); make that first call before any stream capture.  It
+ * launches krs_gemv_t's own kernels on krs_gemv_t's partition.  All calls share the array
  * and it keeps the previous call's contents (nothing needs clearing: every value read is
  * written first by the same call); calls whose kernels overlap on the GPU race.
  * Arguments, layout and alignment as for krs_gemv_t; asynchronous on `stream`. */

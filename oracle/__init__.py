@@ -5,6 +5,10 @@ of ``bench.py`` are the only callers.  The product path (``paper_1301_7530_gb300
 imports this package.  The arithmetic lives in ``krs_oracle.c`` (plain C, FP64, evaluated
 as written); this module only compiles it with gcc and marshals numpy arrays.
 
+Two builds of the same file: ``liborc.so`` (the parity oracle, sequential sums) and
+``liborc_omp.so`` (``-fopenmp``: the long loops split across host threads), which only the
+benchmark's CPU baseline loads (``omp=True``) to time the oracle on all host cores.
+
 Parity status of each function (what pins it; the pins live under tests/):
   spmv, precond            -- dense products on tiny meshes, block inverse identity
   cholesky / chol_solve    -- numpy.linalg.cholesky / solve (library references)
@@ -32,8 +36,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "krs_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liborc.so")
+_LIB_OMP_PATH = os.path.join(_BUILD, "liborc_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 OK, ERR_INVALID_ARG, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_OOM = 0, 1, 2, 3, 4
 RECYCLE = {"none": 0, "trks": 1, "srks": 2}
@@ -58,54 +64,85 @@ class Stats(ct.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-def build(force: bool = False) -> str:
-    """Compile krs_oracle.c with gcc into oracle/_build/liborc.so (idempotent)."""
+def _compile(path: str, extra, force: bool) -> str:
     with _lock:
         os.makedirs(_BUILD, exist_ok=True)
-        if (not force and os.path.exists(_LIB_PATH)
-                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-            return _LIB_PATH
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+        if (not force and os.path.exists(path)
+                and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+            return path
+        tmp = path + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *extra,
                "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-        return _LIB_PATH
+        subprocess.run(cmd, check=True, capture_output=True)
+        os.replace(tmp, path)
+        return path
 
 
-def lib():
-    global _lib
+def build(force: bool = False) -> str:
+    """Compile krs_oracle.c with gcc into oracle/_build/liborc.so (the parity oracle) and,
+    when the compiler supports OpenMP, oracle/_build/liborc_omp.so (the timing build)."""
+    path = _compile(_LIB_PATH, [], force)
+    try:
+        _compile(_LIB_OMP_PATH, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass  # the timing build is optional; build_omp() raises the reason
+    return path
+
+
+def build_omp(force: bool = False) -> str:
+    """The OpenMP timing build (raises when the compiler cannot build it)."""
+    return _compile(_LIB_OMP_PATH, ["-fopenmp"], force)
+
+
+def lib(omp: bool = False):
+    """The parity oracle (omp=False) or the OpenMP timing build (omp=True)."""
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            _lib_omp = _declare(ct.CDLL(build_omp()))
+        return _lib_omp
     if _lib is None:
-        L = ct.CDLL(build())
-        dp, ip = ct.POINTER(ct.c_double), ct.POINTER(ct.c_int32)
-        L.orc_spmv.argtypes = [ct.c_int, ip, ip, dp, dp, dp]
-        L.orc_precond_setup.argtypes = [ct.c_int, ct.c_int, ip, ip, dp, dp]
-        L.orc_precond_apply.argtypes = [ct.c_int, ct.c_int, dp, dp, dp]
-        L.orc_cholesky.argtypes = [ct.c_int, dp]
-        L.orc_chol_solve.argtypes = [ct.c_int, dp, dp]
-        L.orc_lanczos.argtypes = [ct.c_int, dp, dp, dp, dp]
-        L.orc_sym_eig.argtypes = [ct.c_int, dp, dp, dp]
-        L.orc_tridiag_eig.argtypes = [ct.c_int, dp, dp, dp, dp]
-        L.orc_srks_select.argtypes = [ct.c_int, dp, dp, ct.c_double, ct.c_double, ct.c_int, ip]
-        L.orc_srks_select2.argtypes = [ct.c_int, dp, dp, ct.c_double, ct.c_double, ct.c_int, ct.c_int, ip]
-        L.orc_cluster_reselect.argtypes = [ct.c_int, dp, ip]
-        L.orc_cluster_reselect.restype = None
-        L.orc_seq_create.argtypes = [ct.c_int64]
-        L.orc_seq_create.restype = ct.c_void_p
-        L.orc_seq_destroy.argtypes = [ct.c_void_p]
-        for f in ("orc_seq_nc", "orc_seq_m", "orc_seq_nsel"):
-            getattr(L, f).argtypes = [ct.c_void_p]
-        L.orc_seq_get_C.argtypes = [ct.c_void_p, dp]
-        L.orc_seq_set_C.argtypes = [ct.c_void_p, ct.c_int, dp, ct.c_int]
-        L.orc_seq_get_W.argtypes = [ct.c_void_p, dp]
-        L.orc_seq_get_AW.argtypes = [ct.c_void_p, dp]
-        L.orc_seq_get_Z.argtypes = [ct.c_void_p, dp]
-        L.orc_seq_get_coeffs.argtypes = [ct.c_void_p, dp, dp, dp]
-        L.orc_seq_get_ritz.argtypes = [ct.c_void_p, dp, dp, ip, dp]
-        L.orc_seq_solve.argtypes = [ct.c_void_p, ct.c_int, ip, ip, dp, dp, dp, ct.c_double,
-                                    ct.POINTER(Policy), ct.POINTER(Stats)]
-        _lib = L
+        _lib = _declare(ct.CDLL(build()))
     return _lib
+
+
+def _declare(L):
+    """Argument types of the library's functions."""
+    dp, ip = ct.POINTER(ct.c_double), ct.POINTER(ct.c_int32)
+    L.orc_spmv.argtypes = [ct.c_int, ip, ip, dp, dp, dp]
+    L.orc_precond_setup.argtypes = [ct.c_int, ct.c_int, ip, ip, dp, dp]
+    L.orc_precond_apply.argtypes = [ct.c_int, ct.c_int, dp, dp, dp]
+    L.orc_cholesky.argtypes = [ct.c_int, dp]
+    L.orc_chol_solve.argtypes = [ct.c_int, dp, dp]
+    L.orc_lanczos.argtypes = [ct.c_int, dp, dp, dp, dp]
+    L.orc_sym_eig.argtypes = [ct.c_int, dp, dp, dp]
+    L.orc_tridiag_eig.argtypes = [ct.c_int, dp, dp, dp, dp]
+    L.orc_srks_select.argtypes = [ct.c_int, dp, dp, ct.c_double, ct.c_double, ct.c_int, ip]
+    L.orc_srks_select2.argtypes = [ct.c_int, dp, dp, ct.c_double, ct.c_double, ct.c_int, ct.c_int, ip]
+    L.orc_cluster_reselect.argtypes = [ct.c_int, dp, ip]
+    L.orc_cluster_reselect.restype = None
+    L.orc_seq_create.argtypes = [ct.c_int64]
+    L.orc_seq_create.restype = ct.c_void_p
+    L.orc_seq_destroy.argtypes = [ct.c_void_p]
+    for f in ("orc_seq_nc", "orc_seq_m", "orc_seq_nsel"):
+        getattr(L, f).argtypes = [ct.c_void_p]
+    L.orc_seq_get_C.argtypes = [ct.c_void_p, dp]
+    L.orc_seq_set_C.argtypes = [ct.c_void_p, ct.c_int, dp, ct.c_int]
+    L.orc_seq_get_W.argtypes = [ct.c_void_p, dp]
+    L.orc_seq_get_AW.argtypes = [ct.c_void_p, dp]
+    L.orc_seq_get_Z.argtypes = [ct.c_void_p, dp]
+    L.orc_seq_get_coeffs.argtypes = [ct.c_void_p, dp, dp, dp]
+    L.orc_seq_get_ritz.argtypes = [ct.c_void_p, dp, dp, ip, dp]
+    L.orc_seq_solve.argtypes = [ct.c_void_p, ct.c_int, ip, ip, dp, dp, dp, ct.c_double,
+                                ct.POINTER(Policy), ct.POINTER(Stats)]
+    L.orc_seq_get_times.argtypes = [ct.c_void_p, dp]
+    L.orc_num_threads.argtypes = []
+    return L
+
+
+def num_threads(omp: bool = False) -> int:
+    """Host threads the build's loops use (1 for the parity build)."""
+    return int(lib(omp).orc_num_threads())
 
 
 def _d(a):
@@ -127,11 +164,11 @@ def _bsr_args(A):
     return rp, ci, v
 
 
-def spmv(A, x):
+def spmv(A, x, omp: bool = False):
     rp, ci, v = _bsr_args(A)
     x = _f64(x)
     y = np.empty(A.n)
-    lib().orc_spmv(A.n_block_rows, _i(rp), _i(ci), _d(v), _d(x), _d(y))
+    lib(omp).orc_spmv(A.n_block_rows, _i(rp), _i(ci), _d(v), _d(x), _d(y))
     return y
 
 
@@ -191,13 +228,13 @@ def sym_eig(S):
     return th, np.asarray(Q)
 
 
-def tridiag_eig(delta, eta, vectors=True):
+def tridiag_eig(delta, eta, vectors=True, omp: bool = False):
     delta, eta = _f64(delta), _f64(eta)
     m = delta.shape[0]
     th = np.empty(m)
     Q = np.empty((m, m), order="F") if vectors else None
     e = eta if eta.size else np.zeros(1)
-    lib().orc_tridiag_eig(m, _d(delta), _d(e), _d(th),
+    lib(omp).orc_tridiag_eig(m, _d(delta), _d(e), _d(th),
                           Q.ctypes.data_as(ct.POINTER(ct.c_double)) if vectors else None)
     return (th, np.asarray(Q)) if vectors else th
 
@@ -230,39 +267,40 @@ def make_policy(recycle="none", precond="jacobi", reorth="full", cap_mode="trunc
 class Sequence:
     """Oracle sequence state: the augmentation basis C and the last solve's internals."""
 
-    def __init__(self, n: int):
+    def __init__(self, n: int, omp: bool = False):
         self.n = int(n)
-        self._h = lib().orc_seq_create(self.n)
+        self._L = lib(omp)
+        self._h = self._L.orc_seq_create(self.n)
         if not self._h:
             raise MemoryError
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h and _lib is not None:
-            _lib.orc_seq_destroy(h)
+        if h:
+            self._L.orc_seq_destroy(h)
             self._h = None
 
     @property
     def nc(self) -> int:
-        return lib().orc_seq_nc(self._h)
+        return self._L.orc_seq_nc(self._h)
 
     @property
     def m(self) -> int:
-        return lib().orc_seq_m(self._h)
+        return self._L.orc_seq_m(self._h)
 
     @property
     def C(self) -> np.ndarray:
         nc = self.nc
         out = np.empty((nc, self.n))
         if nc:
-            lib().orc_seq_get_C(self._h, _d(out))
+            self._L.orc_seq_get_C(self._h, _d(out))
         return out.T  # n x nc view (column-major storage)
 
     def set_C(self, C, as_c0: bool = False):
         C = np.asarray(C, dtype=np.float64)
         nc = 0 if C.size == 0 else C.shape[1]
         buf = np.ascontiguousarray(C.T) if nc else np.zeros(1)
-        st = lib().orc_seq_set_C(self._h, nc, _d(buf), int(as_c0))
+        st = self._L.orc_seq_set_C(self._h, nc, _d(buf), int(as_c0))
         if st:
             raise MemoryError
 
@@ -274,35 +312,41 @@ class Sequence:
 
     @property
     def W(self):
-        return self._cols(lib().orc_seq_get_W, self.m)
+        return self._cols(self._L.orc_seq_get_W, self.m)
 
     @property
     def AW(self):
-        return self._cols(lib().orc_seq_get_AW, self.m)
+        return self._cols(self._L.orc_seq_get_AW, self.m)
 
     @property
     def Z(self):
-        return self._cols(lib().orc_seq_get_Z, self.m)
+        return self._cols(self._L.orc_seq_get_Z, self.m)
 
     def coeffs(self):
         m = self.m
         a, r, g = np.empty(max(m, 1)), np.empty(max(m, 1)), np.empty(max(m, 1))
-        lib().orc_seq_get_coeffs(self._h, _d(a), _d(r), _d(g))
+        self._L.orc_seq_get_coeffs(self._h, _d(a), _d(r), _d(g))
         return a[:m], r[:m], g[:m]
 
     def ritz(self):
-        m, ns = self.m, lib().orc_seq_nsel(self._h)
+        m, ns = self.m, self._L.orc_seq_nsel(self._h)
         tm, tm1 = np.empty(max(m, 1)), np.empty(max(m, 1))
         sel = np.empty(max(ns, 1), dtype=np.int32)
         Y = np.empty((max(ns, 1), self.n))
-        lib().orc_seq_get_ritz(self._h, _d(tm), _d(tm1), _i(sel), _d(Y))
+        self._L.orc_seq_get_ritz(self._h, _d(tm), _d(tm1), _i(sel), _d(Y))
         return tm[:m], tm1[:max(m - 1, 0)], sel[:ns], Y[:ns].T
+
+    def times(self):
+        """Wall-clock seconds of the last solve's set-up, iterations and recycling."""
+        out = np.zeros(3)
+        self._L.orc_seq_get_times(self._h, _d(out))
+        return out
 
     def solve(self, A, b, tol: float, policy: Policy):
         rp, ci, v = _bsr_args(A)
         b = _f64(b)
         x = np.zeros(self.n)
         st = Stats()
-        lib().orc_seq_solve(self._h, A.n_block_rows, _i(rp), _i(ci), _d(v), _d(b), _d(x),
+        self._L.orc_seq_solve(self._h, A.n_block_rows, _i(rp), _i(ci), _d(v), _d(b), _d(x),
                             float(tol), ct.byref(policy), ct.byref(st))
         return x, st.as_dict()

@@ -28,11 +28,24 @@
  *   - Convergence: ||r_j||^2 <= tol^2 ||b||^2 on the recursive residual.
  * Every floating-point expression is evaluated as written (compiled with
  * -ffp-contract=off), in plain loops, with no blocking or reordering.
+ *
+ * Timing build.  The same file is also compiled with -fopenmp into a second library that
+ * only the CPU baseline of the benchmark loads: the "omp" pragmas below split the long
+ * loops over n (and the sparse product's rows) across host threads.  The parity build is
+ * compiled without -fopenmp, so there the pragmas are inert and every sum keeps the
+ * sequential order written here.  Wall-clock stamps of the solve's three stages (set-up,
+ * iterations, recycling) are recorded for the benchmark's cost model; they do not touch
+ * the arithmetic.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { ORC_OK = 0, ORC_ERR_INVALID_ARG = 1, ORC_ERR_NOT_SPD = 2, ORC_ERR_NO_CONVERGENCE = 3,
        ORC_ERR_OOM = 4 };
@@ -59,6 +72,7 @@ typedef struct {
 /* y = A x for a 3x3 block-CSR A: y_{3i+d} = sum_k sum_e A_k[d][e] x_{3 col_k + e}. */
 void orc_spmv(int nbr, const int32_t* rp, const int32_t* ci, const double* v,
               const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < nbr; i++) {
     for (int d = 0; d < 3; d++) {
       double s = 0.0;
@@ -72,6 +86,7 @@ void orc_spmv(int nbr, const int32_t* rp, const int32_t* ci, const double* v,
 
 static double dot(int64_t n, const double* a, const double* b) {
   double s = 0.0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
   for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
   return s;
 }
@@ -107,10 +122,13 @@ int orc_precond_setup(int kind, int nbr, const int32_t* rp, const int32_t* ci,
 void orc_precond_apply(int kind, int nbr, const double* minv, const double* r, double* u) {
   int64_t n = 3 * (int64_t)nbr;
   if (kind == ORC_PRECOND_IDENTITY) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) u[i] = r[i];
   } else if (kind == ORC_PRECOND_JACOBI) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) u[i] = minv[i] * r[i];
   } else {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < nbr; i++)
       for (int d = 0; d < 3; d++)
         u[3 * i + d] = minv[9 * i + 3 * d + 0] * r[3 * i + 0] + minv[9 * i + 3 * d + 1] * r[3 * i + 1]
@@ -365,7 +383,27 @@ typedef struct {
   int32_t* sel;
   int n_sel;
   orc_stats st;
+  double t_stage[3];  /* seconds of the last solve: set-up + init, iterations, recycling */
 } orc_seq;
+
+static double wall_seconds(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/* Wall-clock seconds of the last solve's stages (set-up and initialisation, the iteration
+ * loop, the recycling step). */
+void orc_seq_get_times(const orc_seq* s, double* out) { memcpy(out, s->t_stage, sizeof(s->t_stage)); }
+
+/* Host threads the library's loops use (1 in the parity build). */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 orc_seq* orc_seq_create(int64_t n) {
   orc_seq* s = (orc_seq*)calloc(1, sizeof(orc_seq));
@@ -456,12 +494,15 @@ static int grow(orc_seq* s, int need) {
 /* z = P M^-1 r with P = I - C (C^T A C)^-1 C^T A, applied as u - C L^-T L^-1 (AC)^T u. */
 static void project(int64_t n, int nc, const double* C, const double* AC, const double* L,
                     const double* u, double* z, double* t) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; i++) z[i] = u[i];
   if (nc == 0) return;
   for (int c = 0; c < nc; c++) t[c] = dot(n, AC + (int64_t)c * n, u);
   orc_chol_solve(nc, L, t);
-  for (int c = 0; c < nc; c++)
+  for (int c = 0; c < nc; c++) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) z[i] -= C[(int64_t)c * n + i] * t[c];
+  }
 }
 
 /* One solve of the sequence, APCG(A, M, C, b) (Algorithm 1 with full reorthogonalisation)
@@ -482,6 +523,8 @@ int orc_seq_solve(orc_seq* s, int nbr, const int32_t* rp, const int32_t* ci, con
   }
   const int nc = s->nc;
   int status = ORC_OK;
+  double t_mark = wall_seconds();
+  s->t_stage[0] = s->t_stage[1] = s->t_stage[2] = 0.0;
   double *minv = NULL, *AC = NULL, *L = NULL, *r = NULL, *u = NULL, *z = NULL, *t = NULL,
          *g = NULL, *q = NULL, *res = NULL;
   minv = (double*)malloc(sizeof(double) * 9 * (size_t)nbr);
@@ -513,11 +556,13 @@ int orc_seq_solve(orc_seq* s, int nbr, const int32_t* rp, const int32_t* ci, con
   if (nc > 0) {
     for (int c = 0; c < nc; c++) t[c] = dot(n, s->C + (int64_t)c * n, b);
     orc_chol_solve(nc, L, t);
-    for (int c = 0; c < nc; c++)
+    for (int c = 0; c < nc; c++) {
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; i++) {
         x[i] += s->C[(int64_t)c * n + i] * t[c];
         r[i] -= AC[(int64_t)c * n + i] * t[c];
       }
+    }
   }
   double rr = dot(n, r, r);
   st.rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
@@ -531,6 +576,8 @@ int orc_seq_solve(orc_seq* s, int nbr, const int32_t* rp, const int32_t* ci, con
   memcpy(s->W, z, sizeof(double) * n);
   s->rho[0] = dot(n, r, z);
   if (!(s->rho[0] > 0.0)) { status = ORC_ERR_NOT_SPD; goto done; }
+  s->t_stage[0] = wall_seconds() - t_mark;
+  t_mark = wall_seconds();
 
   for (int j = 0;; j++) {
     double* wj = s->W + (int64_t)j * n;
@@ -541,6 +588,7 @@ int orc_seq_solve(orc_seq* s, int nbr, const int32_t* rp, const int32_t* ci, con
     double alpha = dot(n, r, wj) / gam;
     s->gamma[j] = gam;
     s->alpha[j] = alpha;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) { x[i] += alpha * wj[i]; r[i] -= alpha * qj[i]; }
     s->m = j + 1;
     rr = dot(n, r, r);
@@ -561,12 +609,18 @@ int orc_seq_solve(orc_seq* s, int nbr, const int32_t* rp, const int32_t* ci, con
     if (!g) { status = ORC_ERR_OOM; goto done; }
     for (int i = i0; i <= j; i++) g[i] = dot(n, s->AW + (int64_t)i * n, z) / s->gamma[i];
     double* wn = s->W + (int64_t)(j + 1) * n;
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n; k++) wn[k] = z[k];
-    for (int i = i0; i <= j; i++)
+    for (int i = i0; i <= j; i++) {
+#pragma omp parallel for schedule(static)
       for (int64_t k = 0; k < n; k++) wn[k] -= g[i] * s->W[(int64_t)i * n + k];
+    }
   }
 
 converged:
+  if (s->t_stage[0] == 0.0) s->t_stage[0] = wall_seconds() - t_mark;  /* m = 0: set-up only */
+  else s->t_stage[1] = wall_seconds() - t_mark;
+  t_mark = wall_seconds();
   /* true residual */
   orc_spmv(nbr, rp, ci, v, x, res);
   {
@@ -619,8 +673,10 @@ converged:
           double* y = s->Y + (int64_t)c * n;
           for (int j = 0; j < m; j++) {
             double f = ((j & 1) ? -1.0 : 1.0) / sqrt(s->rho[j]) * Q[j + (int64_t)idx * m];
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < n; i++) y[i] += s->Z[(int64_t)j * n + i] * f;
           }
+#pragma omp parallel for schedule(static)
           for (int64_t i = 0; i < n; i++) y[i] *= sc;
         }
       }
@@ -640,9 +696,11 @@ converged:
       orc_seq_set_C(s, s->nc0, s->C0, 0);
     }
     st.n_c_after = s->nc;
+    s->t_stage[2] = wall_seconds() - t_mark;
   }
 
 done:
+  if (status && s->t_stage[1] == 0.0 && s->t_stage[0] > 0.0) s->t_stage[1] = wall_seconds() - t_mark;
   if (status) st.m = s->m;
   st.status = status;
   if (out) *out = st;

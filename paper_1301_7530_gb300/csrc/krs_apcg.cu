@@ -17,8 +17,9 @@
 //       u = M^-1 r; partials t = (AC)^T u
 //   P3  convergence ||r||^2 <= tol^2 ||b||^2; t reduced (slice, or whole when n_c is small)
 //   P4  slice of s = (C^T A C)^-1 t (only when n_c is not small)
-//   P5  z = u - C s (stored as Z[:, j+1]); partials (r, z), g = (AW)^T z
-//   P6  rho_{j+1} = (r, z); slice of g_i / gamma_i
+//   P5  z = u - C s (Z[:, j+1], or the single z column); partials (r, z), g = (AW)^T z
+//   P6  rho_{j+1} = (r, z); slice of g_i / gamma_i (also kept in the packed coefficient
+//       rows U when z is not stored: z_{j+1} = w_{j+1} + sum_i g_i w_i)
 //   P7  w_{j+1} = z - W g (stored as W[:, j+1])
 // The projection P u = u - C (C^T A C)^-1 (AC)^T u is the projector of Eq. 5; its two
 // block products and the coarse solve are the items of Section 2.3.
@@ -79,7 +80,10 @@ struct ApcgCtx {
   const double* Ginv;
   M* W;
   M* AW;
-  M* Z;
+  M* Z;                // z_j: column j at Z + j * zld (zld = 0: one column, reused)
+  int64_t zld;
+  double* ucoef;       // zld = 0: packed reorthogonalisation coefficients, row j at
+                       // j (j - 1) / 2 holding g_i of w_j = z_j - sum_{i<j} g_i w_i
   V* x;
   V* r;
   V* u;
@@ -328,7 +332,7 @@ __device__ __forceinline__ void phase5(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm
   using MC = typename Pr::MC;
   int64_t r0, r1;
   cta_rows(c.nbr, c.npc, c.lb, r0, r1);
-  M* z = c.Z + (int64_t)(j + 1) * c.ld;
+  M* z = c.Z + (int64_t)(j + 1) * c.zld;
   if (c.nc > 0) {
     if (!s_in_smem) {
       for (int k = threadIdx.x; k < c.nc; k += TPB) sm.svc[k] = (MC)c.sfull[k];
@@ -362,9 +366,14 @@ __device__ __forceinline__ int phase6(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm)
   int a, e;
   col_slice(kk, c.P, c.lb, a, e);
   const int warp = threadIdx.x >> 5;
+  double* urow = c.ucoef ? c.ucoef + (int64_t)(j + 1) * j / 2 + base : nullptr;  // row j + 1 of U
   for (int col = a + warp; col < e; col += TPB / 32) {
     const double v = warp_sum_strided(c.gpart + col, c.P, c.vld);
-    if ((threadIdx.x & 31) == 0) c.gfull[col] = v / c.gamma[base + col];
+    if ((threadIdx.x & 31) == 0) {
+      const double g = v / c.gamma[base + col];
+      c.gfull[col] = g;
+      if (urow) urow[col] = g;
+    }
   }
   return PH_CONTINUE;
 }
@@ -378,7 +387,7 @@ __device__ __forceinline__ void phase7(const ApcgCtx<Pr>& c, int j, Smem<Pr>& sm
   const int kk = j + 1 - base;
   for (int k = threadIdx.x; k < kk; k += TPB) sm.sv[k] = (M)c.gfull[k];
   __syncthreads();
-  const M* z = c.Z + (int64_t)(j + 1) * c.ld;
+  const M* z = c.Z + (int64_t)(j + 1) * c.zld;
   M* wn = c.W + (int64_t)(j + 1) * c.ld;
   double* wv = nullptr;
   if constexpr (Pr::id == 3) wv = c.wv;  // the FP64 copy of w_{j+1} for the next operator product
@@ -700,6 +709,7 @@ static ApcgCtx<Pr> make_ctx(const IterArgs& a) {
   c.C = static_cast<const typename Pr::MC*>(a.C); c.AC = static_cast<const typename Pr::MC*>(a.AC);
   c.Ginv = a.Ginv;
   c.W = static_cast<M*>(a.W); c.AW = static_cast<M*>(a.AW); c.Z = static_cast<M*>(a.Z);
+  c.zld = a.zld; c.ucoef = a.zld == 0 ? a.ucoef : nullptr;
   c.x = static_cast<V*>(a.x); c.r = static_cast<V*>(a.r); c.u = static_cast<V*>(a.u);
   c.q = static_cast<V*>(a.q);
   c.wv = static_cast<V*>(a.wv);

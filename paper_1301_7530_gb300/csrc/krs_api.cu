@@ -167,19 +167,24 @@ static krs_status ensure_scalars(krs_seq* s, int need, int keep) {
   return KRS_OK;
 }
 
-// FP64 direction storage (W, AW, Z) and the scalars for max_iter iterations
+// packed reorthogonalisation coefficient rows of `cap` columns (rows 1 .. cap - 1)
+static size_t ucoef_entries(int cap) { return cap > 1 ? (size_t)cap * (size_t)(cap - 1) / 2 : 1; }
+
+// FP64 direction storage (W, AW, one z column, the coefficient rows U) and the scalars for
+// max_iter iterations
 static krs_status ensure_cap_w(krs_seq* s, int max_iter) {
   const int need = max_iter + 1;
   KRS_TRY(ensure_scalars(s, need, 0));
+  if (!s->Z) KRS_TRY(alloc_n(s, &s->Z, (size_t)s->ld));
   if (need <= s->cap_w) return KRS_OK;
   int cap = (int)round_up(need, 32);
   dev_free(s, s->W);
   dev_free(s, s->AW);
-  dev_free(s, s->Z);
-  s->W = s->AW = s->Z = nullptr;
+  dev_free(s, s->ucoef);
+  s->W = s->AW = s->ucoef = nullptr;
   KRS_TRY(alloc_n(s, &s->W, (size_t)cap * s->ld));
   KRS_TRY(alloc_n(s, &s->AW, (size_t)cap * s->ld));
-  KRS_TRY(alloc_n(s, &s->Z, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &s->ucoef, ucoef_entries(cap)));
   s->cap_w = cap;
   return KRS_OK;
 }
@@ -443,7 +448,7 @@ krs_status krs_release(krs_seq_t s, int32_t what) {
     p = nullptr;
   };
   if (what & KRS_RELEASE_SCRATCH) {
-    drop(s->W); drop(s->AW); drop(s->Z);
+    drop(s->W); drop(s->AW); drop(s->Z); drop(s->ucoef);
     drop(s->alpha); drop(s->gamma); drop(s->rho); drop(s->gfull);
     s->cap_w = 0;
     s->cap_sc = 0;
@@ -536,11 +541,18 @@ krs_status krs_last_vectors(krs_seq_t s, int32_t which, double* out) {
   if (m == 0) return KRS_OK;
   if (!out) return fail(KRS_ERR_INVALID_ARG, "NULL output");
   KRS_CUDA(cudaSetDevice(s->device));
-  const double* src = which == 0 ? s->W : (which == 1 ? s->AW : s->Z);
+  const double* src = which == 0 ? s->W : (which == 1 ? s->AW : s->W);
   if (!src || !single_pass(s->last_prec))
     return fail(KRS_ERR_INVALID_ARG, "the last solve stored no FP64 vectors (mixed precision)");
   double* tmp = nullptr;
-  if (s->last_prec == KRS_DOUBLE_FLOAT) {  // double-float pairs -> doubles
+  double* ud = nullptr;
+  const bool df = s->last_prec == KRS_DOUBLE_FLOAT;
+  if (which == 2) {  // z_j = w_j + sum_i U[i, j] w_i from the stored coefficients
+    KRS_TRY(alloc_n(s, &tmp, (size_t)m * s->ld));
+    KRS_TRY(alloc_n(s, &ud, (size_t)m * m));
+    KRS_CUDA(launch_z_from_wu(s->n, s->ld, m, s->W, df, s->ucoef, s->last_reorth_full, ud, tmp, s->stream));
+    src = tmp;
+  } else if (df) {  // double-float pairs -> doubles
     KRS_TRY(alloc_n(s, &tmp, (size_t)m * s->ld));
     KRS_CUDA(launch_df2d(reinterpret_cast<const dfl*>(src), tmp, (int64_t)m * s->ld, s->stream));
     src = tmp;
@@ -550,6 +562,7 @@ krs_status krs_last_vectors(krs_seq_t s, int32_t which, double* out) {
                                     dv ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   dev_free(s, tmp);
+  dev_free(s, ud);
   KRS_CUDA(e);
   return KRS_OK;
 }
@@ -752,20 +765,6 @@ static krs_status run_loop(krs_seq* s, IterArgs& a, int exec, int* status, int* 
   return KRS_OK;
 }
 
-// One APCG solve (init + iterations) to ||r|| <= tol ||b_in||; *bb = ||b_in||^2.
-static krs_status run_apcg(krs_seq* s, IterArgs& a, const void* b_in, double tol, int exec, int* status, int* m,
-                           double* bb, float* t_iter_ms, int64_t* launches) {
-  double rr0 = 0.0;
-  *status = KRS_OK;
-  *m = 0;
-  KRS_TRY(run_init(s, a, b_in, tol, bb, &rr0, launches));
-  if (rr0 <= a.tol2) return KRS_OK;
-  // the stall test watches only the last stretch: below 1e-3 of the pass's first residual
-  // (earlier plateaus of the CG residual are normal)
-  a.stall_rr = 1e-6 * rr0;
-  return run_loop(s, a, exec, status, m, t_iter_ms, launches);
-}
-
 // SRKS, first half: H_m from the coefficients, the eigenvalues of H_m and H_{m-1}, the
 // selection; the selected count goes to pinned host memory (h_ctrl[16]), valid once the
 // stream has been synchronised.
@@ -784,9 +783,10 @@ static krs_status srks_begin(krs_seq* s, int m, int room, const krs_policy* p, i
 
 // SRKS, second half (after the stream was synchronised): eigenvectors of the selected
 // values and the Ritz vectors, written to C[:, nc .. nc + *cnt) (not yet counted in s->nc).
-// The z's: Z32 (FP32) when given, else Z -- FP64, or double-float pairs when z_df.
-static krs_status srks_finish(krs_seq* s, int m, int nc, const double* Z, const float* Z32, int* cnt,
-                              int64_t* launches, bool can_grow, bool z_df = false) {
+// The z's: Z32 (FP32) when given, else W and the coefficient rows U (z_j = w_j + sum_i
+// U[i, j] w_i) -- FP64 W, or double-float pairs when w_df.
+static krs_status srks_finish(krs_seq* s, int m, int nc, const float* Z32, int* cnt, int64_t* launches,
+                              bool can_grow, bool w_df = false) {
   *cnt = 0;
   const int k = s->h_ctrl[16];
   s->last_nsel = k;
@@ -795,23 +795,24 @@ static krs_status srks_finish(krs_seq* s, int m, int nc, const double* Z, const 
     if (!can_grow) return fail(KRS_ERR_INVALID_ARG, "internal: augmentation capacity not reserved");
     KRS_TRY(ensure_cap_c(s, nc + k));  // one APCG solve: nothing else uses C, AC, G^-1 now
   }
-  const size_t wneed = eigvecs_work_doubles(m, k) + (size_t)m * k * 2;
+  const size_t wneed = eigvecs_work_doubles(m, k) + (size_t)m * k * 3;
   dev_free(s, s->eigwork);
   s->eigwork = nullptr;
   KRS_TRY(alloc_n(s, &s->eigwork, wneed));
   double* Q = s->eigwork;
   double* Fm = s->eigwork + (size_t)m * k;
-  double* wk = s->eigwork + 2 * (size_t)m * k;
+  double* F2 = s->eigwork + 2 * (size_t)m * k;
+  double* wk = s->eigwork + 3 * (size_t)m * k;
   KRS_CUDA(launch_tridiag_eigvecs(m, s->delta, s->eta, k, s->tsel, Q, wk, s->stream));
-  if (Z32)
+  if (Z32) {
     KRS_CUDA(launch_ritz_vectors_f(s->n, s->ld, m, k, Z32, s->rho, Q, s->tsel, Fm, s->C + (size_t)nc * s->ld,
                                    s->stream));
-  else if (z_df)
-    KRS_CUDA(launch_ritz_vectors_df(s->n, s->ld, m, k, reinterpret_cast<const dfl*>(Z), s->rho, Q, s->tsel, Fm,
-                                    s->C + (size_t)nc * s->ld, s->stream));
-  else
-    KRS_CUDA(launch_ritz_vectors(s->n, s->ld, m, k, Z, s->rho, Q, s->tsel, Fm, s->C + (size_t)nc * s->ld, s->stream));
-  *launches += 3;
+    *launches += 3;
+  } else {
+    KRS_CUDA(launch_ritz_vectors_wu(s->n, s->ld, m, k, s->W, w_df, s->ucoef, s->last_reorth_full, s->rho, Q, s->tsel,
+                                    Fm, F2, s->C + (size_t)nc * s->ld, s->stream));
+    *launches += 4;
+  }
   *cnt = k;
   return KRS_OK;
 }
@@ -819,12 +820,12 @@ static krs_status srks_finish(krs_seq* s, int m, int nc, const double* Z, const 
 // SRKS extraction (Algorithm 3) from the coefficients of an m-iteration solve and its z's
 // (FP64 or FP32): selected Ritz vectors written to C[:, nc .. nc + *cnt) (not yet counted in
 // s->nc).  room: how many may be appended.
-static krs_status srks_extract(krs_seq* s, int m, int nc, int room, const krs_policy* p, const double* Z,
-                               const float* Z32, int* cnt, int64_t* launches, bool can_grow) {
+static krs_status srks_extract(krs_seq* s, int m, int nc, int room, const krs_policy* p, const float* Z32, int* cnt,
+                               int64_t* launches, bool can_grow) {
   *cnt = 0;
   KRS_TRY(srks_begin(s, m, room, p, launches));
   KRS_CUDA(cudaStreamSynchronize(s->stream));
-  return srks_finish(s, m, nc, Z, Z32, cnt, launches, can_grow);
+  return srks_finish(s, m, nc, Z32, cnt, launches, can_grow);
 }
 
 __global__ void k_recip(const double* __restrict__ src, double* __restrict__ dst, int count) {
@@ -1021,16 +1022,18 @@ static krs_status seq_setup(krs_seq* s, const krs_bsr* A, const double* b, const
   a.part = s->part; a.vpart = s->vpart; a.gpart = s->gpart; a.vld = s->vld; a.ctrl = s->ctrl; a.bar = s->bar;
   if (mixed) {
     a.vals = s->vals32; a.minv = s->minv32; a.C = s->C32; a.AC = s->AC32;
-    a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.x = s->x32; a.r = s->r32; a.u = s->u32;
+    a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.zld = s->ld; a.x = s->x32; a.r = s->r32; a.u = s->u32;
     a.stall_win = 32; a.rrh = s->rrh;
   } else if (proj) {
     a.vals = s->vals_use; a.minv = s->minv; a.C = s->C32; a.AC = s->AC32; a.Ci = s->C; a.ACi = s->AC;
-    a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.x = s->x; a.r = s->r; a.u = s->u; a.q = s->q64;
+    a.W = s->W32; a.AW = s->AW32; a.Z = s->Z32; a.zld = s->ld; a.x = s->x; a.r = s->r; a.u = s->u; a.q = s->q64;
     a.stall_win = 32; a.rrh = s->rrh;
   } else {
-    // KRS_DOUBLE_FLOAT: W, AW, Z hold double-float pairs (8 bytes, like the FP64 directions)
+    // KRS_DOUBLE_FLOAT: W, AW, z hold double-float pairs (8 bytes, like the FP64 directions);
+    // one z column, the coefficient rows U instead of the stored z_j
     a.vals = s->vals_use; a.minv = s->minv; a.C = s->C; a.AC = s->AC;
-    a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.x = s->x; a.r = s->r; a.u = s->u;
+    a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.zld = 0; a.ucoef = s->ucoef; a.x = s->x; a.r = s->r; a.u = s->u;
+    s->last_reorth_full = (p->reorth == KRS_REORTH_FULL);
     if (dfk) {
       a.q = s->q64;
       a.wv = s->wv;
@@ -1055,23 +1058,26 @@ krs_status krs::seq_grow_directions(krs_seq* s, int cap_iter, int keep, int prec
   const int need = cap_iter + 1;
   if (prec == KRS_MIXED_PROJ) return ensure_w32(s, need, keep);
   KRS_TRY(ensure_scalars(s, need, keep));
+  if (!s->Z) KRS_TRY(alloc_n(s, &s->Z, (size_t)s->ld));
   if (need <= s->cap_w) return KRS_OK;
   const int cap = (int)round_up(need, 32);
-  double *W = nullptr, *AW = nullptr, *Z = nullptr;
+  double *W = nullptr, *AW = nullptr, *U = nullptr;
   KRS_TRY(alloc_n(s, &W, (size_t)cap * s->ld));
   KRS_TRY(alloc_n(s, &AW, (size_t)cap * s->ld));
-  KRS_TRY(alloc_n(s, &Z, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &U, ucoef_entries(cap)));
   if (keep > s->cap_w) keep = s->cap_w;
   if (keep > 0) {
     const size_t vb = sizeof(double) * (size_t)keep * s->ld;
     KRS_CUDA(cudaMemcpyAsync(W, s->W, vb, cudaMemcpyDeviceToDevice, s->stream));
     KRS_CUDA(cudaMemcpyAsync(AW, s->AW, vb, cudaMemcpyDeviceToDevice, s->stream));
-    KRS_CUDA(cudaMemcpyAsync(Z, s->Z, vb, cudaMemcpyDeviceToDevice, s->stream));
+    if (keep > 1)  // coefficient rows 1 .. keep - 1
+      KRS_CUDA(cudaMemcpyAsync(U, s->ucoef, sizeof(double) * ucoef_entries(keep), cudaMemcpyDeviceToDevice,
+                               s->stream));
   }
   dev_free(s, s->W);
   dev_free(s, s->AW);
-  dev_free(s, s->Z);
-  s->W = W; s->AW = AW; s->Z = Z;
+  dev_free(s, s->ucoef);
+  s->W = W; s->AW = AW; s->ucoef = U;
   s->cap_w = cap;
   return KRS_OK;
 }
@@ -1094,8 +1100,8 @@ krs_status krs::seq_end_stage(krs_seq* s, SolveState* ss, int status, int m, dou
   }
   if (stage == 2) {
     if (!mixed && status == KRS_OK) {
-      // ---- FP64: the recycling step on this solve's W / Z
-      const bool dfk = p->precision == KRS_DOUBLE_FLOAT;  // W, AW, Z hold double-float pairs
+      // ---- FP64: the recycling step on this solve's W (and its coefficient rows U)
+      const bool dfk = p->precision == KRS_DOUBLE_FLOAT;  // W, AW hold double-float pairs
       if (p->recycle == KRS_RECYCLE_TRKS && m > 0) {
         const int add = m < ss->room ? m : ss->room;
         if (add > 0) {
@@ -1123,7 +1129,7 @@ krs_status krs::seq_end_stage(krs_seq* s, SolveState* ss, int status, int m, dou
         }
         ss->add = add;
       } else if (srks) {
-        KRS_TRY(srks_finish(s, m, nc, s->Z, nullptr, &ss->add, &launches, true, dfk));
+        KRS_TRY(srks_finish(s, m, nc, nullptr, &ss->add, &launches, true, dfk));
       }
     }
     // ---- result and true residual
@@ -1303,7 +1309,7 @@ krs_status krs::refine_pass_end(krs_seq* s, const krs_policy* p, double tol, Sol
       }
       ss->add = add;
     } else if (p->recycle == KRS_RECYCLE_SRKS && m_in >= 2) {
-      KRS_TRY(srks_extract(s, m_in, nc, room, p, nullptr, s->Z32, &ss->add, &launches, false));
+      KRS_TRY(srks_extract(s, m_in, nc, room, p, s->Z32, &ss->add, &launches, false));
     }
     ss->first = false;
   }
@@ -1435,13 +1441,7 @@ static krs_status check_tall(int64_t n, int32_t k, const double* V, int64_t ldv,
 
 // rows per CTA of the stand-alone tall-skinny launches
 static krs_status tall_partition(int64_t n, int* P, int64_t* rpc) {
-  int dev = 0, sms = 0;
-  KRS_CUDA(cudaGetDevice(&dev));
-  KRS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  int64_t r = round_up((n + sms - 1) / (sms > 0 ? sms : 1), 4);
-  if (r < 64) r = 64;
-  *rpc = r;
-  *P = (int)((n + r - 1) / r);
+  KRS_CUDA(gemv_rows_partition(n, P, rpc));
   return KRS_OK;
 }
 

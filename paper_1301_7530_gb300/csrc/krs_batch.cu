@@ -240,7 +240,7 @@ static IterArgs group_args(const Entry* e, int64_t vld) {
   krs_seq* s = e->s;
   IterArgs a = e->ss.a;
   if (single_pass(e->p.precision)) {  // FP64 / double-float storage may have grown since the set-up
-    a.W = s->W; a.AW = s->AW; a.Z = s->Z;
+    a.W = s->W; a.AW = s->AW; a.Z = s->Z; a.ucoef = s->ucoef;
     a.alpha = s->alpha; a.gamma = s->gamma; a.rho = s->rho; a.gfull = s->gfull;
   }
   a.tfull = s->tfull; a.sfull = s->sfull;

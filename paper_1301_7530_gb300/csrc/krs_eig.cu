@@ -543,11 +543,6 @@ static cudaError_t ritz_vectors_t(int64_t n, int64_t ld, int m, int k, const TZ*
   return cudaGetLastError();
 }
 
-cudaError_t launch_ritz_vectors(int64_t n, int64_t ld, int m, int k, const double* Z, const double* rho,
-                                const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st) {
-  return ritz_vectors_t<double>(n, ld, m, k, Z, rho, Q, tsel, F, Y, st);
-}
-
 // Ritz vectors from single-precision z_j (inner solve of the mixed-precision refinement);
 // accumulated and stored in FP64.
 cudaError_t launch_ritz_vectors_f(int64_t n, int64_t ld, int m, int k, const float* Z, const double* rho,
@@ -555,11 +550,61 @@ cudaError_t launch_ritz_vectors_f(int64_t n, int64_t ld, int m, int k, const flo
   return ritz_vectors_t<float>(n, ld, m, k, Z, rho, Q, tsel, F, Y, st);
 }
 
-// Ritz vectors from double-float z_j (the double-float precision); accumulated and stored
-// in FP64.
-cudaError_t launch_ritz_vectors_df(int64_t n, int64_t ld, int m, int k, const dfl* Z, const double* rho,
-                                   const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st) {
-  return ritz_vectors_t<dfl>(n, ld, m, k, Z, rho, Q, tsel, F, Y, st);
+// ------------------------------------------------------------------------------------
+// The z_j of a solve that kept only its reorthogonalisation coefficients: w_j = z_j -
+// sum_{i<j} g_i^(j) w_i, so z_j = w_j + sum_{i<j} U[i, j] w_i with U[i, j] = g_i^(j) (packed
+// rows: row j at j (j - 1) / 2).  Then sum_j z_j F[j, c] = sum_i w_i F2[i, c] with
+// F2[i, c] = F[i, c] + sum_{j>i} U[i, j] F[j, c]: the Ritz vectors are formed from W.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double u_entry(const double* __restrict__ U, int full, int i, int j) {
+  // U[i, j] for i < j (full == 0: classical CG, only the previous direction is used)
+  return (full || i == j - 1) ? U[(int64_t)j * (j - 1) / 2 + i] : 0.0;
 }
+
+__global__ void k_ritz_fold(int m, int k, const double* __restrict__ U, int full, const double* __restrict__ F,
+                            double* __restrict__ F2) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)m * k) return;
+  const int i = (int)(e % m), c = (int)(e / m);
+  double acc = F[(size_t)i * k + c];
+  const int jend = full ? m : min(m, i + 2);
+  for (int j = i + 1; j < jend; j++) acc += u_entry(U, full, i, j) * F[(size_t)j * k + c];
+  F2[(size_t)i * k + c] = acc;
+}
+
+// Ud[i, c] (row-major, m x m) = coefficient of w_i in z_c: 1 on the diagonal, U above it
+__global__ void k_dense_u(int m, const double* __restrict__ U, int full, double* __restrict__ Ud) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)m * m) return;
+  const int i = (int)(e / m), c = (int)(e % m);
+  Ud[e] = (i == c) ? 1.0 : (i < c ? u_entry(U, full, i, c) : 0.0);
+}
+
+cudaError_t launch_ritz_vectors_wu(int64_t n, int64_t ld, int m, int k, const void* W, bool w_df, const double* ucoef,
+                                   int full, const double* rho, const double* Q, const double* tsel, double* F,
+                                   double* F2, double* Y, cudaStream_t st) {
+  if (k <= 0 || m <= 0) return cudaSuccess;
+  k_ritz_coeffs<<<(m * k + 255) / 256, 256, 0, st>>>(m, k, Q, rho, tsel, F);
+  k_ritz_fold<<<(unsigned)(((int64_t)m * k + 255) / 256), 256, 0, st>>>(m, k, ucoef, full, F, F2);
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)((k + RITZ_COLS - 1) / RITZ_COLS));
+  if (w_df)
+    k_ritz_gemm<dfl><<<grid, 256, 0, st>>>(n, ld, m, k, static_cast<const dfl*>(W), F2, Y);
+  else
+    k_ritz_gemm<double><<<grid, 256, 0, st>>>(n, ld, m, k, static_cast<const double*>(W), F2, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_z_from_wu(int64_t n, int64_t ld, int m, const void* W, bool w_df, const double* ucoef, int full,
+                             double* Ud, double* Y, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  k_dense_u<<<(unsigned)(((int64_t)m * m + 255) / 256), 256, 0, st>>>(m, ucoef, full, Ud);
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)((m + RITZ_COLS - 1) / RITZ_COLS));
+  if (w_df)
+    k_ritz_gemm<dfl><<<grid, 256, 0, st>>>(n, ld, m, m, static_cast<const dfl*>(W), Ud, Y);
+  else
+    k_ritz_gemm<double><<<grid, 256, 0, st>>>(n, ld, m, m, static_cast<const double*>(W), Ud, Y);
+  return cudaGetLastError();
+}
+
 
 }  // namespace krs

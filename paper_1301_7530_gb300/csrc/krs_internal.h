@@ -43,6 +43,10 @@ struct IterArgs {
   const void* ACi;
   const double* Ginv;
   void *W, *AW, *Z, *x, *r, *u;
+  int64_t zld;      // stride of the z columns: ld (Z holds z_j for every j) or 0 (FP64 and
+                    // double-float: one z column reused every iteration; the coefficients
+                    // of each w_j go to ucoef instead, so that z_j = w_j + sum_i g_i w_i)
+  double* ucoef;    // zld == 0: packed rows of those coefficients (row j at j (j - 1) / 2)
   void* q;          // prec 2, 3: FP64 product A w_j
   void* wv;         // prec 3: FP64 search direction w_j (n + padding doubles)
   const void* vals_df;  // prec 3: matrix values as double-float pairs (9 nnzb)
@@ -123,6 +127,9 @@ cudaError_t launch_true_residual(int nbr, const int* rp, const int* ci, const do
                                  const double* x, const double* b, double* tmp, double* part,
                                  double* out, cudaStream_t st);
 // tall-skinny products over general rows (CTA b owns rows [b*rpc, (b+1)*rpc), rpc % 4 == 0)
+// partition of n rows for them: rpc = n / SMs rounded up to a multiple of 4 (at least 64),
+// P = ceil(n / rpc) row blocks (at most one per SM)
+cudaError_t gemv_rows_partition(int64_t n, int* P, int64_t* rpc);
 cudaError_t launch_gemv_t_rows(int64_t n, int k, const double* V, int64_t ldv, const double* u, double* t,
                                double* vpart, int P, int64_t rpc, cudaStream_t st);
 cudaError_t launch_gemv_n_rows(int64_t n, int k, const double* V, int64_t ldv, const double* s, const double* u,
@@ -157,14 +164,20 @@ size_t eigvecs_work_doubles(int m, int k);
 cudaError_t launch_srks_select(int m, const double* theta_m, const double* theta_m1, double eps,
                                double theta_frac, int reselect, int room, int* sel, int* count, double* tsel,
                                cudaStream_t st);
-// Y[:, c] = sum_j Z[:, j] (-1)^j Q[j, c] / sqrt(rho_j) / sqrt|theta_c|  for c < k
-cudaError_t launch_ritz_vectors(int64_t n, int64_t ld, int m, int k, const double* Z, const double* rho,
-                                const double* Q, const double* tsel, double* F, double* Y,
-                                cudaStream_t st);
+// Y[:, c] = sum_j z_j (-1)^j Q[j, c] / sqrt(rho_j) / sqrt|theta_c|  for c < k, with the z_j
+// given as W U: z_j = w_j + sum_{i<j} U[i, j] w_i, U packed by rows of j (row j at
+// j (j - 1) / 2, entries i < j; full == 0: only i = j - 1 is used).  W: FP64, or
+// double-float pairs when w_df.  F: m k doubles, F2: m k doubles (scratch).
+cudaError_t launch_ritz_vectors_wu(int64_t n, int64_t ld, int m, int k, const void* W, bool w_df, const double* ucoef,
+                                   int full, const double* rho, const double* Q, const double* tsel, double* F,
+                                   double* F2, double* Y, cudaStream_t st);
+// Z = W U (the z_j of a solve that did not store them), n x m into Y (leading dimension ld);
+// Ud: m m doubles of scratch
+cudaError_t launch_z_from_wu(int64_t n, int64_t ld, int m, const void* W, bool w_df, const double* ucoef, int full,
+                             double* Ud, double* Y, cudaStream_t st);
+// Y[:, c] = sum_j Z[:, j] (-1)^j Q[j, c] / sqrt(rho_j) / sqrt|theta_c|  for c < k, from the
+// FP32 z_j of an inner solve of the mixed-precision refinement
 cudaError_t launch_ritz_vectors_f(int64_t n, int64_t ld, int m, int k, const float* Z, const double* rho,
                                   const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st);
-struct dfl;
-cudaError_t launch_ritz_vectors_df(int64_t n, int64_t ld, int m, int k, const dfl* Z, const double* rho,
-                                   const double* Q, const double* tsel, double* F, double* Y, cudaStream_t st);
 
 }  // namespace krs

@@ -413,6 +413,18 @@ __global__ void __launch_bounds__(TPB, 1) k_gemv_n_rows2(const double* V, int64_
 
 size_t gemv_rows_smem(int k) { return sizeof(double) * (size_t)(ROW_CHUNK + 4 * TPB + ((k + 3) & ~3)); }
 
+cudaError_t gemv_rows_partition(int64_t n, int* P, int64_t* rpc) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  int64_t r = ((n + sms - 1) / (sms > 0 ? sms : 1) + 3) / 4 * 4;
+  if (r < 64) r = 64;
+  *rpc = r;
+  *P = (int)((n + r - 1) / r);
+  return cudaSuccess;
+}
+
 cudaError_t launch_gemv_t_rows(int64_t n, int k, const double* V, int64_t ldv, const double* u, double* t,
                                double* vpart, int P, int64_t rpc, cudaStream_t st) {
   if (k <= 0) return cudaSuccess;

@@ -73,9 +73,13 @@ struct krs_seq {
   double* C0 = nullptr;
 
   // Krylov storage and vectors
-  int cap_w = 0;   // columns of the FP64 W, AW, Z
+  int cap_w = 0;   // columns of the FP64 W, AW (and rows of ucoef)
   int cap_sc = 0;  // iterations the scalar arrays alpha, gamma, rho, gfull hold
-  double *W = nullptr, *AW = nullptr, *Z = nullptr;
+  // FP64 / double-float solves keep no z_j: Z is one column, reused every iteration, and
+  // ucoef the packed reorthogonalisation coefficients (row j at j (j - 1) / 2: the g_i of
+  // w_j = z_j - sum_{i<j} g_i w_i), from which z_j = w_j + sum_i g_i w_i when needed
+  double *W = nullptr, *AW = nullptr, *Z = nullptr, *ucoef = nullptr;
+  int last_reorth_full = 1;  // reorthogonalisation of the last solve (which U entries exist)
   double *x = nullptr, *r = nullptr, *u = nullptr, *b = nullptr, *tmp = nullptr;
 
   // scalars, partials, control
@@ -179,12 +183,13 @@ struct SolveState {
 // one read of ||b||^2 and ||r_0||^2.  On return ss->need_iter says whether iterations run.
 krs_status seq_begin(krs_seq* s, const krs_bsr* A, const double* b, double tol, const krs_policy* p, int cap_iter,
                      SolveState* ss);
-// Grow the direction storage of precision `prec` (FP64 W, AW, Z, or FP32 W32, AW32, Z32
-// for KRS_MIXED_PROJ) to at least cap_iter + 1 columns keeping the first `keep` columns and
-// the scalars of the first `keep` iterations (between launches).
+// Grow the direction storage of precision `prec` (FP64 W, AW and the coefficient rows, or
+// FP32 W32, AW32, Z32 for KRS_MIXED_PROJ) to at least cap_iter + 1 columns keeping the
+// first `keep` columns, coefficient rows and the scalars of the first `keep` iterations
+// (between launches).
 krs_status seq_grow_directions(krs_seq* s, int cap_iter, int keep, int prec);
 // columns of the direction storage a solve of precision `prec` uses (KRS_DOUBLE_FLOAT keeps
-// its double-float directions in the 8-byte W, AW, Z of the FP64 path)
+// its double-float directions in the 8-byte W, AW of the FP64 path)
 inline int dir_cap(const krs_seq* s, int prec) {
   return (prec == KRS_FP64 || prec == KRS_DOUBLE_FLOAT) ? s->cap_w : s->cap_w32;
 }

@@ -63,6 +63,101 @@ def test_srks_damage_sequence(gpu_lib, eps, frac):
     assert total_sel > 0
 
 
+@pytest.mark.parametrize("tol,frac", [(1e-12, 0.1), (1e-8, 0.0)])
+def test_srks14_selects_in_lockstep(gpu_lib, tol, frac):
+    """SRKS with the paper's chosen stagnation threshold eps = 1e-14 ("srks14", Section 5.1)
+    on a 6^3 damage sequence where it selects vectors (a tight tolerance lets Ritz values
+    converge to the rounding level; without the theta filter the converged upper end is
+    kept too): lock-step with the oracle, and the GPU's selection is Eq. 16 applied to its
+    own Ritz values."""
+    N = 6
+    mask, b, gen = P.elasticity_sequence_damage(N, 4, 11, 2000)
+    seq = B.Sequence(3 * N * (N + 1) ** 2)
+    pol = B.make_policy("srks", "block_jacobi3", ritz_eps=1e-14, theta_frac=frac, max_aug=60)
+    total_sel = 0
+    for k, Ak in gen:
+        x, st, xo, so, ora, C = solve_pair(seq, Ak, b, tol, pol, version=k + 1)
+        check_pair(Ak, b, tol, pol, x, st, xo, so, C)
+        tm, tm1, sel = seq.last_ritz()
+        if st["m"] >= 2:
+            assert list(O.srks_select(tm, tm1, 1e-14, frac, 60 - st["n_c"])) == list(sel)
+        total_sel += st["n_selected"]
+    assert total_sel > 0
+
+
+@pytest.mark.parametrize("recycle", ["trks", "srks"])
+def test_cap_restart_returns_to_initial_space(gpu_lib, recycle):
+    """KRS_CAP_RESTART (Algorithm 3, last step): once the space reaches max_aug after the
+    recycling step, C goes back to C^(0).  Both sides start from the same seeded C^(0) of 4
+    columns; lock-step (the oracle gets the GPU's C and the same C^(0) before each solve);
+    the augmentation sizes after each solve agree and every restart leaves exactly C^(0)."""
+    N = 5
+    n = 3 * N * (N + 1) ** 2
+    rng = np.random.default_rng(55)
+    C0 = rng.standard_normal((n, 4))
+    if recycle == "trks":
+        A, bs = P.elasticity_sequence_fixed(N, 6, 500)
+        systems = [(A, bb, 1) for bb in bs]
+        pol = B.make_policy("trks", "jacobi", max_aug=160, cap_mode="restart")
+    else:
+        mask, b, gen = P.elasticity_sequence_damage(N, 6, 12, 2200)
+        systems = [(Ak, b, k + 1) for k, Ak in gen]
+        pol = B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, theta_frac=0.0, max_aug=24, cap_mode="restart")
+    seq = B.Sequence(n)
+    seq.import_space(C0, as_c0=True)
+    opol = O.make_policy(recycle, "jacobi" if recycle == "trks" else "block_jacobi3", "full", "restart",
+                         pol.max_aug, pol.max_iter, pol.ritz_eps, pol.theta_frac)
+    restarts = 0
+    for A, bb, ver in systems:
+        C = seq.export_space()
+        ora = O.Sequence(n)
+        ora.set_C(C0, as_c0=True)
+        ora.set_C(C)
+        x, st = seq.solve(A, bb, 1e-8, pol, version=ver)
+        xo, so = ora.solve(A, bb, 1e-8, opol)
+        check_pair(A, bb, 1e-8, pol, x, st, xo, so, C)
+        appended = st["n_c"] + st["n_selected"]
+        if appended >= pol.max_aug:
+            restarts += 1
+            assert st["n_c_after"] == 4 and np.array_equal(seq.export_space(), C0)
+        else:
+            assert st["n_c_after"] == appended
+        if st["n_selected"] == so["n_selected"]:
+            assert so["n_c_after"] == st["n_c_after"]
+    assert restarts >= 1
+
+
+@pytest.mark.parametrize("precision,reorth", [("fp64", "full"), ("fp64", "none"), ("double_float", "full")])
+def test_z_from_stored_coefficients(gpu_lib, precision, reorth):
+    """The FP64 and double-float solves keep one z column and the reorthogonalisation
+    coefficients instead of every z_j: krs_last_vectors(Z) rebuilds z_j = w_j + sum_i g_i w_i.
+    Its first 30 columns (where the GPU and oracle trajectories still agree to rounding)
+    match the oracle's stored z_j, and the direction storage is two n-vectors per iteration
+    (W, AW), not three."""
+    N = 6
+    mask, b, gen = P.elasticity_sequence_damage(N, 1, 11, 2000)
+    k, A = next(gen)
+    seq = B.Sequence(A.n)
+    pol = B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, theta_frac=0.1, max_aug=60, reorth=reorth,
+                        precision=precision, max_iter=400)
+    x, st, xo, so, ora, C = solve_pair(seq, A, b, 1e-8, pol, version=1)
+    check_pair(A, b, 1e-8, pol, x, st, xo, so, C)
+    Zg = seq.last_vectors("Z")
+    Zo = ora.Z
+    q = min(30, st["m"], so["m"])
+    tol = 1e-9 if precision == "fp64" else 1e-7
+    for j in range(q):
+        assert rel(Zg[:, j], Zo[:, j]) <= tol, (j, rel(Zg[:, j], Zo[:, j]))
+    W = seq.last_vectors("W")
+    assert np.array_equal(Zg[:, 0], W[:, 0])  # z_0 = w_0
+    ld = (A.n + 31) // 32 * 32
+    cap = (400 + 1 + 31) // 32 * 32
+    held = seq.device_bytes()
+    seq.release(B.RELEASE_SCRATCH)
+    scratch = held - seq.device_bytes()
+    assert 2 * 8 * ld * cap <= scratch < 3 * 8 * ld * cap, (scratch, 8 * ld * cap)
+
+
 def test_exec_modes_bitwise_equal(gpu_lib):
     """The persistent kernel and the per-phase kernels compute the same bits."""
     N = 5
@@ -250,28 +345,59 @@ def test_invalid_arguments(gpu_lib):
 # full size of the benchmark workload (32^3 damage sequence, 104,544 dofs)
 # ---------------------------------------------------------------------------------------
 
-def test_full_size_first_solve_and_sequence_properties(gpu_lib):
-    """First system of the 32^3 damage sequence against the oracle (C = 0); then three
-    more GPU solves checked by properties that hold at any size: true residual, the
-    augmentation cap, C^T r = 0 for the returned x."""
+def test_full_size_first_solves_lockstep_and_sequence_properties(gpu_lib):
+    """First three systems of the 32^3 damage sequence in lock-step with the oracle (the
+    oracle gets the GPU's space before each solve): iterations, solution, Ritz values, the
+    SRKS selection (Eq. 16 on the GPU's values, and the oracle's own selection when the two
+    value sets agree) and the Ritz vectors of well-separated selected values; then a fourth
+    GPU solve checked by properties that hold at any size: true residual, the augmentation
+    cap, C^T r = 0 for the returned x."""
     N = 32
+    eps, frac, cap = 1e-6, 0.1, 200
     mask, b, gen = P.elasticity_sequence_damage(N, 20, 2000, 2000)
     seq = B.Sequence(3 * N * (N + 1) ** 2)
-    pol = B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, theta_frac=0.1, max_aug=200)
-    k, A0 = next(gen)
-    x, st, xo, so, ora, C = solve_pair(seq, A0, b, 1e-8, pol, version=1)
-    check_pair(A0, b, 1e-8, pol, x, st, xo, so, C)
+    pol = B.make_policy("srks", "block_jacobi3", ritz_eps=eps, theta_frac=frac, max_aug=cap)
     for k, Ak in gen:
         if k > 3:
             break
+        if k <= 2:
+            x, st, xo, so, ora, C = solve_pair(seq, Ak, b, 1e-8, pol, version=k + 1)
+            check_pair(Ak, b, 1e-8, pol, x, st, xo, so, C)
+            tm, tm1, sel = seq.last_ritz()
+            otm, otm1, osel, oY = ora.ritz()
+            assert list(O.srks_select(tm, tm1, eps, frac, cap - st["n_c"])) == list(sel)
+            if st["m"] == so["m"]:
+                # A Ritz value is known to about its own stagnation gap |theta_m - theta_m-1|
+                # (Eq. 16).  Values whose gap is below 1e-12 |theta| (on the oracle's values)
+                # agree to 1e-9 theta_max; values below 1e-6 |theta| (the selection threshold
+                # of this run) to 1e-5 |theta|; the others are set by the last iterations'
+                # coefficients, which sit at the residual's rounding floor (FP64: ~m 2^-53 / tol
+                # relative), so all of them to 1e-3 theta_max
+                d = np.abs(tm - otm)
+                for eps_t, bound in ((1e-12, np.full_like(otm, 1e-9 * otm[0])),
+                                     (1e-6, 1e-5 * np.abs(otm) + 1e-11 * otm[0])):
+                    tier = np.zeros(len(otm), bool)
+                    tier[O.srks_select(otm, otm1, eps_t, 0.0)] = True
+                    bad = tier & (d > bound)
+                    assert not bad.any(), (k, eps_t, np.flatnonzero(bad), d[bad], otm[bad])
+                assert d.max() <= 1e-3 * otm[0], (k, d.max(), int(np.argmax(d)))
+                assert np.all(d[sel] <= 1e-5 * np.abs(otm[sel]) + 1e-11 * otm[0]), (k, d[sel])
+                if list(sel) == list(osel):
+                    Yg = seq.export_space()[:, st["n_c"]:]
+                    for c in range(len(sel)):
+                        th = tm[sel[c]]
+                        gap = np.min(np.abs(np.delete(tm, sel[c]) - th))
+                        if gap > 1e-3 * tm[0]:
+                            a, bb = Yg[:, c], oY[:, c]
+                            assert min(rel(a, bb), rel(a, -bb)) <= 1e-6
+            continue
         Cb = seq.export_space()
         x, st = seq.solve(Ak, b, 1e-8, pol, version=k + 1)
         assert st["true_rel_res"] <= 1e-7
         r = b - Ak.to_scipy() @ x
         if Cb.shape[1]:
-            AC = Ak.to_scipy() @ Cb
             assert np.abs(Cb.T @ r).max() <= 1e-9 * np.linalg.norm(Cb, axis=0).max() * np.linalg.norm(b) * np.sqrt(Cb.shape[1])
-        assert seq.nc <= 200
+        assert seq.nc <= cap
 
 
 def test_misaligned_device_matrix_is_copied(gpu_lib):

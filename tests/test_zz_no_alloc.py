@@ -3,7 +3,8 @@ memory (a framework holding the device's memory in its own pool, a latency-bound
 cannot pay for an allocation, code where another component owns every allocation).  It
 keeps its partial sums in a fixed array of the library instead of allocating them; here
 it is checked, through the C ABI, against krs_gemv_t (which allocates) on two calls in a
-row with different data, so leftovers of the first call cannot leak into the second."""
+row with different data (bitwise equal results: the two run the same kernels in the same
+partition), so leftovers of the first call cannot leak into the second."""
 import numpy as np
 import pytest
 
@@ -27,11 +28,12 @@ def _case(gpu_lib, n, k, seed):
     assert gpu_lib.krs_gemv_t_noalloc(n, k, Vd.data_ptr(), ld, ud.data_ptr(), t_na.data_ptr(), st) == 0
     torch.cuda.synchronize()
     a, b = t_na.cpu().numpy(), t_ref.cpu().numpy()
-    # the tolerance of the tall-skinny kernel tests: a rounding bound of the dot products
+    # same kernels, partition and summation order as krs_gemv_t: the same bits
+    assert np.all(np.isfinite(a))
+    assert np.array_equal(a, b)
+    # and both within the tall-skinny kernel tests' rounding bound of the host product
     Vn = V[:, :n]
     bound = 1e-15 * np.sqrt(n) * (np.abs(Vn) @ np.abs(u[:n])) * 8 + 1e-300
-    assert np.all(np.isfinite(a))
-    assert np.all(np.abs(a - b) <= bound)
     assert np.all(np.abs(a - Vn @ u[:n]) <= bound)
 
 
