@@ -50,7 +50,7 @@ CSRC = os.path.join(ROOT, "paper_1301_7530_gb300", "csrc")
 
 # the two sequences: (cube, systems, cap, stored-direction budget, step unit)
 SEQUENCES = {
-    "inclusions": {"N": 64, "systems": 15, "max_aug": 300, "max_iter": 10000, "step": "system"},
+    "inclusions": {"N": 64, "systems": 15, "max_aug": 300, "max_iter": 7000, "step": "system"},
     "damage": {"N": 32, "systems": 20, "max_aug": 200, "max_iter": 2000, "step": "sequence"},
 }
 
@@ -114,7 +114,7 @@ def parse_args(argv=None):
                          "(a bounded launch for ncu; no timing line)")
     ap.add_argument("--capture-nc", type=int, default=0,
                     help="profiling: the captured solve starts from a seeded space of this many columns")
-    ap.add_argument("--workload", choices=["sequence", "batched", "served"], default="sequence",
+    ap.add_argument("--workload", choices=["sequence", "batched", "served", "conditioning"], default="sequence",
                     help="sequence: one sequence (default); batched: many sequences of uneven size "
                          "through the batched engine; served: Poisson requests of many clients")
     ap.add_argument("--nseq", type=int, default=None, help="batched/served: sequences (256 / 64)")
@@ -125,6 +125,10 @@ def parse_args(argv=None):
     ap.add_argument("--group-ctas", type=int, default=0, help="batched/served: CTAs per solve (0: autotune)")
     ap.add_argument("--quantum", type=int, default=None, help="batched/served: iterations per launch")
     ap.add_argument("--group-scale", type=int, default=0, help="batched/served: group size scale in percent (0: autotune)")
+    ap.add_argument("--lanczos-steps", type=int, default=30, help="conditioning: Lanczos steps on A^-1")
+    ap.add_argument("--check-sample", type=int, default=8,
+                    help="batched/served: error of the results of this many (smallest) sequences, first and "
+                         "last system, against the FP64 oracle's solution")
     ap.add_argument("--baseline-seqs", type=int, default=None,
                     help="batched/served: sequences in the per-solve reference sample (default all)")
     args = ap.parse_args(argv)
@@ -538,11 +542,16 @@ def run_krs(args, rank, world, local):
         torch.cuda.synchronize()
         e_ms = all_max((time.perf_counter() - t0) * 1e3, world)
         e_solves = all_sum(len(ks), world)
+        dev_same = float(np.sum(lat[:len(ks)])) / 1e3  # the same systems in the timed region
         e2e = {"value": e_solves / (e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d / args.e2e_steps), "d2h_bytes_per_step": int(8 * n * len(ks) / args.e2e_steps),
                "steps": args.e2e_steps, "systems": ks,
+               "device_resident_same_systems": {"value": len(ks) / dev_same, "unit": UNIT,
+                                                "what": "the same systems in the timed region (inputs on the device)"},
                "what": "krs_solve with pinned host A, b and x (A uploaded by the first solve, b and x every "
-                       "solve), from the recycled space the timed region started from; wall clock"}
+                       "solve), from the recycled space the timed region started from; wall clock.  These are the "
+                       "first timed steps' systems, not the timed region's mix (which includes a first system of "
+                       "the sequence): compare with device_resident_same_systems"}
 
     extra = {}
     if not args.no_variant and args.precision == "fp64" and args.problem == "inclusions" and args.variant_systems > 0:
@@ -864,7 +873,7 @@ def run_reference(args, rank, world):
                                     f"operator product, the eigensolver at orders {CAL_EIG}), extrapolated to "
                                     "the whole solve by the cost model with the sequence's recorded "
                                     "(m, n_c, selected); value and ms_per_step are modelled oracle time, the "
-                                    f"samples took {np.mean(wall_ms) / 1e3:.1f} s of wall clock per timed step"),
+                                    f"samples took {np.mean(wall_ms):.0f} ms of wall clock per timed step"),
                          "calibration": base},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -907,6 +916,37 @@ def _reset(clients):
         c.m_prev = 0
 
 
+def result_errors(args, kind, Ns, systems, clients, reqs, sample):
+    """Error of a seeded sample of results against the FP64 oracle: for the `sample`
+    smallest sequences, their first and last system, ||x - x_o|| / ||x_o|| where x_o is the
+    oracle's solution of the same A^(k) x = b to relative residual 1e-12 (block-Jacobi, no
+    augmentation), beside the result's own FP64 residual.  A result at residual tol is within
+    about kappa(A) tol of the exact solution."""
+    import oracle as O
+    seed = 7000 if kind == "batched" else 9000
+    dks = P.damage_factors(systems)
+    pick = sorted(range(len(clients)), key=lambda i: (clients[i].n, i))[:sample]
+    by = {(r.cid, r.k): r for r in reqs}
+    rows = []
+    for cid in pick:
+        A_out, vin, b = P.damage_parts(int(Ns[cid]), seed + cid, seed + 10000 + cid)
+        for k in sorted({0, systems - 1}):
+            r = by.get((cid, k))
+            if r is None or r.x is None or r.status != 0:
+                continue
+            A = P.damage_matrix(A_out, vin, dks[k])
+            xo, so = O.Sequence(A.n).solve(A, b, 1e-12, O.make_policy("none", "block_jacobi3", max_iter=20000))
+            x = r.x.cpu().numpy()
+            rows.append({"seq": cid, "N": int(Ns[cid]), "system": k, "m": r.m,
+                         "rel_err": float(np.linalg.norm(x - xo) / np.linalg.norm(xo)),
+                         "true_rel_res": float(r.true_rel_res), "oracle_m": so["m"]})
+    errs = [row["rel_err"] for row in rows]
+    return {"what": "||x - x_oracle|| / ||x_oracle||, x_oracle the FP64 oracle's solution of the same system "
+                    "to relative residual 1e-12; results of the smallest sequences, first and last system",
+            "count": len(rows), "max": max(errs) if errs else None,
+            "median": float(np.median(errs)) if errs else None, "results": rows}
+
+
 def run_many(args, kind):
     import torch
     from paper_1301_7530_gb300 import binding as B
@@ -944,6 +984,7 @@ def run_many(args, kind):
     gbs = 0.5 * byts / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
     value = len(reqs) / wall
     srv.close()
+    errors = result_errors(args, kind, Ns, systems, clients, reqs, args.check_sample) if args.check_sample > 0 else None
     # per-solve launches (krs_solve, one full-device persistent launch per solve) on the
     # same sequences: the reference point the batched / served form must beat
     nb = args.baseline_seqs or len(clients)
@@ -998,6 +1039,7 @@ def run_many(args, kind):
                       "what": "half the FP64 algorithmic bytes of all inner iterations (FP32 storage) / "
                               "batched kernel time", "kernel_ms": kern_ms, "share_of_wall": kern_ms / (wall * 1e3)}),
         "hbm_peak": {"value": hbm_peak, "kind": hbm_kind},
+        "result_errors": errors,
         "server": {"steps": srv.steps, "evictions": srv.evictions, "reimports": srv.reimports,
                    "peak_held_gb": srv.peak_held / 2 ** 30},
         "e2e": None,
@@ -1010,8 +1052,64 @@ def run_many(args, kind):
         c.close()
 
 
+def run_conditioning(args):
+    """Condition numbers of the inclusion cube's matrix (the quantity that decides whether
+    FP32 inner solves can drive an FP64 refinement): kappa(M^-1 A) for the block-Jacobi
+    preconditioner from the extreme Ritz values of one tight preconditioned solve (random
+    right-hand side), lambda_max(A) by scipy's Lanczos on the host, lambda_min(A) as
+    1 / lambda_max(A^-1) by a Lanczos process on A^-1 whose products are library solves
+    (block-Jacobi, relative residual 1e-12, TRKS reuse of the earlier solves' directions)."""
+    import scipy.sparse.linalg as sla
+    import torch
+    from paper_1301_7530_gb300 import binding as B
+    torch.cuda.set_device(0)
+    N = args.N
+    A = P.elasticity_inclusions(N, 3000)
+    n = A.n
+    rng = np.random.default_rng(99)
+    t0 = time.perf_counter()
+    seq = B.Sequence(n)
+    v = rng.standard_normal(n)
+    _, st = seq.solve(A, v, 1e-12, B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, max_aug=1, max_iter=20000),
+                      version=1)
+    th, _, _ = seq.last_ritz()
+    kappa_m = float(th[0] / th[-1])
+    seq.close()
+    lmax = float(sla.eigsh(A.to_scipy(), k=1, which="LA", tol=1e-8, return_eigenvectors=False)[0])
+    seq = B.Sequence(n)
+    pol = B.make_policy("trks", "block_jacobi3", max_aug=6000, max_iter=20000)
+    L = args.lanczos_steps
+    Q = np.zeros((n, L + 1))
+    q = rng.standard_normal(n)
+    Q[:, 0] = q / np.linalg.norm(q)
+    al, be = [], []
+    for i in range(L):
+        w, st2 = seq.solve(A, Q[:, i], 1e-12, pol, version=1)
+        a_i = float(Q[:, i] @ w)
+        w = w - Q[:, :i + 1] @ (Q[:, :i + 1].T @ w)  # full reorthogonalisation (host, small)
+        w = w - Q[:, :i + 1] @ (Q[:, :i + 1].T @ w)
+        b_i = float(np.linalg.norm(w))
+        al.append(a_i)
+        be.append(b_i)
+        Q[:, i + 1] = w / b_i
+    T = np.diag(al) + np.diag(be[:-1], 1) + np.diag(be[:-1], -1)
+    mu = np.linalg.eigvalsh(T)
+    lmin = float(1.0 / mu[-1])
+    seq.close()
+    out = {"workload": "conditioning", "problem": f"{N}^3 Q1 elasticity with stiff spherical inclusions (5 %, contrast 1e3)",
+           "n": n, "kappa_A": lmax / lmin, "lambda_max_A": lmax, "lambda_min_A": lmin,
+           "lambda_min_A_change_last_step": float(abs(1.0 / mu[-1] - 1.0 / np.linalg.eigvalsh(T[:-1, :-1])[-1]) / lmin),
+           "kappa_MinvA_block_jacobi": kappa_m, "preconditioned_solve_iterations": st["m"],
+           "u32": 2.0 ** -24, "kappa_A_u32": lmax / lmin * 2.0 ** -24, "kappa_MinvA_u32": kappa_m * 2.0 ** -24,
+           "lanczos_steps": L, "seconds": time.perf_counter() - t0}
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
+    if args.workload == "conditioning":
+        run_conditioning(args)
+        return
     if args.impl == "krs" and args.workload != "sequence":
         run_many(args, args.workload)
         return
