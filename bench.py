@@ -125,7 +125,7 @@ def parse_args(argv=None):
     ap.add_argument("--group-ctas", type=int, default=0, help="batched/served: CTAs per solve (0: autotune)")
     ap.add_argument("--quantum", type=int, default=None, help="batched/served: iterations per launch")
     ap.add_argument("--group-scale", type=int, default=0, help="batched/served: group size scale in percent (0: autotune)")
-    ap.add_argument("--lanczos-steps", type=int, default=30, help="conditioning: Lanczos steps on A^-1")
+    ap.add_argument("--lanczos-steps", type=int, default=12, help="conditioning: Lanczos steps on A^-1")
     ap.add_argument("--check-sample", type=int, default=8,
                     help="batched/served: error of the results of this many (smallest) sequences, first and "
                          "last system, against the FP64 oracle's solution")
@@ -236,22 +236,27 @@ def make_config(args, A, world):
         "l2": l2}
 
 
-def alg_counts(N, precond_bytes_per_dof, m, nc):
-    """Algorithmic FP64 flops and bytes of one launch of the iteration kernel (m iterations,
-    augmentation size nc): every array counted once per phase that needs it -- the operator
+def alg_counts(N, precond_bytes_per_dof, m, nc, passes=1, m2=None):
+    """Algorithmic FP64 flops and bytes of the iteration kernel over m iterations with
+    augmentation size nc: every array counted once per phase that needs it -- the operator
     product 76 bytes and 18 flops per block, the updates and the preconditioner O(n), the two
-    projection products 8 n nc bytes each, the reorthogonalisation 16 n (j + 1) bytes; the last
-    iteration stops after the convergence test."""
+    projection products 8 n nc bytes each, the reorthogonalisation 16 n (j + 1) bytes at
+    iteration j of its pass; the last iteration of a pass stops after the convergence test.
+    One pass by default; for the refinement precisions, `passes` passes whose iteration
+    counts sum to m and whose squares sum to m2."""
     s = P.sizes(N)
     n, nb, nodes = s["n"], s["nb"], s["free_nodes"]
     if m <= 0:
         return 0.0, 0.0
+    if m2 is None:
+        m2 = float(m) * m
     # P1-P2 (every iteration): SpMV, (w,q), (r,w), x/r update, (r,r), M^-1 r, (AC)^T u
     f12 = 18 * nb + 4 * n + 6 * n + 6 * n + 2 * n * nc
     b12 = 76 * nb + 4 * (nodes + 1) + precond_bytes_per_dof * n + 8 * n * nc + 48 * n
-    # P4-P7 (all but the last): s = G^-1 t, z = u - C s, (r,z), g = (AW)^T z, w = z - W g
-    k = m - 1
-    sj = k * (k + 1) / 2.0  # sum over j < m - 1 of (j + 1)
+    # P4-P7 (all but the last of each pass): s = G^-1 t, z = u - C s, (r,z), g = (AW)^T z,
+    # w = z - W g; sum over the passes of sum_{j < m_p - 1} (j + 1) = (m2 - m) / 2
+    k = m - passes
+    sj = (m2 - m) / 2.0
     f47 = k * (2 * nc * nc + 2 * n * nc + 2 * n) + 4 * n * sj
     b47 = k * (8 * n * nc + 16 * n) + 16 * n * sj
     return m * f12 + f47, m * b12 + b47
@@ -384,8 +389,13 @@ def roofline_of(args, stats, t_step_ms, precision, hbm_peak, hbm_kind):
     """Roofline object of the persistent iteration kernel over the solves `stats`: its
     algorithmic FP64 flops and bytes (alg_counts) / its event-timed duration."""
     flops = byts = t_iter = 0.0
+    refine = precision in ("mixed_ir", "mixed_proj")
     for st in stats:
-        f, bb = alg_counts(args.N, 24, st["m"], st["n_c"])
+        if refine:  # the passes of the refinement, FP32 directions: half the value bytes
+            f, bb = alg_counts(args.N, 24, st["m"], st["n_c"], max(1, st["outer_iters"]), st["inner_m2"])
+            bb *= 0.5
+        else:
+            f, bb = alg_counts(args.N, 24, st["m"], st["n_c"])
         flops += f
         byts += bb
         t_iter += st["t_iter_ms"]
@@ -407,6 +417,10 @@ def roofline_of(args, stats, t_step_ms, precision, hbm_peak, hbm_kind):
         # the streams run on the FP32 pipes: memory is the bound
         r = {"kernel": "k_apcg_persistent<PrecE>", "bound": "hbm", **hbm, **traffic,
              "fp64_view": dict(fp64, what="FP64-equivalent algorithmic flops / time (part of them on FP32 pipes)")}
+    elif refine:
+        # FP32 passes: memory is the bound; bytes counted per pass (stats: m, passes, sum m_p^2)
+        r = {"kernel": "k_apcg_persistent<PrecF>", "bound": "hbm", **hbm, **traffic,
+             "what": "half the FP64 algorithmic bytes of the inner passes (FP32 values) / iteration kernel time"}
     else:
         r = {"kernel": "k_apcg_persistent", "bound": "alu", **fp64,
              "flops": "FP64 algorithmic flops of the iterations" if precision == "fp64" else
@@ -902,12 +916,13 @@ def _many(args, kind):
     return Ns, systems, clients
 
 
+def _counts_of(r, Ns):
+    """Algorithmic (flops, bytes) of one served request: one pass, or the refinement's passes."""
+    return alg_counts(int(Ns[r.cid]), 24, r.m, r.n_c, r.passes, r.m2 if r.m2 > 0 else None)
+
+
 def _flops_of(reqs, Ns):
-    f = 0.0
-    for r in reqs:
-        if r.m > 0:
-            f += alg_counts(int(Ns[r.cid]), 24, r.m, r.n_c)[0]
-    return f
+    return sum(_counts_of(r, Ns)[0] for r in reqs if r.m > 0)
 
 
 def _reset(clients):
@@ -979,7 +994,7 @@ def run_many(args, kind):
     kern_ms = bst["total_kernel_ms"] - bst0["total_kernel_ms"]
     flops = _flops_of(reqs, Ns)
     ach = flops / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
-    byts = sum(alg_counts(int(Ns[r.cid]), 24, r.m, r.n_c)[1] for r in reqs if r.m > 0)
+    byts = sum(_counts_of(r, Ns)[1] for r in reqs if r.m > 0)
     hbm_peak, hbm_kind = measured_peaks()
     gbs = 0.5 * byts / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
     value = len(reqs) / wall
@@ -1058,7 +1073,7 @@ def run_conditioning(args):
     preconditioner from the extreme Ritz values of one tight preconditioned solve (random
     right-hand side), lambda_max(A) by scipy's Lanczos on the host, lambda_min(A) as
     1 / lambda_max(A^-1) by a Lanczos process on A^-1 whose products are library solves
-    (block-Jacobi, relative residual 1e-12, TRKS reuse of the earlier solves' directions)."""
+    (block-Jacobi, relative residual 1e-9, TRKS reuse of the earlier solves' directions)."""
     import scipy.sparse.linalg as sla
     import torch
     from paper_1301_7530_gb300 import binding as B
@@ -1070,21 +1085,24 @@ def run_conditioning(args):
     t0 = time.perf_counter()
     seq = B.Sequence(n)
     v = rng.standard_normal(n)
-    _, st = seq.solve(A, v, 1e-12, B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, max_aug=1, max_iter=20000),
+    # tolerance 1e-9: CG's recursive residual cannot go much below u kappa(A) (~1e-10 at 48^3)
+    _, st = seq.solve(A, v, 1e-9, B.make_policy("srks", "block_jacobi3", ritz_eps=1e-6, max_aug=1, max_iter=12000),
                       version=1)
     th, _, _ = seq.last_ritz()
     kappa_m = float(th[0] / th[-1])
     seq.close()
     lmax = float(sla.eigsh(A.to_scipy(), k=1, which="LA", tol=1e-8, return_eigenvectors=False)[0])
     seq = B.Sequence(n)
-    pol = B.make_policy("trks", "block_jacobi3", max_aug=6000, max_iter=20000)
+    # A^-1 products: solves to 1e-9 recycling (TRKS) at most 1,500 earlier directions, so
+    # that each later solve starts deflated and the work stays bounded
+    pol = B.make_policy("trks", "block_jacobi3", max_aug=1500, max_iter=12000)
     L = args.lanczos_steps
     Q = np.zeros((n, L + 1))
     q = rng.standard_normal(n)
     Q[:, 0] = q / np.linalg.norm(q)
     al, be = [], []
     for i in range(L):
-        w, st2 = seq.solve(A, Q[:, i], 1e-12, pol, version=1)
+        w, st2 = seq.solve(A, Q[:, i], 1e-9, pol, version=1)
         a_i = float(Q[:, i] @ w)
         w = w - Q[:, :i + 1] @ (Q[:, :i + 1].T @ w)  # full reorthogonalisation (host, small)
         w = w - Q[:, :i + 1] @ (Q[:, :i + 1].T @ w)

@@ -184,6 +184,9 @@ typedef struct {
   int64_t kernel_launches;/* kernels this library launched for the solve */
   int32_t outer_iters;    /* refinement steps (KRS_MIXED_IR; 0 for KRS_FP64) */
   int32_t inner_m_first;  /* iterations of the first inner solve (KRS_MIXED_IR) */
+  double inner_m2;        /* sum over the solve's passes of their iteration counts squared (one
+                             pass: m^2); with m and outer_iters it gives the reorthogonalisation
+                             work, which grows with the square of a pass's length */
 } krs_solve_stats;
 
 /* --- sequence life cycle -------------------------------------------------------------- */

@@ -56,7 +56,8 @@ class krs_solve_stats(ct.Structure):
                 ("n_selected", ct.c_int32), ("n_c_after", ct.c_int32), ("rel_res", ct.c_double),
                 ("true_rel_res", ct.c_double), ("t_setup_ms", ct.c_double), ("t_iter_ms", ct.c_double),
                 ("t_recycle_ms", ct.c_double), ("t_total_ms", ct.c_double),
-                ("kernel_launches", ct.c_int64), ("outer_iters", ct.c_int32), ("inner_m_first", ct.c_int32)]
+                ("kernel_launches", ct.c_int64), ("outer_iters", ct.c_int32), ("inner_m_first", ct.c_int32),
+                ("inner_m2", ct.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

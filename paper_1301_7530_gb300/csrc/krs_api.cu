@@ -470,6 +470,8 @@ krs_status krs_release(krs_seq_t s, int32_t what) {
     drop(s->C32); drop(s->AC32); drop(s->dinv);
     s->cap_c32 = 0;
     drop(s->x32); drop(s->r32); drop(s->u32); drop(s->b32); drop(s->minv32);
+    drop(s->Pout); drop(s->APout); drop(s->oscal); drop(s->ovpart);
+    s->cap_out = 0;
     s->minv32_kind = -1;
     drop(s->vals32);
     s->vals32_cap = 0;
@@ -833,6 +835,17 @@ __global__ void k_recip(const double* __restrict__ src, double* __restrict__ dst
   if (i < count) dst[i] = 1.0 / src[i];
 }
 
+// t[i] /= gamma[i], i < k (the A-orthogonalisation coefficients of a new outer direction)
+__global__ void k_div_elem(double* __restrict__ t, const double* __restrict__ gamma, int k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) t[i] /= gamma[i];
+}
+
+// out = num / den (one thread): the flexible CG step length
+__global__ void k_ratio(const double* __restrict__ num, const double* __restrict__ den, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = num[0] / den[0];
+}
+
 __global__ void k_f2d_cols(const float* __restrict__ src, double* __restrict__ dst, int64_t count) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = (double)src[i];
@@ -1155,6 +1168,7 @@ krs_status krs::seq_end_stage(krs_seq* s, SolveState* ss, int status, int m, dou
   st.n_c = nc;
   st.outer_iters = ss->outer;
   st.inner_m_first = ss->m_first;
+  st.inner_m2 = single_pass(p->precision) ? (double)st.m * (double)st.m : ss->m2;
   st.true_rel_res = bb > 0.0 ? sqrt(s->h_scal[2] / bb) : 0.0;
   st.rel_res = mixed ? st.true_rel_res : (bb > 0.0 ? sqrt(s->h_scal[3] / bb) : 0.0);
   if (status != KRS_OK) {
@@ -1218,6 +1232,62 @@ krs_status krs::refine_setup(krs_seq* s, const krs_bsr* A, const double* b, cons
   return seq_setup(s, A, b, p, p->max_iter, ss);
 }
 
+// storage of the flexible CG over the refinement passes (KRS_MIXED_IR): cap outer directions
+static krs_status ensure_outer(krs_seq* s, int cap) {
+  if (cap <= s->cap_out) return KRS_OK;
+  dev_free(s, s->Pout);
+  dev_free(s, s->APout);
+  dev_free(s, s->oscal);
+  dev_free(s, s->ovpart);
+  s->Pout = s->APout = s->oscal = s->ovpart = nullptr;
+  s->cap_out = 0;
+  KRS_TRY(alloc_n(s, &s->Pout, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &s->APout, (size_t)cap * s->ld));
+  KRS_TRY(alloc_n(s, &s->oscal, (size_t)2 * cap + 8));
+  KRS_TRY(alloc_n(s, &s->ovpart, (size_t)256 * (cap + 2)));
+  // rows n .. ld - 1 of the directions stay zero (the tall-skinny kernels read them)
+  KRS_CUDA(cudaMemsetAsync(s->Pout, 0, sizeof(double) * (size_t)cap * s->ld, s->stream));
+  KRS_CUDA(cudaMemsetAsync(s->APout, 0, sizeof(double) * (size_t)cap * s->ld, s->stream));
+  s->cap_out = cap;
+  return KRS_OK;
+}
+
+// One outer step of the flexible CG over the refinement passes (KRS_MIXED_IR), all FP64:
+// p_k = d - sum_{i<k} ((A p_i, d) / (p_i, A p_i)) p_i with d the pass's FP32 correction,
+// gamma_k = (p_k, A p_k), alpha = (p_k, r) / gamma_k, x += alpha p_k.  Iterative refinement
+// takes x += d; choosing the step and removing the components along the earlier
+// corrections makes every step minimise the A-norm of the error over all corrections so
+// far, so an inexact FP32 correction cannot make the refinement stall or diverge.
+static krs_status fcg_step(krs_seq* s, int k, double* x, double* r, int64_t* launches) {
+  const int64_t ld = s->ld, n = s->n;
+  double* pk = s->Pout + (size_t)k * ld;
+  double* apk = s->APout + (size_t)k * ld;
+  double* gam = s->oscal;
+  double* t = s->oscal + s->cap_out;
+  double* sc = s->oscal + 2 * s->cap_out;  // [0] (p, r), [1] alpha, [2] scratch
+  k_f2d_cols<<<1216, 256, 0, s->stream>>>(s->x32, pk, n);
+  KRS_CUDA(cudaGetLastError());
+  int P = 0;
+  int64_t rpc = 0;
+  KRS_CUDA(gemv_rows_partition(n, &P, &rpc));
+  if (k > 0) {
+    KRS_CUDA(launch_gemv_t_rows(n, k, s->APout, ld, pk, t, s->ovpart, P, rpc, s->stream));
+    k_div_elem<<<(k + 255) / 256, 256, 0, s->stream>>>(t, gam, k);
+    KRS_CUDA(cudaGetLastError());
+    KRS_CUDA(launch_gemv_n_rows(n, k, s->Pout, ld, t, pk, pk, P, rpc, s->stream));
+    *launches += 4;
+  }
+  KRS_CUDA(launch_spmv(s->nbr, s->rp_use, s->ci_use, s->vals_use, pk, apk, s->stream));
+  KRS_CUDA(launch_gemv_t_rows(n, 1, apk, ld, pk, gam + k, s->ovpart, P, rpc, s->stream));
+  KRS_CUDA(launch_gemv_t_rows(n, 1, r, ld, pk, sc, s->ovpart, P, rpc, s->stream));
+  k_ratio<<<1, 32, 0, s->stream>>>(sc, gam + k, sc + 1);
+  KRS_CUDA(cudaGetLastError());
+  // x += alpha p_k (the r update of this kernel is overwritten by the FP64 residual after)
+  KRS_CUDA(launch_axpy2_dot(n, sc + 1, pk, apk, x, r, sc + 2, s->ovpart, s->stream));
+  *launches += 10;
+  return KRS_OK;
+}
+
 krs_status krs::refine_start(krs_seq* s, const krs_policy* p, double tol, SolveState* ss) {
   const bool pp = p->precision == KRS_MIXED_PROJ;
   double* xtot = pp ? s->xacc : s->x;
@@ -1230,6 +1300,9 @@ krs_status krs::refine_start(krs_seq* s, const krs_policy* p, double tol, SolveS
   ss->outer = 0;
   ss->m_first = 0;
   ss->add = 0;
+  ss->stall = 0;
+  ss->m2 = 0.0;
+  if (!pp) KRS_TRY(ensure_outer(s, p->max_outer > 0 ? p->max_outer : 30));
   KRS_CUDA(cudaMemsetAsync(xtot, 0, sizeof(double) * s->ld, s->stream));
   // r = b - A*0 = b (FP64), r32 = (float) b, rr = ||b||^2
   KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, xtot, s->b, s->tmp, rout, r32out,
@@ -1239,6 +1312,7 @@ krs_status krs::refine_start(krs_seq* s, const krs_policy* p, double tol, SolveS
   KRS_CUDA(cudaStreamSynchronize(s->stream));
   ss->bb = s->h_scal[4];
   ss->rr = ss->bb;
+  ss->rr_best = ss->bb;
   if (!isfinite(ss->bb)) return fail(KRS_ERR_INVALID_ARG, "right-hand side is not finite");
   return KRS_OK;
 }
@@ -1267,6 +1341,10 @@ krs_status krs::refine_pass_begin(krs_seq* s, const krs_policy* p, double tol, S
   if (tin < inner_tol) tin = inner_tol;
   if (tin > 0.5) tin = 0.5;
   a.max_iter = p->max_iter - ss->m;
+  // KRS_MIXED_IR: a later pass (same operator, new right-hand side) gets at most twice the
+  // first pass's iterations; one that stagnates above its target ends there and the flexible
+  // CG uses its partial correction
+  if (!pp && !ss->first && a.max_iter > 2 * ss->m_first + 100) a.max_iter = 2 * ss->m_first + 100;
   double bb_in = 0.0, rr0 = 0.0;
   KRS_TRY(run_init(s, a, rhs_in, tin, &bb_in, &rr0, &ss->launches));
   // the stall test watches only the last stretch: below 1e-3 of the pass's first residual
@@ -1296,6 +1374,7 @@ krs_status krs::refine_pass_end(krs_seq* s, const krs_policy* p, double tol, Sol
     return KRS_OK;
   }
   ss->m += m_in;
+  ss->m2 += (double)m_in * (double)m_in;
   s->last_m = m_in;
   if (ss->first) {
     ss->m_first = m_in;
@@ -1313,9 +1392,13 @@ krs_status krs::refine_pass_end(krs_seq* s, const krs_policy* p, double tol, Sol
     }
     ss->first = false;
   }
-  // The next inner solve (same operator) is augmented by this one's directions: they
-  // are A-conjugate to C and to each other, so their coarse block is diag(1/(w, Aw)).
-  if (m_in > 0) {
+  // KRS_MIXED_PROJ: the next inner solve (same operator) is augmented by this one's
+  // directions: they are A-conjugate to C and to each other, so their coarse block is
+  // diag(1/(w, Aw)).  KRS_MIXED_IR does not: FP32 directions are A-conjugate only to about
+  // u_32 kappa, and with hundreds of them the assumed-diagonal coarse block stops being a
+  // projector (later passes stagnated on the stiff-inclusion cubes); its passes start from
+  // the recycled space alone and the FP64 flexible CG combines their corrections.
+  if (m_in > 0 && pp) {
     const int nct = a.nc;
     KRS_CUDA(cudaMemcpyAsync(s->C32 + (size_t)nct * s->ld, s->W32, sizeof(float) * (size_t)m_in * s->ld,
                              cudaMemcpyDeviceToDevice, s->stream));
@@ -1331,9 +1414,10 @@ krs_status krs::refine_pass_end(krs_seq* s, const krs_policy* p, double tol, Sol
       a.ACi = nullptr;
     }
   }
-  // x += d (FP64), r = b - A x (FP64), next pass's right-hand side (r32 = (float) r)
+  // KRS_MIXED_PROJ: x += d; KRS_MIXED_IR: the flexible CG step over the FP32 corrections
+  // (FP64); then r = b - A x (FP64) and the next pass's right-hand side (r32 = (float) r)
   if (pp) KRS_CUDA(launch_add_d(xtot, s->x, s->n, s->stream));
-  else KRS_CUDA(launch_add_f2d(xtot, s->x32, s->n, s->stream));
+  else KRS_TRY(fcg_step(s, ss->outer, xtot, rout, &launches));
   KRS_CUDA(launch_resid_update(s->nbr, s->rp_use, s->ci_use, s->vals_use, xtot, s->b, s->tmp, rout, r32out,
                                s->part, s->scal + 4, s->stream));
   launches += 4;
@@ -1342,11 +1426,27 @@ krs_status krs::refine_pass_end(krs_seq* s, const krs_policy* p, double tol, Sol
   const double rr_new = s->h_scal[4];
   ss->outer++;
   const double bb = ss->bb;
-  if (!(rr_new < 0.81 * ss->rr) && !(rr_new <= tol * tol * bb)) {  // stagnation: refinement no longer pays
-    ss->rr = rr_new;
-    ss->status = KRS_ERR_NO_CONVERGENCE;
-    *finished = true;
-    return KRS_OK;
+  if (!(rr_new <= tol * tol * bb)) {
+    bool stalled;
+    if (pp) {
+      stalled = !(rr_new < 0.81 * ss->rr);  // one step without a 10 % fall
+    } else {
+      // the flexible CG minimises the A-norm of the error, not ||r||: three steps in a row
+      // without a new 10 % low of ||r|| end it
+      if (rr_new < 0.81 * ss->rr_best) {
+        ss->rr_best = rr_new;
+        ss->stall = 0;
+      } else {
+        ss->stall++;
+      }
+      stalled = ss->stall >= 3 || !isfinite(rr_new);
+    }
+    if (stalled) {  // stagnation: refinement no longer pays
+      ss->rr = rr_new;
+      ss->status = KRS_ERR_NO_CONVERGENCE;
+      *finished = true;
+      return KRS_OK;
+    }
   }
   ss->rr = rr_new;
   return KRS_OK;

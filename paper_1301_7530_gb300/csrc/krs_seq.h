@@ -114,6 +114,11 @@ struct krs_seq {
   krs::dfl* vals_df = nullptr;  // double-float precision: the matrix values as double-float pairs
   int64_t vals_df_cap = 0;
   bool vals_df_valid = false;
+  // KRS_MIXED_IR: the FP64 outer directions of the flexible CG over the refinement passes
+  // (p_k from pass k's FP32 correction, A-orthogonalised against the earlier p_i), their
+  // products A p_k, scalars (gamma_k, coefficients, step) and partial sums
+  double *Pout = nullptr, *APout = nullptr, *oscal = nullptr, *ovpart = nullptr;
+  int cap_out = 0;
   double* xacc = nullptr;  //   sum of the passes' corrections
   double* rres = nullptr;  //   FP64 residual b - A xacc (the next pass's right-hand side)
   double* rrh = nullptr;   //   ||r_j||^2 history of the stall test
@@ -173,9 +178,12 @@ struct SolveState {
   float t_iter = 0.f;
   // refinement state (KRS_MIXED_IR, KRS_MIXED_PROJ) between passes
   double rr = 0.0;     // ||b - A x||^2 of the current iterate
+  double rr_best = 0.0;  // KRS_MIXED_IR: smallest ||b - A x||^2 so far, and outer steps since
+  int stall = 0;         //   it last fell by 10 % (three such steps end the refinement)
   bool first = true;   // the next pass is the first one
   int status = 0;      // outcome so far
   int m = 0;           // inner iterations so far
+  double m2 = 0.0;     // sum of the passes' iteration counts squared
 };
 
 // Stage 1: matrix, preconditioner, right-hand side, storage (direction capacity `cap_iter`

@@ -41,6 +41,8 @@ class Request:
     true_rel_res: float = float("nan")
     launches: int = 0     # kernels the library launched for this solve outside the batched kernel
     x: object = None
+    passes: int = 1       # refinement passes (FP32 inner solves) and the sum of their lengths squared
+    m2: float = 0.0
     vals: object = None  # the request's matrix values (device), alive while in flight
 
 
@@ -98,9 +100,10 @@ class Server:
 
     # ---- memory accounting
     def estimate(self, c: Client) -> int:
-        """Bytes the next solve of c adds: direction storage (W, AW, Z at 1.25x the previous
-        iteration count, as the engine sizes it), growth of the space, the request's matrix
-        values, and the space itself if it has to be re-imported."""
+        """Bytes the next solve of c adds: direction storage (FP64 / double-float: W, AW and the
+        coefficient rows at 1.25x the previous iteration count, as the engine sizes it; FP32
+        refinement: W32, AW32, Z32 for max_iter inner iterations), growth of the space, the
+        request's matrix values, and the space itself if it has to be re-imported."""
         ld = _round_up(c.n, 32)
         m = c.m_prev if c.m_prev > 0 else 12.0 * c.n ** (1.0 / 3.0)
         cap = _round_up(int(1.25 * m) + 48, 32)
@@ -109,7 +112,7 @@ class Server:
             wi = _round_up(self.policy.max_iter + 1, 32)
             est = ld * (4 * 3 * wi + 4 * 2 * (room + wi) + 8 * 2 * room + 40) + (72 + 36) * c.nnzb
         else:
-            est = 8 * ld * (3 * cap + 2 * room) + 72 * c.nnzb
+            est = 8 * ld * (2 * cap + 1 + 2 * room) + 4 * cap * cap + 72 * c.nnzb
         if c.evicted is not None:
             est += 16 * ld * c.evicted.shape[1]
         return est
@@ -174,6 +177,8 @@ class Server:
         r.n_c = st["n_c"]
         r.true_rel_res = st["true_rel_res"]
         r.launches = st["kernel_launches"]
+        r.passes = max(1, st["outer_iters"])
+        r.m2 = st["inner_m2"]
         r.vals = None
         c.m_prev = st["m"] if st["m"] > 0 else c.m_prev
         c.last_done = now

@@ -105,3 +105,25 @@ def test_mixed_no_convergence_keeps_space(gpu_lib):
                       version=1, raise_on_error=False)
     assert st["status"] == B.ERR_NO_CONVERGENCE
     assert np.array_equal(seq.export_space(), C0)
+
+
+@pytest.mark.parametrize("N", [16, 32])
+def test_mixed_refinement_on_stiff_inclusion_cube(gpu_lib, N):
+    """Stiff inclusions (contrast 1e3) make kappa(A) u_32 large enough that plain iterative
+    refinement (x += d) stalls; the flexible CG over the FP32 corrections converges to the FP64
+    tolerance, and its result is as close to the tight FP64 solution as an FP64 solve at the
+    same tolerance is (error of each against an FP64 solve to 1e-11, whose own parity with the
+    oracle the FP64 tests establish)."""
+    A = P.elasticity_inclusions(N, 3000)
+    b = P.traction_rhs(N, P.random_traction(N, 3100))
+    ref, st_ref = B.Sequence(A.n).solve(A, b, 1e-11, B.make_policy("none", "block_jacobi3", max_iter=12000),
+                                        version=1)
+    x64, st64 = B.Sequence(A.n).solve(A, b, 1e-8, B.make_policy("none", "block_jacobi3", max_iter=12000), version=1)
+    seq = B.Sequence(A.n)
+    x, st = seq.solve(A, b, 1e-8, B.make_policy("none", "block_jacobi3", precision="mixed_ir", max_iter=16000),
+                      version=1, raise_on_error=False)
+    assert st["status"] == 0, st
+    assert st["true_rel_res"] <= 1e-8
+    e_mixed = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+    e_fp64 = np.linalg.norm(x64 - ref) / np.linalg.norm(ref)
+    assert e_mixed <= 10 * e_fp64 + 1e-12, (e_mixed, e_fp64, st["outer_iters"], st["m"])
