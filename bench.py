@@ -101,6 +101,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-variant", action="store_true",
                     help="skip the extra objects (double-float sample, 32^3 damage sequence)")
+    ap.add_argument("--mixed-systems", type=int, default=3,
+                    help="systems of the mixed-precision sample (the sequence's first ones, from an empty space)")
+    ap.add_argument("--mixed-inner-tol", type=float, default=0.0,
+                    help="mixed-precision sample: relative residual of the first FP32 pass (0: the library default)")
     ap.add_argument("--variant-systems", type=int, default=3,
                     help="systems of the double-float sample of the headline sequence")
     ap.add_argument("--precision", choices=["fp64", "double_float", "mixed_ir", "mixed_proj"], default="fp64",
@@ -114,7 +118,8 @@ def parse_args(argv=None):
                          "(a bounded launch for ncu; no timing line)")
     ap.add_argument("--capture-nc", type=int, default=0,
                     help="profiling: the captured solve starts from a seeded space of this many columns")
-    ap.add_argument("--workload", choices=["sequence", "batched", "served", "conditioning"], default="sequence",
+    ap.add_argument("--workload", choices=["sequence", "batched", "served", "conditioning", "fp64peak"],
+                    default="sequence",
                     help="sequence: one sequence (default); batched: many sequences of uneven size "
                          "through the batched engine; served: Poisson requests of many clients")
     ap.add_argument("--nseq", type=int, default=None, help="batched/served: sequences (256 / 64)")
@@ -450,7 +455,7 @@ def run_krs(args, rank, world, local):
     def policy(precision):
         return B.make_policy("srks", "block_jacobi3", ritz_eps=args.ritz_eps, theta_frac=args.theta_frac,
                              max_aug=args.max_aug, max_iter=args.max_iter, exec=args.exec, precision=precision,
-                             reselect=args.reselect)
+                             reselect=args.reselect, inner_tol=args.inner_tol)
 
     pol = policy(args.precision)
     seq = B.Sequence(n, device=local, stream=stream)
@@ -477,6 +482,9 @@ def run_krs(args, rank, world, local):
 
     counter = {"step": 0}
 
+    keep_x = {}  # FP64 results of the sequence's first systems (the mixed-precision sample's reference)
+    mixed_ks = list(range(min(args.mixed_systems, args.systems))) if args.problem == "inclusions" else []
+
     def one_step(record=None, lat=None, sq=None, pl=None):
         sq = sq or seq
         pl = pl or pol
@@ -491,6 +499,8 @@ def run_krs(args, rank, world, local):
                 raise RuntimeError(f"solve {k} failed: {st}")
             if record is not None:
                 record.append(dict(st, system=k))
+                if k in mixed_ks and k not in keep_x:
+                    keep_x[k] = x_d.clone()  # 6.5 MB device copy, microseconds
         counter["step"] += 1
 
     gpu_index = gpu_index_of(local)
@@ -567,9 +577,8 @@ def run_krs(args, rank, world, local):
                        "first timed steps' systems, not the timed region's mix (which includes a first system of "
                        "the sequence): compare with device_resident_same_systems"}
 
-    extra = {}
-    if not args.no_variant and args.precision == "fp64" and args.problem == "inclusions" and args.variant_systems > 0:
-        # the first timed systems again in the double-float precision, from the same space
+    def df_sample():
+        """The first timed systems again in the double-float precision, from the same space."""
         seq.import_space(C_warm)
         pdf = policy("double_float")
         vstats, vlat = [], []
@@ -594,7 +603,7 @@ def run_krs(args, rank, world, local):
         vms = v0.elapsed_time(v1)
         vroof, _ = roofline_of(args, vstats, vms, "double_float", hbm_peak, hbm_kind)
         fp64_same = lat[:len(ks)]
-        extra["double_float"] = {
+        return {
             "precision": "double_float", "dtype": dtype_of("double_float"), "systems": ks,
             "value": len(ks) / (vms / 1e3), "unit": UNIT, "ms_per_system": vms / len(ks),
             "fp64_ms_per_system_same_systems": float(np.sum(fp64_same) / len(fp64_same)),
@@ -604,9 +613,66 @@ def run_krs(args, rank, world, local):
             "what": "a bounded sample: the first timed systems again from the same recycled space, precision "
                     "KRS_DOUBLE_FLOAT (FP64 recurrences, projection and coarse solve; double-float directions "
                     "and matrix values)"}
+
+    def mixed_sample():
+        """The sequence's first systems in KRS_MIXED_IR (FP32 passes, FP64 flexible-CG outer
+        step) from an empty space, against FP64's time and result on the same systems."""
+        seq.release(B.RELEASE_SCRATCH)  # the FP64 direction storage makes room for the FP32 passes'
+        seq.import_space(np.zeros((n, 0)))
+        pmx = B.make_policy("srks", "block_jacobi3", ritz_eps=args.ritz_eps, theta_frac=args.theta_frac,
+                            max_aug=args.max_aug, max_iter=16000, exec=args.exec, precision="mixed_ir",
+                            inner_tol=args.mixed_inner_tol)
+        mstats, mdiff = [], []
+        torch.cuda.synchronize()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        for k in mixed_ks:
+            _, st = seq.solve(mat_of(k), b_ds[k], TOL, pmx, x=x_d, version=ver_of(k) + 3000)
+            if st["status"] != 0:
+                raise RuntimeError(f"mixed-precision solve {k} failed: {st}")
+            mstats.append(dict(st, system=k))
+            mdiff.append(float(torch.linalg.norm(x_d - keep_x[k]) / torch.linalg.norm(keep_x[k])))
+        m1.record(stream)
+        torch.cuda.synchronize()
+        mms = m0.elapsed_time(m1)
+        fp64_ms = [lt for st, lt in zip(stats, lat) if st["system"] in mixed_ks][:len(mixed_ks)]
+        mroof, _ = roofline_of(args, mstats, mms, "mixed_ir", hbm_peak, hbm_kind)
+        return {
+            "precision": "mixed_ir", "dtype": dtype_of("mixed_ir"), "systems": mixed_ks,
+            "inner_tol": args.mixed_inner_tol or 0.1,
+            "value": len(mixed_ks) / (mms / 1e3), "unit": UNIT, "ms_per_system": mms / len(mixed_ks),
+            "fp64_ms_per_system_same_systems": float(np.mean(fp64_ms)) if fp64_ms else None,
+            "inner_iterations": [st["m"] for st in mstats], "passes": [st["outer_iters"] for st in mstats],
+            "inner_m_first": [st["inner_m_first"] for st in mstats], "n_c": [st["n_c"] for st in mstats],
+            "n_selected": [st["n_selected"] for st in mstats],
+            "fp64_m": [st["m"] for st in stats if st["system"] in mixed_ks][:len(mixed_ks)],
+            "true_rel_res_max": float(max(st["true_rel_res"] for st in mstats)),
+            "rel_diff_from_fp64_result": mdiff,
+            "roofline": mroof, "gpu_launches": int(sum(st["kernel_launches"] for st in mstats)),
+            "what": "the sequence's first systems from an empty space in KRS_MIXED_IR: FP32 operator, "
+                    "preconditioner, projection and reorthogonalisation in the passes, FP64 flexible-CG outer "
+                    "step, residual, coarse Cholesky and Ritz eigensolve; rel_diff_from_fp64_result is each "
+                    "result's relative difference from the FP64 solve of the same system in the timed region "
+                    "(both at relative residual 1e-8)"}
+
+    # extra objects: never allowed to take the headline line down
+    extra = {}
+    variants = not args.no_variant and args.precision == "fp64" and args.problem == "inclusions"
+    for name, fn, on in (("double_float", df_sample, variants and args.variant_systems > 0),
+                         ("mixed_ir", mixed_sample, variants and bool(mixed_ks) and all(k in keep_x for k in mixed_ks))):
+        if on:
+            try:
+                extra[name] = fn()
+            except Exception as exc:  # noqa: BLE001
+                extra[name] = {"error": f"{type(exc).__name__}: {exc}"}
     seq.close()
-    if not args.no_variant and args.problem == "inclusions" and args.precision == "fp64":
-        extra["cube32_damage_sequence"] = damage_line(args, rank, world, local, hbm_peak, hbm_kind)
+    keep_x.clear()
+    if variants:
+        try:
+            extra["cube32_damage_sequence"] = damage_line(args, rank, world, local, hbm_peak, hbm_kind)
+        except Exception as exc:  # noqa: BLE001
+            extra["cube32_damage_sequence"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -1123,10 +1189,42 @@ def run_conditioning(args):
     print(json.dumps(out))
 
 
+def run_fp64peak(args):
+    """Measured FP64 rate of this GPU, the co-roof of the FP64 path: torch's FP64 matrix
+    product (cuBLAS, 8192^3, 2 N^3 flops), best of 5 after a warm-up, CUDA events, clocks
+    sampled meanwhile; beside the derived 152 SMs x 2 FMA/clk x 2 x 2.07 GHz."""
+    import torch
+    torch.cuda.set_device(0)
+    N = 8192
+    a = torch.randn(N, N, dtype=torch.float64, device="cuda")
+    b = torch.randn(N, N, dtype=torch.float64, device="cuda")
+    c = a @ b
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_index_of(0), enabled=not args.no_clocks)
+    times = []
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c = a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    del c
+    tf = 2.0 * N ** 3 / (min(times) / 1e3) / 1e12
+    print(json.dumps({"workload": "fp64peak", "what": "torch.matmul float64 8192^3 (cuBLAS), best of 5",
+                      "tflops": tf, "ms": times, "derived_peak_tflops": FP64_PEAK_TFLOPS,
+                      "frac_of_derived": tf / FP64_PEAK_TFLOPS, "clocks": clk}))
+
+
 def main():
     args = parse_args()
     if args.workload == "conditioning":
         run_conditioning(args)
+        return
+    if args.workload == "fp64peak":
+        run_fp64peak(args)
         return
     if args.impl == "krs" and args.workload != "sequence":
         run_many(args, args.workload)

@@ -91,14 +91,12 @@ typedef struct {
  *               grid-wide barriers; KRS_EXEC_KERNELS launches one kernel per phase.  Both
  *               compute the same arithmetic in the same order.
  *   precision:  KRS_FP64: the whole solve in FP64.  KRS_MIXED_IR: iterative refinement --
- *               an FP64 outer loop (x += d, r = b - A x in FP64) around inner APCG solves
- *               A d = r whose SpMV, preconditioner, projections and reorthogonalisation run
- *               in FP32 (FP32 copies of A, M^-1, C, AC; FP32 directions), while C^T A C, its
- *               Cholesky factor and inverse, the Lanczos tridiagonal and its eigensolve stay
- *               FP64.  Within one system every inner solve after the first is augmented
- *               by the directions of the earlier ones (same operator: they are A-conjugate
- *               to C and to each other, so their coarse block is diagonal), so refinement
- *               does not restart the Krylov space.  The recycling step (TRKS / SRKS) between
+ *               an FP64 outer loop (a flexible CG over the inner corrections, r = b - A x in
+ *               FP64) around inner APCG solves A d = r whose SpMV, preconditioner,
+ *               projections and reorthogonalisation run in FP32 (FP32 copies of A, M^-1,
+ *               C, AC; FP32 directions), while C^T A C, its Cholesky factor and inverse,
+ *               the Lanczos tridiagonal and its eigensolve stay FP64.  Every inner solve
+ *               starts from the recycled space C; the recycling step (TRKS / SRKS) between
  *               systems uses the first inner solve.  An FP32 breakdown ((w, Aw) <= 0 or
  *               (r, z) <= 0) after some progress ends that inner solve only.
  *               KRS_MIXED_PROJ: one APCG solve whose operator product, preconditioner and
@@ -120,14 +118,15 @@ typedef struct {
  *               1e-30 .. 1e38 in magnitude keep the full significand); TRKS appends them to C
  *               in FP64, SRKS forms Ritz vectors from them in FP64, krs_last_vectors returns
  *               them as doubles.
- *   inner_tol:  KRS_MIXED_IR: relative residual each inner solve aims for (<= 0: 0.1);
- *               the last one is loosened to what the outer tolerance still needs.  An inner
- *               solve also ends when its residual stalls (fell less than 4x over 32
- *               iterations once below 1e-3 of its first value).  Smaller values make the
- *               first pass long enough for SRKS to find converged Ritz values (1e-5 ran the
- *               32^3 damage sequence at 23.9 solves/s against 17.9 at 0.1) but an inner
- *               solve that FP32 cannot bring that far (stiff inclusions) then runs on to
- *               max_iter.
+ *   inner_tol:  KRS_MIXED_IR: relative residual the first inner solve aims for (<= 0: 0.1);
+ *               later inner solves aim for max(inner_tol, 0.1), and none for less than the
+ *               outer tolerance still needs.  An inner solve also ends when its residual
+ *               stalls (fell less than 4x over 32 iterations once below 1e-3 of its first
+ *               value), and a later one after 2 m_first + 100 iterations.  The first inner
+ *               solve's Krylov space feeds the recycling step: a smaller inner_tol gives
+ *               SRKS converged Ritz vectors.  The outer step is a flexible CG in FP64 over
+ *               the inner solves' corrections (each A-orthogonalised against the earlier
+ *               ones, step length from FP64 products).
  *   max_outer:  KRS_MIXED_IR: limit of refinement steps (<= 0: 30).  max_iter bounds the
  *               total of inner iterations.
  *   reselect:   SRKS only.  KRS_RESELECT_NONE (0), or KRS_RESELECT_CLUSTER (1): after the
@@ -370,7 +369,8 @@ krs_status krs_axpy2_dot(int64_t n, const double* alpha, const double* w, const 
 
 /* Eigenvalues (descending) of the symmetric tridiagonal matrix with diagonal delta[m] and
  * off-diagonal eta[m-1] (device pointers; theta: m doubles) by bisection on Sturm counts
- * -- the eigensolve of H_m (Section 4.1, Algorithm 3). */
+ * -- the eigensolve of H_m (Section 4.1, Algorithm 3).  m <= 16001 (KRS_ERR_INVALID_ARG
+ * beyond); orders whose matrix does not fit in shared memory read it from global memory. */
 krs_status krs_tridiag_eigvals(int32_t m, const double* delta, const double* eta,
                                double* theta, void* stream);
 

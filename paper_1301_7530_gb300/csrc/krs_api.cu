@@ -24,8 +24,10 @@
 using namespace krs;
 
 namespace krs {
+// eigenvalues of H_m and of its leading block of order m1 (Sturm multisection); e2_scratch:
+// m doubles, used when the order is too large to stage the matrix in shared memory
 cudaError_t launch_tridiag_eigvals2(int m, int m1, const double* delta, const double* eta, double* theta_m,
-                                    double* theta_m1, cudaStream_t st);
+                                    double* theta_m1, cudaStream_t st, double* e2_scratch);
 }
 static cudaError_t launch_df2d(const dfl* src, double* dst, int64_t count, cudaStream_t st);
 
@@ -775,7 +777,8 @@ static krs_status srks_begin(krs_seq* s, int m, int room, const krs_policy* p, i
   s->last_ritz_m = m;
   KRS_TRY(ensure_eig(s, m));
   KRS_CUDA(launch_lanczos(m, s->alpha, s->rho, s->delta, s->eta, s->stream));
-  KRS_CUDA(launch_tridiag_eigvals2(m, m - 1, s->delta, s->eta, s->theta_m, s->theta_m1, s->stream));
+  // tsel (5m doubles) is free until the selection: scratch of the long-order bisection
+  KRS_CUDA(launch_tridiag_eigvals2(m, m - 1, s->delta, s->eta, s->theta_m, s->theta_m1, s->stream, s->tsel));
   KRS_CUDA(launch_srks_select(m, s->theta_m, s->theta_m1, p->ritz_eps, p->theta_frac, p->reselect, room, s->sel,
                               s->selcount, s->tsel, s->stream));
   *launches += 3;
@@ -1336,9 +1339,12 @@ krs_status krs::refine_pass_begin(krs_seq* s, const krs_policy* p, double tol, S
     *finished = true;
     return KRS_OK;
   }
-  // aim at inner_tol, or less when the outer tolerance is closer than that
+  // the first pass aims at inner_tol (its Krylov space feeds the recycling step: a longer
+  // first pass gives SRKS converged Ritz vectors), later passes at max(inner_tol, 0.1); none
+  // aims lower than the outer tolerance still needs
+  const double pass_tol = (pp || ss->first) ? inner_tol : (inner_tol > 0.1 ? inner_tol : 0.1);
   double tin = 0.5 * tol * sqrt(bb / ss->rr);
-  if (tin < inner_tol) tin = inner_tol;
+  if (tin < pass_tol) tin = pass_tol;
   if (tin > 0.5) tin = 0.5;
   a.max_iter = p->max_iter - ss->m;
   // KRS_MIXED_IR: a later pass (same operator, new right-hand side) gets at most twice the
@@ -1585,8 +1591,13 @@ krs_status krs_axpy2_dot(int64_t n, const double* alpha, const double* w, const 
 
 krs_status krs_tridiag_eigvals(int32_t m, const double* delta, const double* eta, double* theta, void* stream) {
   if (m < 0 || (m > 0 && (!delta || !theta || (m > 1 && !eta)))) return fail(KRS_ERR_INVALID_ARG, "bad argument");
-  if (m > 12000) return fail(KRS_ERR_INVALID_ARG, "m > 12000");
-  KRS_CUDA(launch_tridiag_eigvals(m, delta, eta, theta, (cudaStream_t)stream));
+  if (m > 16001) return fail(KRS_ERR_INVALID_ARG, "m > 16001");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* e2 = nullptr;  // scratch of the long-order path (squared off-diagonal)
+  if (m > 1) KRS_CUDA(cudaMallocAsync((void**)&e2, sizeof(double) * (size_t)m, st));
+  const cudaError_t e = launch_tridiag_eigvals2(m, 0, delta, eta, theta, nullptr, st, e2);
+  if (e2) cudaFreeAsync(e2, st);
+  KRS_CUDA(e);
   return KRS_OK;
 }
 

@@ -87,17 +87,30 @@ __device__ __forceinline__ int sturm_count(int m, const double* d, const double*
 // q - m of T_{m1} (leading block).  Output: theta_m[m], theta_m1[m1], descending.
 constexpr int BISECT_WARPS = 4;  // one warp per SM sub-partition
 
+// SM: the tridiagonal is staged in shared memory (2m + 1 doubles); otherwise (an order too
+// large for shared memory) it is read from global memory, `eta` then holding the squared
+// off-diagonal (k_square below).
+template <bool SM>
 __global__ void __launch_bounds__(32 * BISECT_WARPS) k_bisect(int m, int m1, int L, const double* __restrict__ delta,
                                                               const double* __restrict__ eta, double* theta_m,
                                                               double* theta_m1) {
   extern __shared__ double sh[];
-  double* d = sh;
-  double* e2 = sh + m;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    d[i] = delta[i];
-    if (i < m - 1) e2[i] = eta[i] * eta[i];
+  const double* d;
+  const double* e2;
+  if constexpr (SM) {
+    double* ds = sh;
+    double* es = sh + m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      ds[i] = delta[i];
+      if (i < m - 1) es[i] = eta[i] * eta[i];
+    }
+    __syncthreads();
+    d = ds;
+    e2 = es;
+  } else {
+    d = delta;
+    e2 = eta;
   }
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int per_warp = 32 / L;
   const int grp = lane / L, sub = lane % L;
@@ -149,8 +162,13 @@ __global__ void __launch_bounds__(32 * BISECT_WARPS) k_bisect(int m, int m1, int
   }
 }
 
+__global__ void k_square(const double* __restrict__ v, double* __restrict__ out, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = v[i] * v[i];
+}
+
 cudaError_t launch_tridiag_eigvals2(int m, int m1, const double* delta, const double* eta, double* theta_m,
-                                    double* theta_m1, cudaStream_t st) {
+                                    double* theta_m1, cudaStream_t st, double* e2_scratch) {
   if (m <= 0) return cudaSuccess;
   const int jobs = m + m1;
   int dev = 0, sms = 152;
@@ -163,17 +181,28 @@ cudaError_t launch_tridiag_eigvals2(int m, int m1, const double* delta, const do
   const int per_warp = 32 / L;
   const int per_cta = per_warp * BISECT_WARPS;
   const size_t sm = sizeof(double) * (size_t)(2 * m + 1);
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
+  int sm_max = 0;
+  cudaDeviceGetAttribute(&sm_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const unsigned grid = (unsigned)((jobs + per_cta - 1) / per_cta);
+  if (sm <= (size_t)sm_max) {
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute((const void*)k_bisect<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    k_bisect<true><<<grid, 32 * BISECT_WARPS, sm, st>>>(m, m1, L, delta, eta, theta_m, theta_m1);
+  } else {
+    // too long for shared memory: the squared off-diagonal in the caller's scratch (m doubles)
+    if (!e2_scratch) return cudaErrorInvalidValue;
+    k_square<<<(m + 255) / 256, 256, 0, st>>>(eta, e2_scratch, m - 1);
+    k_bisect<false><<<grid, 32 * BISECT_WARPS, 0, st>>>(m, m1, L, delta, e2_scratch, theta_m, theta_m1);
   }
-  k_bisect<<<(jobs + per_cta - 1) / per_cta, 32 * BISECT_WARPS, sm, st>>>(m, m1, L, delta, eta, theta_m, theta_m1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tridiag_eigvals(int m, const double* delta, const double* eta, double* theta,
                                    cudaStream_t st) {
-  return launch_tridiag_eigvals2(m, 0, delta, eta, theta, nullptr, st);
+  return launch_tridiag_eigvals2(m, 0, delta, eta, theta, nullptr, st, nullptr);
 }
 
 // ------------------------------------------------------------------------------------

@@ -123,8 +123,10 @@ def test_axpy2_dot(gpu_lib):
     assert abs(_np(rr)[0] - rr_ref @ rr_ref) <= 1e-13 * (rr_ref @ rr_ref)
 
 
-@pytest.mark.parametrize("m", [1, 2, 9, 64, 333])
+@pytest.mark.parametrize("m", [1, 2, 9, 64, 333, 15000])
 def test_tridiag_eigvals_closed_form(gpu_lib, m):
+    """tridiag(1, 2, 1): eigenvalues 2 + 2 cos(k pi / (m + 1)).  m = 15000 is too long for the
+    matrix to be staged in shared memory (the bisection reads it from global memory)."""
     import torch
     d, e = _dev(np.full(m, 2.0)), _dev(np.ones(max(m - 1, 1)))
     th = torch.zeros(m, device="cuda", dtype=torch.float64)

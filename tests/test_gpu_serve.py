@@ -61,7 +61,9 @@ def test_eviction_under_small_budget_same_results():
     arrivals = S.poisson_arrivals(len(NS), SYSTEMS, rate=2000.0, seed=23)
     big, info_big = _serve(list(range(len(NS))), arrivals)
     assert info_big["evictions"] == 0
-    small, info_small = _serve(list(range(len(NS))), arrivals, budget=24 << 20)
+    # a budget of half the device memory the unconstrained run held at its peak forces
+    # idle clients' spaces out to the host and back
+    small, info_small = _serve(list(range(len(NS))), arrivals, budget=max(1 << 20, info_big["peak"] // 2))
     assert info_small["evictions"] > 0 and info_small["reimports"] > 0
     for key, (x, m, nc, st, _) in big.items():
         xs, ms, ncs, sts, _ = small[key]
