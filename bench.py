@@ -1035,7 +1035,7 @@ def run_many(args, kind):
     Ns, systems, clients = _many(args, kind)
     B.lib()
     pol = B.make_policy("srks", "block_jacobi3", ritz_eps=args.ritz_eps, theta_frac=args.theta_frac,
-                        max_aug=100, max_iter=1000 if args.precision in ("fp64", "double_float") else 800,
+                        max_aug=100, max_iter=1000 if args.precision in ("fp64", "double_float") else 1500,
                         precision=args.precision, inner_tol=args.inner_tol)
     quantum = args.quantum if args.quantum is not None else (0 if kind == "batched" else 32)
     budget = int(args.budget_gb * (1 << 30)) if kind == "served" else int(200 * (1 << 30))

@@ -673,9 +673,10 @@ static krs_status ensure_mixed(krs_seq* s, int max_iter, int64_t nnzb) {
     KRS_TRY(alloc_n(s, &s->rrh, (size_t)s->cap_w32));
     s->rrh_cap = s->cap_w32;
   }
-  // C32 / AC32 hold C, then the directions of the earlier inner solves of the same system
-  if (s->cap_c + s->cap_w32 > s->cap_c32) {
-    const int cap = s->cap_c + s->cap_w32;
+  // C32 / AC32 hold the FP32 copy of C (every inner solve starts from the recycled space
+  // alone, so no room for earlier passes' directions)
+  if (s->cap_c > s->cap_c32 || !s->C32) {
+    const int cap = s->cap_c > 0 ? s->cap_c : 1;
     dev_free(s, s->C32);
     dev_free(s, s->AC32);
     dev_free(s, s->dinv);
@@ -683,7 +684,7 @@ static krs_status ensure_mixed(krs_seq* s, int max_iter, int64_t nnzb) {
     s->dinv = nullptr;
     KRS_TRY(alloc_n(s, &s->C32, (size_t)cap * s->ld));
     KRS_TRY(alloc_n(s, &s->AC32, (size_t)cap * s->ld));
-    KRS_TRY(alloc_n(s, &s->dinv, (size_t)s->cap_w32));
+    KRS_TRY(alloc_n(s, &s->dinv, 1));
     s->cap_c32 = cap;
   }
   return KRS_OK;

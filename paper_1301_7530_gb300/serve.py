@@ -110,7 +110,7 @@ class Server:
         room = self.policy.max_aug if self.policy.max_aug > 0 else cap
         if self.policy.precision == 1:  # refinement: FP32 storage for max_iter inner iterations
             wi = _round_up(self.policy.max_iter + 1, 32)
-            est = ld * (4 * 3 * wi + 4 * 2 * (room + wi) + 8 * 2 * room + 40) + (72 + 36) * c.nnzb
+            est = ld * (4 * 3 * wi + 4 * 2 * room + 8 * 2 * room + 40) + (72 + 36) * c.nnzb
         else:
             est = 8 * ld * (2 * cap + 1 + 2 * room) + 4 * cap * cap + 72 * c.nnzb
         if c.evicted is not None:
