@@ -15,8 +15,10 @@ of GB) is far larger than L2.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl krs|reference]
 
 Beside the headline the line carries: the same systems in the double-float precision (a
-bounded sample), the 32^3 damage sequence in FP64 (one step = its 20 systems), an
-end-to-end figure through the C ABI with host buffers, and the oracle's CPU baseline.
+bounded sample), the sequence's first systems in the mixed precision (FP32 passes under an
+FP64 flexible-CG outer step) against FP64's time and results on them, the 32^3 damage
+sequence in FP64 (one step = its 20 systems), an end-to-end figure through the C ABI with
+host buffers, and the oracle's CPU baseline.
 Multi-GPU (torchrun): every rank solves its own sequence (independent problems, no data
 collective); value = all ranks' solves / the slowest rank's time ("weak" scaling).
 --impl reference times the FP64 CPU oracle (rank 0 only): each step a bounded sample of the
