@@ -103,3 +103,18 @@ def test_sequence_profile_shape():
     assert prof[0][1] == 0  # the sequence starts from an empty space
     for k in range(1, 15):  # n_c grows by the selected vectors, up to the cap
         assert prof[k][1] == min(300, prof[k - 1][1] + prof[k - 1][2])
+
+
+def test_cost_model_calibration_runs_on_a_small_cube():
+    """The CPU baseline's calibration (bounded oracle samples) on a 6^3 cube: every constant
+    is a positive time and the model grows with the iteration count and the space size."""
+    A = P.elasticity_inclusions(6, 3000)
+    b = P.traction_rhs(6, P.random_traction(6, 3100))
+    cal = bench.oracle_calibrate(A, b, eig=False)
+    for key in ("t_pre", "c_fix", "t_spmv"):
+        assert cal[key] > 0.0, (key, cal)
+    assert cal["c_col"] >= 0.0 and cal["t_dot"] >= 0.0 and cal["threads"] >= 1
+    cal.update({"t_eig_cal": 1.0, "m_eig_cal": 100, "eig_exponent": 3.0})
+    t1 = sum(bench.oracle_model_seconds(cal, 0, 100, 1))
+    t2 = sum(bench.oracle_model_seconds(cal, 50, 200, 1))
+    assert t2 > t1 > 0.0
