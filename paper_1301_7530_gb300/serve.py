@@ -20,7 +20,6 @@ from __future__ import annotations
 
 import collections
 import dataclasses
-import math
 import time
 
 import numpy as np
